@@ -1,0 +1,258 @@
+"""FP64 CPU oracle for the DirectLiNGAM causal-ordering path -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline
+leg and ``--impl reference`` arm) may import this package.  It shares no code
+with the CUDA path (``paper_2403_03772_gb300``) and neither imports the other.
+
+Pieces and the passage each follows (AcceleratedLiNGAM, arXiv 2403.03772):
+
+* ``causal_order`` / ``search_step`` -- Algorithm 1 and the DirectLiNGAM loop
+  of Sec. 2.2, in plain C (``lingam_oracle.c``, FP64, OpenMP over pairs only).
+* ``fit_adjacency`` -- Sec. 1: each variable is regressed by least squares on
+  the variables earlier in the causal order; the coefficients form the
+  weighted adjacency matrix B[effect, cause] (Sec. 4.1 calls it the "weighted
+  adjacency matrix").  ``numpy.linalg.lstsq`` per row on the centred data.
+* ``varlingam`` -- Sec. 3.2: least-squares VAR fit (intercept included, as in
+  the statsmodels estimator named in Sec. 4.2), DirectLiNGAM on the
+  innovations, then B_tau = (I - B0) M_tau.
+
+Parity pins live in ``tests/test_oracle_*.py``.  Everything here is pinned
+except the three literature constants K1, GAMMA and K2 of the entropy
+approximation beyond what quadrature and the closed form of K2 fix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lingam_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBPATH = os.path.join(_LIBDIR, "liblingam_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_DEGENERATE, ERR_NOMEM = 0, 1, 2, 3, 5
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with status {code}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if (not force and os.path.exists(_LIBPATH)
+            and os.path.getmtime(_LIBPATH) >= os.path.getmtime(_SRC)):
+        return _LIBPATH
+    tmp = _LIBPATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIBPATH)
+        D, I64, I32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+        PD, PI32 = ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int32)
+        lib.oracle_search_step.argtypes = [PD, I64, I64, PI32, I64, PD, I32, I32, PD, PD, PD,
+                                           ctypes.POINTER(I32)]
+        lib.oracle_causal_order.argtypes = [PD, I64, I64, I32, I32, PI32, PD, I64]
+        lib.oracle_moments.argtypes = [PD, I64, PD, PD, PD, PD]
+        lib.oracle_entropy.argtypes = [PD, I64, PD, PD]
+        lib.oracle_entropy_from_moments.argtypes = [D, D]
+        lib.oracle_entropy_from_moments.restype = D
+        lib.oracle_residual.argtypes = [PD, PD, I64, PD, PD]
+        lib.oracle_standardize.argtypes = [PD, I64, PD, PD]
+        lib.oracle_diff_mutual_info.argtypes = [PD, PD, PD, PD, I64, PD, PD]
+        lib.oracle_argmax_first.argtypes = [PD, I64]
+        lib.oracle_mean.argtypes = [PD, I64]
+        lib.oracle_mean.restype = D
+        lib.oracle_max_threads.restype = I32
+        _lib = lib
+        return lib
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise OracleError(code, what)
+
+
+# ------------------------------------------------------------- primitives ----
+
+def standardize(x) -> np.ndarray:
+    x = _f64(x)
+    out = np.empty_like(x)
+    tmp = np.empty_like(x)
+    _check(_load().oracle_standardize(_pd(x), x.size, _pd(out), _pd(tmp)), "standardize")
+    return out
+
+
+def residual(a, b) -> np.ndarray:
+    """_residual(a, b) = a - (cov(a, b)/var(b)) b, cov and var normalised by 1/n."""
+    a, b = _f64(a), _f64(b)
+    out = np.empty_like(a)
+    tmp = np.empty_like(a)
+    _check(_load().oracle_residual(_pd(a), _pd(b), a.size, _pd(out), _pd(tmp)), "residual")
+    return out
+
+
+def moments(v) -> tuple[float, float]:
+    """(E[log cosh u], E[u exp(-u^2/2)]) of v standardised by its own mean/std."""
+    v = _f64(v)
+    m1, m2, var = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    tmp = np.empty_like(v)
+    _check(_load().oracle_moments(_pd(v), v.size, ctypes.byref(m1), ctypes.byref(m2),
+                                  ctypes.byref(var), _pd(tmp)), "moments")
+    return m1.value, m2.value
+
+
+def entropy(v) -> float:
+    v = _f64(v)
+    h = ctypes.c_double()
+    tmp = np.empty_like(v)
+    _check(_load().oracle_entropy(_pd(v), v.size, ctypes.byref(h), _pd(tmp)), "entropy")
+    return h.value
+
+
+def entropy_from_moments(m1: float, m2: float) -> float:
+    return _load().oracle_entropy_from_moments(float(m1), float(m2))
+
+
+def diff_mutual_info(xi_std, xj_std, ri_j, rj_i) -> float:
+    arrs = [_f64(a) for a in (xi_std, xj_std, ri_j, rj_i)]
+    out = ctypes.c_double()
+    tmp = np.empty_like(arrs[0])
+    _check(_load().oracle_diff_mutual_info(*[_pd(a) for a in arrs], arrs[0].size,
+                                           ctypes.byref(out), _pd(tmp)), "diff_mutual_info")
+    return out.value
+
+
+def argmax_first(v) -> int:
+    v = _f64(v)
+    return int(_load().oracle_argmax_first(_pd(v), v.size))
+
+
+# ----------------------------------------------------------- one step -------
+
+def search_step(R, U=None, literal: bool = False, threads: int | None = None,
+                ref_var=None) -> dict:
+    """Algorithm 1 on data R ([n, d] samples x variables) over variables U.
+
+    Returns k_list [p], I [p, p] (I[a, b] = I(U[a], U[b])), Hz [p] and m (the
+    chosen original index) and m_pos."""
+    R = np.asarray(R, dtype=np.float64)
+    n, d = R.shape
+    Rc = np.ascontiguousarray(R.T)                   # column-major by variable
+    U = np.arange(d, dtype=np.int32) if U is None else np.ascontiguousarray(U, dtype=np.int32)
+    p = U.size
+    kl = np.empty(p)
+    I = np.empty((p, p))
+    Hz = np.empty(p)
+    mpos = ctypes.c_int()
+    ref = None if ref_var is None else _f64(ref_var)
+    code = _load().oracle_search_step(
+        _pd(Rc), n, n, U.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p,
+        _pd(ref) if ref is not None else None, int(bool(literal)),
+        int(threads or default_threads()), _pd(kl), _pd(I), _pd(Hz), ctypes.byref(mpos))
+    _check(code, "search_step")
+    return {"k_list": kl, "I": I, "Hz": Hz, "m_pos": mpos.value, "m": int(U[mpos.value])}
+
+
+def causal_order(X, literal: bool = False, threads: int | None = None,
+                 scores: bool = False, max_steps: int = 0):
+    """DirectLiNGAM causal order of X ([n, d]); optionally the per-step scores
+    (row t = k_list of step t at the original indices, NaN once removed)."""
+    X = _f64(X)
+    n, d = X.shape
+    order = np.empty(d, dtype=np.int32)
+    sc = np.empty((d, d)) if scores else None
+    code = _load().oracle_causal_order(
+        _pd(X), n, d, int(bool(literal)), int(threads or default_threads()),
+        order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        _pd(sc) if sc is not None else None, int(max_steps))
+    _check(code, "causal_order")
+    return (order, sc) if scores else order
+
+
+# ------------------------------------------------------------ adjacency -----
+
+def adjacency_rows(X, order, rows=None) -> np.ndarray:
+    """Rows of the weighted adjacency B for the variables ``rows`` (original
+    indices; default all): B[k, pred(k)] = least-squares coefficients of x_k
+    on every variable before it in ``order`` (centred data, so the intercept
+    drops out).  Returns a [len(rows), d] array."""
+    X = np.asarray(X, dtype=np.float64)
+    Xc = X - X.mean(axis=0)
+    d = X.shape[1]
+    order = np.asarray(order, dtype=np.int64)
+    pos = np.empty(d, dtype=np.int64)
+    pos[order] = np.arange(d)
+    rows = order if rows is None else np.asarray(rows, dtype=np.int64)
+    out = np.zeros((len(rows), d))
+    for r, k in enumerate(rows):
+        pred = order[:pos[k]]
+        if pred.size == 0:
+            continue
+        coef, *_ = np.linalg.lstsq(Xc[:, pred], Xc[:, k], rcond=None)
+        out[r, pred] = coef
+    return out
+
+
+def fit_adjacency(X, order) -> np.ndarray:
+    d = np.asarray(X).shape[1]
+    rows = np.arange(d)
+    return adjacency_rows(X, order, rows)
+
+
+# ------------------------------------------------------------- VarLiNGAM ----
+
+def var_fit(Xt, lags: int = 1):
+    """Least-squares VAR(lags) with intercept.  Returns (M [lags, d, d], E)
+    where x(t) = c + sum_tau M[tau-1] x(t-tau) + E(t), E the residuals."""
+    Xt = np.asarray(Xt, dtype=np.float64)
+    T, d = Xt.shape
+    Y = Xt[lags:]
+    Z = np.hstack([np.ones((T - lags, 1))] + [Xt[lags - tau:T - tau] for tau in range(1, lags + 1)])
+    coef, *_ = np.linalg.lstsq(Z, Y, rcond=None)       # [(1 + lags d), d]
+    E = Y - Z @ coef
+    M = np.stack([coef[1 + (tau - 1) * d:1 + tau * d].T for tau in range(1, lags + 1)])
+    return M, E
+
+
+def varlingam(Xt, lags: int = 1, threads: int | None = None, order=None):
+    """VarLiNGAM (Sec. 3.2): returns order, B0 [d, d], Btau [lags, d, d], M, E.
+
+    ``order`` may be passed to skip the ordering (for sampled checks)."""
+    M, E = var_fit(Xt, lags)
+    if order is None:
+        order = causal_order(E, threads=threads)
+    B0 = fit_adjacency(E, order)
+    d = B0.shape[0]
+    Btau = np.stack([(np.eye(d) - B0) @ M[tau] for tau in range(lags)])
+    return np.asarray(order), B0, Btau, M, E

@@ -1,0 +1,116 @@
+"""Write the stored oracle outputs used by the GPU parity tests.
+
+Every value written here comes from ``oracle/`` (FP64 CPU) run on the seeded
+inputs of ``gen/``; nothing comes from the CUDA path.  Each file records the
+workload, its seed and the SHA-256 prefix of the generated float32 data, so a
+test can refuse to compare against data that drifted.
+
+    python tests/golden/make_golden.py cfg1 cfg2 cfg4 cfg5 cfg3 [--threads N]
+
+cfg3 (d=1000, n=10000) is ~1e5 core-seconds of FP64 libm work.
+"""
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import gen      # noqa: E402
+import oracle   # noqa: E402
+
+# cfg5 instances the oracle orders in full (small uneven ones plus a few resamples)
+CFG5_RESAMPLES = (0, 1, 2, 3)
+CFG5_MAX_D = 120
+
+
+def write_order(name, order, header_lines):
+    path = os.path.join(HERE, f"{name}_order.txt")
+    with open(path + ".tmp", "w") as f:
+        for h in header_lines:
+            f.write(f"# {h}\n")
+        f.write(" ".join(str(int(v)) for v in order) + "\n")
+    os.replace(path + ".tmp", path)
+    print("wrote", path, flush=True)
+
+
+def header(workload, digest, seconds, threads):
+    return [
+        "DirectLiNGAM causal order from the FP64 oracle (oracle.causal_order, memoised mode,",
+        "bitwise identical to the literal Algorithm 1 loop).",
+        f"workload: {workload}",
+        f"data-sha256-16: {digest}",
+        f"oracle wall seconds: {seconds:.1f} on {threads} threads",
+        "written by tests/golden/make_golden.py",
+    ]
+
+
+def run_cfg(k, threads):
+    ds = getattr(gen, f"cfg{k}")()
+    t = time.time()
+    order = oracle.causal_order(ds.X, threads=threads)
+    write_order(f"cfg{k}", order,
+                header(f"cfg{k} d={ds.d} n={ds.n} seed={gen.SEEDS[k]}", ds.digest(),
+                       time.time() - t, threads))
+
+
+def run_cfg4(threads):
+    vd = gen.cfg4()
+    t = time.time()
+    M, E = oracle.var_fit(vd.Xt, 1)
+    order = oracle.causal_order(E, threads=threads)
+    write_order("cfg4", order,
+                header(f"cfg4 VarLiNGAM innovations d={vd.Xt.shape[1]} T={vd.Xt.shape[0]} lag=1 "
+                       f"seed={gen.SEEDS[4]}", vd.digest(), time.time() - t, threads))
+
+
+def cfg5_selected(insts):
+    sel = list(CFG5_RESAMPLES)
+    for k, inst in enumerate(insts):
+        if inst.rows is None and inst.X.shape[1] <= CFG5_MAX_D:
+            sel.append(k)
+    return sel
+
+
+def run_cfg5(threads):
+    insts = gen.cfg5()
+    sel = cfg5_selected(insts)
+    path = os.path.join(HERE, "cfg5_orders.txt")
+    with open(path + ".tmp", "w") as f:
+        f.write("# DirectLiNGAM causal orders from the FP64 oracle for selected cfg5 instances.\n")
+        f.write(f"# workload: cfg5 seed={gen.SEEDS[5]}; one line per instance:\n")
+        f.write("# <instance index> <name> <data-sha256-16> : <order>\n")
+        f.write("# written by tests/golden/make_golden.py\n")
+        for k in sel:
+            X = insts[k].data()
+            dig = __import__("hashlib").sha256(np.ascontiguousarray(X).tobytes()).hexdigest()[:16]
+            t = time.time()
+            order = oracle.causal_order(X, threads=threads)
+            print(f"cfg5[{k}] {insts[k].name} d={X.shape[1]} n={X.shape[0]} "
+                  f"{time.time() - t:.1f}s", flush=True)
+            f.write(f"{k} {insts[k].name} {dig} : " + " ".join(str(int(v)) for v in order) + "\n")
+    os.replace(path + ".tmp", path)
+    print("wrote", path, flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", nargs="+")
+    ap.add_argument("--threads", type=int, default=oracle.default_threads())
+    a = ap.parse_args()
+    for w in a.which:
+        if w in ("cfg1", "cfg2", "cfg3"):
+            run_cfg(int(w[-1]), a.threads)
+        elif w == "cfg4":
+            run_cfg4(a.threads)
+        elif w == "cfg5":
+            run_cfg5(a.threads)
+        else:
+            raise SystemExit(f"unknown workload {w}")
+
+
+if __name__ == "__main__":
+    main()
