@@ -1,0 +1,336 @@
+"""Benchmark of the GB300 DirectLiNGAM causal-ordering path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full causal order (pack, covariance, all d-1 ordering steps of
+Algorithm 1 + regress-out) of the d=1000, n=10000 gene-expression-shaped
+workload (synthetic, scale-free DAG, Student-t(5) noise), input resident in
+HBM.  The unit of work is one residual-sample: an ordered pair (i, j) at one
+sample, W = n (d+1) d (d-1) / 3 per order.  ``value`` is W / time in
+pair-samples per second for the mixed-precision form; the plain FP32 form is
+timed beside it under ``forms``.
+
+Under torchrun (N > 1) every rank orders its own independently seeded dataset
+of the same shape (weak scaling, no data-path collective); a barrier and a
+max over ranks bracket the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
+host cores over a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "order time plain vs mixed/batched at d=1000,n=10k; pair·sample/s vs peak"
+UNIT = "pair·sample/s"
+WORKLOAD = "directlingam_order_d1000_n10000_scalefree_t5"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference --
+def oracle_sample_step(X, p_sample: int, threads: int):
+    """Bounded sample of the workload for the CPU oracle: the first ordering
+    step of Algorithm 1 restricted to the first ``p_sample`` variables."""
+    import oracle
+    U = np.arange(p_sample, dtype=np.int32)
+    t = time.perf_counter()
+    oracle.search_step(X, U=U, threads=threads)
+    dt = time.perf_counter() - t
+    units = X.shape[0] * p_sample * (p_sample - 1)
+    return units, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    ds = gen.cfg3()
+    X = ds.X.astype(np.float64)
+    threads = oracle.default_threads()
+    p_sample = args.ref_p
+    for _ in range(args.warmup):
+        oracle_sample_step(X, p_sample, threads)
+    units = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        u, dt = oracle_sample_step(X, p_sample, threads)
+        units += u
+        secs += dt
+    val = units / secs
+    sample = (f"first ordering step of Algorithm 1 restricted to the first {p_sample} of the "
+              f"1000 variables, n=10000 ({p_sample * (p_sample - 1) * 10000:.3e} "
+              f"residual-samples per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64-oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- ours --
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def time_form(ctx, X, steps, warmup, flush_buf, torch, rank, world):
+    """Per-step device time (events on the caller's stream), L2 flushed between
+    steps; returns (ms list, stats list)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.causal_order(X)
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    for _ in range(steps):
+        flush_buf.add_(1.0)                      # 256 MB write evicts the 129 MB L2
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        order = ctx.causal_order(X)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        stats.append(ctx.stats())
+    return ms, stats, order
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2403_03772_gb300 as pkg
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    seed = gen.SEEDS[3] + 7919 * rank
+    ds = gen.cfg3(seed=seed)
+    n, d = ds.X.shape
+    W = gen.residual_samples(d, n)
+    X = torch.from_numpy(ds.X).to(f"cuda:{dev}")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+
+    forms = {}
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_region0 = time.perf_counter()
+    for prec in args.forms:
+        with pkg.Context(dev, prec, profile=True) as ctx:
+            ms, stats, order = time_form(ctx, X, args.steps, args.warmup, flush, torch, rank, world)
+            pair_ms = sum(s["pair_ms"] for s in stats)
+            pair_units = sum(s["pair_units"] for s in stats)
+            forms[prec] = {"ms": ms, "pair_ms": pair_ms, "pair_units": pair_units,
+                           "pair_launches": sum(s["pair_launches"] for s in stats),
+                           "refined_steps": stats[-1]["refined_steps"],
+                           "genuine_ties": stats[-1]["genuine_ties"],
+                           "graph_nodes": stats[-1]["graph_nodes"],
+                           "order_head": [int(v) for v in order[:8]]}
+    region_s = time.perf_counter() - t_region0
+    clk = clocks.stop()
+
+    # max over ranks of the summed step time
+    head = args.forms[0]
+    tot_ms = {p: sum(forms[p]["ms"]) for p in args.forms}
+    if world > 1:
+        for p in args.forms:
+            t = torch.tensor([tot_ms[p]], dtype=torch.float64, device=f"cuda:{dev}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot_ms[p] = float(t.item())
+
+    # e2e: the same call with a pinned host input, copies inside the timed region
+    e2e = None
+    with pkg.Context(dev, head) as ctx:
+        Xh = torch.from_numpy(ds.X).pin_memory()
+        ctx.causal_order(Xh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            if world > 1:
+                torch.distributed.barrier()
+            ctx.causal_order(Xh)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{dev}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": W * world * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(d * 4)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the pair-moment kernel) against the
+    # per-clock unit rates measured by the probes and the sampled SM clock
+    with pkg.Context(dev, "fp32") as ctx:
+        fma, f_mhz = ctx.peak_probe(0)
+        ex2, e_mhz = ctx.peak_probe(1)
+        lg2, l_mhz = ctx.peak_probe(2)
+        dfma, d_mhz = ctx.peak_probe(3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_clk = {"fp32_ops": fma / 2 / (sms * f_mhz * 1e6), "ex2": ex2 / (sms * e_mhz * 1e6),
+               "lg2": lg2 / (sms * l_mhz * 1e6), "fp64_fma": dfma / 2 / (sms * d_mhz * 1e6)}
+    run_mhz = clk.get("sm_mhz") or f_mhz
+    # fast form per residual-sample: 2 ex2 + 1 lg2 on MUFU, 8 FP32-pipe ops
+    mufu_rate = 1.0 / (2.0 / (per_clk["ex2"] * sms * run_mhz * 1e6) +
+                       1.0 / (per_clk["lg2"] * sms * run_mhz * 1e6))
+    fp32_rate = per_clk["fp32_ops"] * sms * run_mhz * 1e6 / 8.0
+    peak = min(mufu_rate, fp32_rate)
+    f = forms[head]
+    achieved = f["pair_units"] / (f["pair_ms"] * 1e-3) if f["pair_ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"k_pair_moments ({head})",
+                "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gres/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "peak_from": {"sm_mhz": run_mhz, "sms": sms, "per_clock_per_sm": per_clk,
+                              "mufu_bound_gres": mufu_rate / 1e9,
+                              "fp32_bound_gres": fp32_rate / 1e9,
+                              "ops_per_residual_sample": {"mufu_ex2": 2, "mufu_lg2": 1,
+                                                          "fp32_pipe": 8}},
+                "kernel_share": f["pair_ms"] / sum(f["ms"])}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        threads = oracle.default_threads()
+        units, dt = oracle_sample_step(ds.X.astype(np.float64), args.cpu_p, threads)
+        cpu = {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first ordering step of Algorithm 1 over the first {args.cpu_p} of the "
+                         f"1000 variables, n=10000 ({units:.3e} residual-samples, {dt:.1f} s)"}
+
+    ms_per_step = tot_ms[head] / args.steps
+    value = W * world * args.steps / (tot_ms[head] * 1e-3)
+    launches_per_step = f["graph_nodes"] + 2
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "d": d, "n": n, "precision": head,
+                   "residual_samples_per_step": W, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"independent problem per GPU x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "forms": {p: {"ms_per_step": tot_ms[p] / args.steps,
+                      "value": W * world * args.steps / (tot_ms[p] * 1e-3),
+                      "pair_kernel_ms_per_step": forms[p]["pair_ms"] / args.steps,
+                      "refined_steps": forms[p]["refined_steps"],
+                      "genuine_ties": forms[p]["genuine_ties"],
+                      "order_head": forms[p]["order_head"]} for p in args.forms},
+        "timed_region_s": region_s,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--forms", default="mixed,fp32")
+    ap.add_argument("--cpu-p", type=int, default=560)
+    ap.add_argument("--ref-p", type=int, default=240)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.forms = [f for f in args.forms.split(",") if f]
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * lingam.h -- C ABI of the GB300 (sm_103a) DirectLiNGAM / VarLiNGAM library.
+ *
+ * The library computes the causal-ordering step of DirectLiNGAM as described
+ * in AcceleratedLiNGAM (arXiv 2403.03772): Algorithm 1 ("search_causal_order")
+ * repeated inside the DirectLiNGAM loop of Sec. 2.2, the least-squares
+ * adjacency of Sec. 1, and VarLiNGAM (Sec. 3.2).  All arithmetic runs in the
+ * library's own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every call
+ *   - Data X is [n samples][d variables] (the paper's "dataset [m, dim]"):
+ *     LINGAM_ROW_MAJOR: element (s, i) at X[s*ld + i], ld >= d;
+ *     LINGAM_COL_MAJOR: element (s, i) at X[i*ld + s], ld >= n.
+ *     X may be a device pointer or a host pointer (pinned or pageable); the
+ *     library detects which and copies host data to its own device workspace.
+ *   - The caller owns every input and output buffer.  The context owns its
+ *     device workspace and its captured CUDA graphs.
+ *   - Work is ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls that return host outputs synchronise before returning.
+ *   - One context per host thread; a context is not thread-safe.
+ *   - No call throws or aborts.  Errors come back as lingam_status; the text
+ *     of the last error is available from lingam_last_error().
+ *   - Status meanings: ARG = invalid size/pointer/layout; NONFINITE = NaN or
+ *     Inf in the input; DEGENERATE = a variance reached zero relative to the
+ *     variable's original variance (<= 1e-12 relative), or two residualised
+ *     variables became perfectly correlated (1 - rho^2 <= 1e-12), or d > n;
+ *     CUDA = a CUDA runtime error; OOM = device allocation failed; TIMEOUT =
+ *     a bounded device-side wait expired (the kernel gave up and returned).
+ */
+#ifndef LINGAM_GB300_H
+#define LINGAM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lingam_stream_t; /* same type as cudaStream_t */
+typedef struct lingam_ctx lingam_ctx;         /* opaque */
+
+typedef enum {
+    LINGAM_OK = 0,
+    LINGAM_ERR_ARG = 1,
+    LINGAM_ERR_NONFINITE = 2,
+    LINGAM_ERR_DEGENERATE = 3,
+    LINGAM_ERR_CUDA = 4,
+    LINGAM_ERR_OOM = 5,
+    LINGAM_ERR_TIMEOUT = 6
+} lingam_status;
+
+/* Arithmetic of the ordering step.
+ *   FP32  -- entropy moments in FP32 with the accurate CUDA expf/log1pf, FP64
+ *            covariance (Gram), FP64 residual data, rank-1 downdate and OLS.
+ *   MIXED -- Gram on the tensor cores (TF32 hi+lo split products, FP32
+ *            accumulation), entropy moments with the hardware ex2/lg2
+ *            approximations and compensated summation; FP64 downdate and OLS.
+ *   FP64  -- every moment in FP64 (small problems; GB300 FP64 is slow).
+ * In every mode a step whose top scores lie within the FP32 error bound of
+ * each other is re-scored in FP64 before the argmax is taken. */
+typedef enum { LINGAM_PREC_FP32 = 0, LINGAM_PREC_MIXED = 1, LINGAM_PREC_FP64 = 2 } lingam_precision;
+
+typedef enum { LINGAM_ROW_MAJOR = 0, LINGAM_COL_MAJOR = 1 } lingam_layout;
+
+typedef struct {
+    int32_t precision;     /* lingam_precision */
+    int32_t profile;       /* 1: time every launch of the pair-moment kernel
+                              with CUDA events (read back by lingam_get_stats) */
+    double tie_scale;      /* multiplies the FP32 error bound that selects the
+                              candidates re-scored in FP64; 0 means 1.0 */
+    int32_t reserved[8];
+} lingam_opts;
+
+/* Create a context on CUDA device `device`.  opts may be NULL (FP32, no
+ * profiling).  *ctx receives the handle (NULL on failure). */
+lingam_status lingam_create(lingam_ctx **ctx, int device, const lingam_opts *opts);
+
+/* Release the context, its workspace and its graphs.  NULL is allowed. */
+lingam_status lingam_destroy(lingam_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next
+ * call on the same context.  ctx == NULL gives the last creation error. */
+const char *lingam_last_error(const lingam_ctx *ctx);
+
+/* Change the precision of later calls (lingam_precision). */
+lingam_status lingam_set_precision(lingam_ctx *ctx, int32_t precision);
+
+/*
+ * DirectLiNGAM causal order (Algorithm 1 inside the loop of Sec. 2.2).
+ *   X          FP32 data (FP64 when the context precision is FP64), n x d
+ *              in `layout` with leading dimension `ld`; read only.
+ *   order_out  host int32[d]: original variable indices, most exogenous
+ *              first (the paper's causal order K).
+ *   scores_out optional host double[d*d]: row t holds the step-t scores
+ *              M(i) = -sum_j min(0, I(i,j))^2 (Algorithm 1's k_list) at the
+ *              original indices, NaN for variables already ordered; row d-1
+ *              holds 0 for the last variable.
+ * Requires 1 <= d <= n, n >= 2.  d == 1 returns [0].
+ */
+lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
+                                  int64_t ld, int32_t layout, int32_t *order_out,
+                                  double *scores_out, lingam_stream_t stream);
+
+/*
+ * Weighted adjacency by least squares on the causal order (Sec. 1): row k of
+ * B holds the OLS coefficients of x_k regressed on every variable that
+ * precedes k in `order` (data centred, so the intercept drops out); all other
+ * entries are 0.  B[i*d + j] = effect of x_j on x_i.
+ *   order      host int32[d], a permutation of 0..d-1.
+ *   B_out      double[d*d], host memory, or device memory if B_on_device.
+ * Computed as B = I - L^{-1} where the order-permuted covariance is L D L^T,
+ * all in FP64.
+ */
+lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
+                                   int64_t ld, int32_t layout, const int32_t *order,
+                                   double *B_out, int32_t B_on_device, lingam_stream_t stream);
+
+/*
+ * VarLiNGAM (Sec. 3.2): least-squares VAR(lags) with intercept on the time
+ * series Xt ([T][d] in `layout`), DirectLiNGAM on the n = T - lags residual
+ * innovations, B0 by least squares on that order, and B_tau = (I - B0) M_tau.
+ *   order_out  host int32[d]; B0_out host double[d*d]; Btau_out host
+ *              double[lags*d*d] (tau = 1..lags, each d x d, B[i*d+j] =
+ *              effect of x_j(t - tau) on x_i(t)).  B0_out/Btau_out may be NULL.
+ * Xt is FP32.  Requires lags >= 1 and T - lags > lags*d + d.
+ */
+lingam_status varlingam_fit(lingam_ctx *ctx, const void *Xt, int64_t T, int64_t d, int64_t ld,
+                            int32_t layout, int32_t lags, int32_t *order_out, double *B0_out,
+                            double *Btau_out, lingam_stream_t stream);
+
+/*
+ * Many independent DirectLiNGAM problems in one call (bootstrap resamples
+ * and problems of uneven size).  Instance k orders the FP32 data X (row-major
+ * [n_src][ld], ld >= d) restricted to the rows rows[0..n) when rows != NULL
+ * (sampling with replacement is allowed; rows is a host int32 array), or to
+ * its first n rows when rows == NULL (then n <= n_src).
+ *   orders_out[k]  host int32[d_k]
+ *   B_out[k]       optional host double[d_k*d_k] adjacency of instance k
+ *                  (B_out itself may be NULL).
+ * All instances advance through their ordering steps together in one CUDA
+ * graph.  Returns the first failing instance's status; *failed_index (may be
+ * NULL) receives its index or -1.
+ */
+typedef struct {
+    const void *X;        /* FP32 row-major data, device or host */
+    int64_t n_src;        /* rows available in X */
+    int64_t n;            /* rows used (length of rows[] when rows != NULL) */
+    int64_t d;
+    int64_t ld;
+    const int32_t *rows;  /* optional host int32[n] row indices into X */
+} lingam_instance;
+
+lingam_status lingam_causal_order_batch(lingam_ctx *ctx, const lingam_instance *inst,
+                                        int32_t count, int32_t *const *orders_out,
+                                        double *const *B_out, int32_t *failed_index,
+                                        lingam_stream_t stream);
+
+/*
+ * Scores of the first ordering step only, for parity checks: I_out optional
+ * host double[d*d] with I(i, j) of Algorithm 1 at original indices (diagonal
+ * 0); M_out optional host double[d] with M(i).  Same data rules as
+ * lingam_causal_order.
+ */
+lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
+                                   int64_t ld, int32_t layout, double *I_out, double *M_out,
+                                   lingam_stream_t stream);
+
+/* Counters of the last lingam_causal_order / batch call on ctx. */
+typedef struct {
+    double total_ms;          /* device time of the whole call (events) */
+    double pair_ms;           /* summed pair-moment kernel time (profile=1) */
+    int64_t pair_launches;    /* pair-moment kernel launches timed */
+    double pair_units;        /* residual-samples those launches processed */
+    int32_t refined_steps;    /* steps re-scored in FP64 */
+    int32_t genuine_ties;     /* steps whose FP64 top-2 gap <= 1e-9 max|M| */
+    int32_t candidates_max;   /* largest candidate set re-scored */
+    int32_t graph_nodes;      /* kernel nodes in the step graph */
+    double graph_build_ms;    /* capture + instantiate time (0 if cached) */
+    int32_t reserved[6];
+} lingam_stats;
+
+lingam_status lingam_get_stats(const lingam_ctx *ctx, lingam_stats *out);
+
+/*
+ * Throughput probes of the units the entropy kernel is bound by, measured on
+ * the context's device: which = 0 FP32 FMA (flop/s, 2 per FMA), 1 MUFU ex2
+ * (op/s), 2 MUFU lg2 (op/s), 3 FP64 FMA (flop/s).  *ops_per_s receives the
+ * rate and *sm_clock_mhz the average SM clock seen by the probe (from
+ * clock64 over the globaltimer).
+ */
+lingam_status lingam_peak_probe(lingam_ctx *ctx, int32_t which, double *ops_per_s,
+                                double *sm_clock_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LINGAM_GB300_H */

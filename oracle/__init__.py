@@ -70,6 +70,7 @@ def _load():
         PD, PI32 = ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int32)
         lib.oracle_search_step.argtypes = [PD, I64, I64, PI32, I64, PD, I32, I32, PD, PD, PD,
                                            ctypes.POINTER(I32)]
+        lib.oracle_row_scores.argtypes = [PD, I64, I64, PI32, I64, PI32, I64, I32, PD]
         lib.oracle_causal_order.argtypes = [PD, I64, I64, I32, I32, PI32, PD, I64]
         lib.oracle_moments.argtypes = [PD, I64, PD, PD, PD, PD]
         lib.oracle_entropy.argtypes = [PD, I64, PD, PD]
@@ -182,6 +183,22 @@ def search_step(R, U=None, literal: bool = False, threads: int | None = None,
         int(threads or default_threads()), _pd(kl), _pd(I), _pd(Hz), ctypes.byref(mpos))
     _check(code, "search_step")
     return {"k_list": kl, "I": I, "Hz": Hz, "m_pos": mpos.value, "m": int(U[mpos.value])}
+
+
+def row_scores(R, rows, U=None, threads: int | None = None) -> np.ndarray:
+    """Algorithm 1's k for the positions ``rows`` of U only (literal loop)."""
+    R = np.asarray(R, dtype=np.float64)
+    n, d = R.shape
+    Rc = np.ascontiguousarray(R.T)
+    U = np.arange(d, dtype=np.int32) if U is None else np.ascontiguousarray(U, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty(rows.size)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    code = _load().oracle_row_scores(_pd(Rc), n, n, U.ctypes.data_as(P32), U.size,
+                                     rows.ctypes.data_as(P32), rows.size,
+                                     int(threads or default_threads()), _pd(out))
+    _check(code, "row_scores")
+    return out
 
 
 def causal_order(X, literal: bool = False, threads: int | None = None,

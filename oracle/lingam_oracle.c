@@ -365,6 +365,53 @@ int oracle_search_step(const double *R, int64_t n, int64_t ldr, const int32_t *U
     return status;
 }
 
+/*
+ * Algorithm 1's k_list restricted to the positions rows[0..nrows): for each
+ * such i, the literal inner loop over every j in U.  Same helper calls in the
+ * same order as the literal mode of oracle_search_step, so each value equals
+ * the corresponding k_list entry bitwise.  Used to check sampled rows of a
+ * step that is too large to score in full on the CPU.
+ */
+int oracle_row_scores(const double *R, int64_t n, int64_t ldr, const int32_t *U, int64_t p,
+                      const int32_t *rows, int64_t nrows, int nthreads, double *k_out)
+{
+    if (n < 2 || p < 2 || ldr < n || !U || !rows || !k_out) return ORACLE_ERR_ARG;
+    if (nthreads < 1) nthreads = 1;
+    int status = ORACLE_OK;
+#pragma omp parallel num_threads(nthreads)
+    {
+        double *buf = (double *)malloc(sizeof(double) * (size_t)n * 5);
+        int local = buf ? ORACLE_OK : ORACLE_ERR_NOMEM;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nrows; ++r) {
+            if (local) continue;
+            const int64_t a = rows[r];
+            if (a < 0 || a >= p) { local = ORACLE_ERR_ARG; continue; }
+            double k = 0.0;
+            for (int64_t b = 0; b < p; ++b) {
+                if (a == b || local) continue;
+                double *xi_std = buf, *xj_std = buf + n, *ri_j = buf + 2 * n,
+                       *rj_i = buf + 3 * n, *tmp = buf + 4 * n;
+                const double *xi = R + (int64_t)U[a] * ldr, *xj = R + (int64_t)U[b] * ldr;
+                double mi;
+                if ((local = oracle_standardize(xi, n, xi_std, tmp))) break;
+                if ((local = oracle_standardize(xj, n, xj_std, tmp))) break;
+                if ((local = oracle_residual(xi_std, xj_std, n, ri_j, tmp))) break;
+                if ((local = oracle_residual(xj_std, xi_std, n, rj_i, tmp))) break;
+                if ((local = oracle_diff_mutual_info(xi_std, xj_std, ri_j, rj_i, n, &mi, tmp)))
+                    break;
+                double v = fmin(0.0, mi);
+                k += v * v;
+            }
+            k_out[r] = -k;
+        }
+        free(buf);
+#pragma omp critical
+        if (local && !status) status = local;
+    }
+    return status;
+}
+
 /* ------------------------------------------------ DirectLiNGAM order ----- */
 
 /*

@@ -1,0 +1,305 @@
+"""GB300 (sm_103a) DirectLiNGAM causal ordering -- thin Python binding.
+
+Every function here only marshals arguments into the C ABI of
+``include/lingam.h`` (``liblingam_gb300.so``); all arithmetic runs in the
+library's CUDA kernels.  Importing this package never falls back to a CPU
+path: if the shared library is missing or no CUDA device is present, the
+calls raise.
+
+Data arguments may be numpy arrays (host memory) or torch tensors (host or
+CUDA).  A 2-D array of shape [n, d] (samples x variables, the paper's
+[m, dim]) is passed as row-major when C-contiguous and as column-major when
+its transpose is C-contiguous.  CUDA tensors are used in place on the
+current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "_lib", "liblingam_gb300.so")
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_DEGENERATE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT = range(7)
+PREC = {"fp32": 0, "mixed": 1, "fp64": 2}
+ROW_MAJOR, COL_MAJOR = 0, 1
+
+
+class LingamError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lingam status {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("tie_scale", ctypes.c_double), ("reserved", ctypes.c_int32 * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("total_ms", ctypes.c_double), ("pair_ms", ctypes.c_double),
+                ("pair_launches", ctypes.c_int64), ("pair_units", ctypes.c_double),
+                ("refined_steps", ctypes.c_int32), ("genuine_ties", ctypes.c_int32),
+                ("candidates_max", ctypes.c_int32), ("graph_nodes", ctypes.c_int32),
+                ("graph_build_ms", ctypes.c_double), ("reserved", ctypes.c_int32 * 6)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n_src", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("rows", ctypes.POINTER(ctypes.c_int32))]
+
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol declared in include/lingam.h
+_P, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+SIGNATURES = {
+    "lingam_create": (_I32, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(Opts)]),
+    "lingam_destroy": (_I32, [_P]),
+    "lingam_last_error": (ctypes.c_char_p, [_P]),
+    "lingam_set_precision": (_I32, [_P, _I32]),
+    "lingam_causal_order": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _P]),
+    "lingam_fit_adjacency": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _I32, _P]),
+    "varlingam_fit": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _I32, _P, _P, _P, _P]),
+    "lingam_causal_order_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _P, _P, _P]),
+    "lingam_step_measures": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _P]),
+    "lingam_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
+    "lingam_peak_probe": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+}
+
+
+def load(path: str = LIBPATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except Exception:      # torch is optional for host-only use
+        return None
+
+
+def _stream_of(arrs):
+    torch = _torch()
+    if torch is not None:
+        for a in arrs:
+            if isinstance(a, torch.Tensor) and a.is_cuda:
+                return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _matrix(X, dtype):
+    """(pointer, n, d, ld, layout, keepalive) of a 2-D array without copying
+    device data; host data is converted to ``dtype`` contiguous if needed."""
+    torch = _torch()
+    if torch is not None and isinstance(X, torch.Tensor):
+        tdt = torch.float64 if dtype == np.float64 else torch.float32
+        if X.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {X.dtype}")
+        if X.dim() != 2:
+            raise ValueError("X must be 2-D [n, d]")
+        n, d = X.shape
+        if X.stride(1) == 1 and X.stride(0) >= d:
+            return ctypes.c_void_p(X.data_ptr()), n, d, X.stride(0), ROW_MAJOR, X
+        if X.stride(0) == 1 and X.stride(1) >= n:
+            return ctypes.c_void_p(X.data_ptr()), n, d, X.stride(1), COL_MAJOR, X
+        X = X.contiguous()
+        return ctypes.c_void_p(X.data_ptr()), n, d, d, ROW_MAJOR, X
+    A = np.asarray(X)
+    if A.ndim != 2:
+        raise ValueError("X must be 2-D [n, d]")
+    if A.dtype != dtype:
+        A = A.astype(dtype)
+    n, d = A.shape
+    if A.flags.c_contiguous:
+        return ctypes.c_void_p(A.ctypes.data), n, d, d, ROW_MAJOR, A
+    if A.flags.f_contiguous:
+        return ctypes.c_void_p(A.ctypes.data), n, d, n, COL_MAJOR, A
+    A = np.ascontiguousarray(A)
+    return ctypes.c_void_p(A.ctypes.data), n, d, d, ROW_MAJOR, A
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """A library context on one CUDA device (owns workspace and graphs)."""
+
+    def __init__(self, device: int = 0, precision: str = "fp32", profile: bool = False,
+                 tie_scale: float = 0.0):
+        lib = load()
+        opts = Opts(PREC[precision], int(bool(profile)), float(tie_scale))
+        h = ctypes.c_void_p()
+        code = lib.lingam_create(ctypes.byref(h), int(device), ctypes.byref(opts))
+        if code != OK:
+            raise LingamError(code, lib.lingam_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        self.precision = precision
+
+    # -- plumbing --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lingam_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, code: int):
+        if code != OK:
+            raise LingamError(code, self._lib.lingam_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_precision(self, precision: str):
+        self._check(self._lib.lingam_set_precision(self._h, PREC[precision]))
+        self.precision = precision
+
+    def _dtype(self):
+        return np.float64 if self.precision == "fp64" else np.float32
+
+    # -- the ABI ----------------------------------------------------------------
+    def causal_order(self, X, scores: bool = False):
+        p, n, d, ld, lay, keep = _matrix(X, self._dtype())
+        order = np.empty(d, dtype=np.int32)
+        sc = np.empty((d, d)) if scores else None
+        code = self._lib.lingam_causal_order(self._h, p, n, d, ld, lay, _ptr(order),
+                                             _ptr(sc) if sc is not None else None,
+                                             _stream_of([keep]))
+        self._check(code)
+        return (order, sc) if scores else order
+
+    def step_measures(self, X):
+        """(I [d, d], M [d]) of the first ordering step."""
+        p, n, d, ld, lay, keep = _matrix(X, self._dtype())
+        I = np.empty((d, d))
+        M = np.empty(d)
+        self._check(self._lib.lingam_step_measures(self._h, p, n, d, ld, lay, _ptr(I), _ptr(M),
+                                                   _stream_of([keep])))
+        return I, M
+
+    def fit_adjacency(self, X, order, out=None):
+        p, n, d, ld, lay, keep = _matrix(X, np.float32)
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        torch = _torch()
+        if out is not None and torch is not None and isinstance(out, torch.Tensor) and out.is_cuda:
+            self._check(self._lib.lingam_fit_adjacency(self._h, p, n, d, ld, lay, _ptr(order),
+                                                       ctypes.c_void_p(out.data_ptr()), 1,
+                                                       _stream_of([keep, out])))
+            return out
+        B = np.empty((d, d))
+        self._check(self._lib.lingam_fit_adjacency(self._h, p, n, d, ld, lay, _ptr(order),
+                                                   _ptr(B), 0, _stream_of([keep])))
+        return B
+
+    def varlingam_fit(self, Xt, lags: int = 1):
+        """(order, B0, Btau[lags, d, d]) of VarLiNGAM on the series Xt [T, d]."""
+        p, T, d, ld, lay, keep = _matrix(Xt, np.float32)
+        order = np.empty(d, dtype=np.int32)
+        B0 = np.empty((d, d))
+        Bt = np.empty((lags, d, d))
+        self._check(self._lib.varlingam_fit(self._h, p, T, d, ld, lay, int(lags), _ptr(order),
+                                            _ptr(B0), _ptr(Bt), _stream_of([keep])))
+        return order, B0, Bt
+
+    def causal_order_batch(self, instances, adjacency: bool = False):
+        """instances: list of (X [n_src, d] float32, rows int32[n] or None).
+        Returns the list of orders (and adjacency matrices when asked)."""
+        keep = []
+        arr = (Instance * len(instances))()
+        orders = []
+        Bs = []
+        for k, (X, rows) in enumerate(instances):
+            p, n_src, d, ld, lay, kx = _matrix(X, np.float32)
+            if lay != ROW_MAJOR:
+                raise ValueError("batch instances must be row-major")
+            keep.append(kx)
+            if rows is not None:
+                r = np.ascontiguousarray(rows, dtype=np.int32)
+                keep.append(r)
+                arr[k] = Instance(p, n_src, r.size, d, ld,
+                                  r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+            else:
+                arr[k] = Instance(p, n_src, n_src, d, ld, None)
+            orders.append(np.empty(d, dtype=np.int32))
+            Bs.append(np.empty((d, d)) if adjacency else None)
+        optr = (ctypes.c_void_p * len(instances))(*[o.ctypes.data for o in orders])
+        bptr = (ctypes.c_void_p * len(instances))(*[b.ctypes.data for b in Bs]) if adjacency else None
+        failed = ctypes.c_int32(-1)
+        code = self._lib.lingam_causal_order_batch(self._h, arr, len(instances), optr, bptr,
+                                                   ctypes.byref(failed), _stream_of(keep))
+        self._check(code)
+        return (orders, Bs) if adjacency else orders
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.lingam_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_ if k != "reserved"}
+
+    def peak_probe(self, which: int):
+        """(ops per second, SM MHz) of unit `which`: 0 FP32 FMA flop/s,
+        1 MUFU ex2, 2 MUFU lg2, 3 FP64 FMA flop/s."""
+        r, mhz = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lingam_peak_probe(self._h, int(which), ctypes.byref(r),
+                                                ctypes.byref(mhz)))
+        return r.value, mhz.value
+
+
+# Module-level names mirroring the C ABI (same names, same argument order
+# after the context).
+def lingam_create(device: int = 0, precision: str = "fp32", profile: bool = False) -> Context:
+    return Context(device, precision, profile)
+
+
+def lingam_destroy(ctx: Context):
+    ctx.close()
+
+
+def lingam_causal_order(ctx: Context, X, scores: bool = False):
+    return ctx.causal_order(X, scores)
+
+
+def lingam_fit_adjacency(ctx: Context, X, order):
+    return ctx.fit_adjacency(X, order)
+
+
+def varlingam_fit(ctx: Context, Xt, lags: int = 1):
+    return ctx.varlingam_fit(Xt, lags)
+
+
+def lingam_causal_order_batch(ctx: Context, instances, adjacency: bool = False):
+    return ctx.causal_order_batch(instances, adjacency)
+
+
+def lingam_step_measures(ctx: Context, X):
+    return ctx.step_measures(X)

@@ -1,0 +1,170 @@
+// common.cuh -- device helpers shared by the sm_103a kernels of the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lg {
+
+// ---------------------------------------------------------------- status ---
+// Bits of the device status word (mapped to lingam_status by the host).
+enum : uint32_t {
+    ST_NONFINITE = 1u,
+    ST_DEGENERATE = 2u,
+    ST_TIMEOUT = 4u,
+    ST_ARG = 8u,
+};
+
+// Maximum candidates re-scored in FP64 at one step.
+constexpr int MAXC = 64;
+
+// Device-resident state of one ordering run.
+struct DevState {
+    uint32_t status;
+    int32_t m_pos;          // position (in U) chosen at the current step
+    int32_t ncand;          // candidates selected for FP64 re-scoring
+    int32_t refined_steps;
+    int32_t genuine_ties;
+    int32_t cand_max;
+    int32_t cand_overflow;
+    int32_t pad;
+    int32_t cand[MAXC];     // candidate positions, ascending
+};
+
+// ------------------------------------------------ entropy approximation ----
+// Maximum-entropy approximation of differential entropy (Hyvarinen 1998), the
+// measure behind the pairwise likelihood ratio of Hyvarinen & Smith (2013)
+// cited in Sec. 1:  H(u) = H(nu) - K1 (E log cosh u - GAMMA)^2
+//                               - K2 (E u exp(-u^2/2))^2.
+// H(nu) cancels in I(i, j), so only h = H - H(nu) is formed.
+constexpr double K1 = 79.047;
+constexpr double K2 = 7.4129;
+constexpr double GAMMA = 0.37457;
+constexpr double LN2_D = 0.69314718055994530942;
+constexpr double LOG2E_D = 1.44269504088896340736;
+
+__host__ __device__ inline double neg_entropy_part(double m1, double m2)
+{
+    double a = m1 - GAMMA;
+    return -K1 * a * a - K2 * m2 * m2;
+}
+
+// --------------------------------------------------------------- helpers ---
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t bit)
+{
+    atomicOr(status, bit);
+}
+
+// ------------------------------------------------------------- mbarrier ---
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.  Returns
+// false after ~2^22 polls with back-off (well over a second), so a kernel
+// never spins forever; the caller then records ST_TIMEOUT and winds down.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 64) __nanosleep(256);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ TMA ----
+// 2-D tiled bulk tensor load global -> shared, completion counted on `bar`.
+// x is the innermost coordinate (elements); it must be a multiple of 16 bytes
+// worth of elements -- callers pass multiples of the chunk length.
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int32_t x,
+                                            int32_t y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ------------------------------------------------------ hardware approx ----
+// MUFU approximations exposed by PTX (flush-to-zero forms).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Error-free sum (Knuth TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// ------------------------------------------------------------ reductions ---
+__device__ __forceinline__ double warp_sum_xor(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace lg

@@ -1,0 +1,136 @@
+// kernels.cuh -- launch interface between the host orchestration and kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace lg {
+
+// Tile shape of the FP32 pair-moment kernel: a warp owns a WI x WJ block of
+// ordered pairs (i, j) and its 32 lanes split the samples; WGI x WGJ consumer
+// warps form the CTA tile TI x TJ; one extra warp issues the TMA loads.
+constexpr int PAIR_WI = 4, PAIR_WJ = 4, PAIR_WGI = 2, PAIR_WGJ = 4;
+constexpr int PAIR_TI = PAIR_WI * PAIR_WGI;  // 8 rows  (variables i)
+constexpr int PAIR_TJ = PAIR_WJ * PAIR_WGJ;  // 16 cols (variables j)
+constexpr int PAIR_S = 256;                  // samples per TMA chunk
+constexpr int PAIR_STAGES = 4;
+constexpr int PAIR_VEC = 2;
+constexpr int PAIR_THREADS = 32 * (PAIR_WGI * PAIR_WGJ + 1);
+
+// Scale folded into the fast-form residual: u~ = KSC * u makes
+// 2^(-u~^2) = exp(-u^2/2).
+constexpr double KSC = 0.84932180028801904272;   // sqrt(log2(e) / 2)
+
+enum PairMode { PAIR_ACCURATE = 0, PAIR_FAST = 1 };
+
+struct PairParams {
+    const double *C;      // FP64 covariance of the residual data, [d][ldc]
+    int64_t ldc;
+    const int32_t *U;     // position -> original variable, p entries
+    int p, n;
+    int tiles_i, tiles_j;
+    int nchunks;          // ceil(n / PAIR_S)
+    int cps;              // chunks per sample split
+    int nsplit;
+    double *mom;          // out [nsplit][p][p][2] moment sums of entry (i, j)
+    uint32_t *status;
+};
+
+struct F64Params {
+    const double *R;      // FP64 residual data [d][ldr] by original index
+    int64_t ldr;
+    const double *C;
+    int64_t ldc;
+    const int32_t *U;
+    int p, n;
+    int mode;             // 0: all pairs + variables; 1: FP64 re-score of candidates
+    const DevState *state;
+    double *mom;          // mode 0: [p][p][2]; mode 1: [MAXC][p][4]
+    double *hz;           // [p][2] variable moment sums
+    uint32_t *status;
+};
+
+struct ScoreParams {
+    const double *mom;    // [nsplit][p][p][2]
+    int nsplit, p, n;
+    const double *hz;     // [nsplit_hz][p][2]
+    int nsplit_hz;
+    double a1, b1, a2;    // entry moments: m1 = a1 S1/n + b1, m2 = a2 S2/n
+    double ha1, hb1, ha2; // variable moments, same form
+    double epsI;          // bound on |I_fp32 - I_exact| (0 when exact)
+    const int32_t *U;
+    double *M;            // out [p]
+    double *E;            // out [p] error bound of M
+    double *hist;         // optional [d][d] score history (row already offset)
+    double *Iout;         // optional [p][p] I(i, j) by position (step-measure calls)
+};
+
+struct SelectParams {
+    const double *M, *E;
+    const int32_t *U;
+    int p;
+    DevState *state;
+};
+
+struct RefineSelectParams {
+    const double *mom;    // [MAXC][p][4]
+    const double *hz;     // [p][2]
+    int p, n;
+    const int32_t *U;
+    DevState *state;
+    double *hist;         // optional row of the score history
+};
+
+struct RegressParams {
+    double *R;            // FP64 residual data [d][ldr], updated in place
+    int64_t ldr;
+    float *z;             // FP32 standardised residuals [d][ldz], compacted by position
+    int64_t ldz;
+    const double *C;
+    int64_t ldc;
+    const int32_t *U;     // current positions
+    int32_t *Unext;       // next positions (compacted)
+    int p, n;
+    int sps;              // samples per split
+    DevState *state;
+    int32_t *order;       // order[t] = chosen variable
+    int t;
+    double *hzpart;       // out [nsplit][p'][2] variable moment sums of z
+    const double *ref_var;
+    double *lcoef;        // optional [d][d]: lcoef[i*d + m] = regression coefficient (L of LDL^T)
+    int64_t ldl;
+    uint32_t *status;
+};
+
+// ---- launchers (return the launch error) ----
+cudaError_t launch_pack(const void *X, int is_f64, int layout, int64_t ld, int n, int d,
+                        double *R, int64_t ldr, uint32_t *status, cudaStream_t s);
+cudaError_t launch_center(double *R, int64_t ldr, int n, int d, cudaStream_t s);
+cudaError_t launch_gram_f64(const double *R, int64_t ldr, int n, int d, double *Cpart,
+                            int ksplit, double *C, int64_t ldc, double *ref_var,
+                            cudaStream_t s);
+int gram_ksplit(int n, int d, int num_sms);
+cudaError_t launch_iota(int32_t *U, int d, DevState *state, cudaStream_t s);
+cudaError_t launch_regress(const RegressParams &P, bool init, int nsplit, cudaStream_t s);
+cudaError_t launch_downdate(double *C, int64_t ldc, const int32_t *U, int p,
+                            const DevState *state, cudaStream_t s);
+cudaError_t launch_finish(const int32_t *U, int32_t *order, int d, double *hist_row,
+                          cudaStream_t s);
+
+cudaError_t pair_kernel_setup();
+cudaError_t launch_pair(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
+                        const PairParams &P, cudaStream_t s);
+cudaError_t launch_pairs_f64(const F64Params &P, int grid, cudaStream_t s);
+cudaError_t launch_score(const ScoreParams &P, cudaStream_t s);
+cudaError_t launch_select(const SelectParams &P, cudaStream_t s);
+cudaError_t launch_refine_select(const RefineSelectParams &P, cudaStream_t s);
+
+// Adjacency / VAR helpers
+cudaError_t launch_ldl_step(double *C, int64_t ldc, const int32_t *pivots, int t, int d,
+                            double *L, int64_t ldl, cudaStream_t s);
+cudaError_t launch_unit_lower_inverse(const double *L, int64_t ldl, const int32_t *perm, int d,
+                                      double *W, int64_t ldw, cudaStream_t s);
+
+cudaError_t launch_peak_probe(int which, int blocks, int iters, unsigned long long *cycles,
+                              unsigned long long *ns, float *sink, cudaStream_t s);
+
+}  // namespace lg

@@ -1,0 +1,460 @@
+// kernels_prep.cu -- streaming kernels around the pair-moment kernel:
+// pack/centre, FP64 covariance (Gram), standardise + variable moments,
+// regress-out with rank-1 covariance downdate, and the LDL^T / triangular
+// inverse used by the adjacency estimate.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace lg {
+
+// ------------------------------------------------------------------ pack ---
+// X ([n][d] row-major or [d][n] column-major, FP32 or FP64) -> R [d][ldr]
+// FP64, one column per variable; non-finite values raise ST_NONFINITE.
+template <typename T>
+__global__ void k_pack_rowmajor(const T *__restrict__ X, int64_t ld, int n, int d,
+                                double *__restrict__ R, int64_t ldr, uint32_t *status)
+{
+    __shared__ double tile[32][33];
+    const int s0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    bool bad = false;
+    for (int k = ty; k < 32; k += 8) {
+        const int s = s0 + k, v = v0 + tx;
+        double x = 0.0;
+        if (s < n && v < d) {
+            x = (double)X[(int64_t)s * ld + v];
+            bad |= !isfinite(x);
+        }
+        tile[k][tx] = x;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int v = v0 + k, s = s0 + tx;
+        if (s < n && v < d) R[(int64_t)v * ldr + s] = tile[tx][k];
+    }
+    if (bad) set_status(status, ST_NONFINITE);
+}
+
+template <typename T>
+__global__ void k_pack_colmajor(const T *__restrict__ X, int64_t ld, int n, int d,
+                                double *__restrict__ R, int64_t ldr, uint32_t *status)
+{
+    const int v = blockIdx.y;
+    bool bad = false;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const double x = (double)X[(int64_t)v * ld + s];
+        bad |= !isfinite(x);
+        R[(int64_t)v * ldr + s] = x;
+    }
+    if (bad) set_status(status, ST_NONFINITE);
+}
+
+cudaError_t launch_pack(const void *X, int is_f64, int layout, int64_t ld, int n, int d,
+                        double *R, int64_t ldr, uint32_t *status, cudaStream_t s)
+{
+    if (layout == 0) {
+        dim3 grid((n + 31) / 32, (d + 31) / 32), block(32, 8);
+        if (is_f64)
+            k_pack_rowmajor<double><<<grid, block, 0, s>>>((const double *)X, ld, n, d, R, ldr, status);
+        else
+            k_pack_rowmajor<float><<<grid, block, 0, s>>>((const float *)X, ld, n, d, R, ldr, status);
+    } else {
+        dim3 grid(min((n + 255) / 256, 64), d);
+        if (is_f64)
+            k_pack_colmajor<double><<<grid, 256, 0, s>>>((const double *)X, ld, n, d, R, ldr, status);
+        else
+            k_pack_colmajor<float><<<grid, 256, 0, s>>>((const float *)X, ld, n, d, R, ldr, status);
+    }
+    return cudaGetLastError();
+}
+
+// Block-wide FP64 sum with a fixed reduction tree (deterministic).
+__device__ double block_sum(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum_xor(v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) t = warp_sum_xor(t);
+    __syncthreads();
+    return t;   // valid in warp 0
+}
+
+// Subtract each column's mean (one block per variable).
+__global__ void __launch_bounds__(256) k_center(double *R, int64_t ldr, int n)
+{
+    __shared__ double sh[32];
+    __shared__ double mean;
+    double *r = R + (int64_t)blockIdx.x * ldr;
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) acc += r[s];
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) mean = tot / (double)n;
+    __syncthreads();
+    const double mu = mean;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) r[s] -= mu;
+}
+
+cudaError_t launch_center(double *R, int64_t ldr, int n, int d, cudaStream_t s)
+{
+    k_center<<<d, 256, 0, s>>>(R, ldr, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Gram ---
+// C = R R^T / n over the d variables (FP64 SIMT).  A CTA computes one 64 x 64
+// tile of the upper triangle (tile row <= tile column) over one slice of the
+// samples; k_gram_reduce sums the slices in order, mirrors and scales, so C
+// is exactly symmetric.
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_gram_f64(const double *__restrict__ R, int64_t ldr,
+                                                  int n, int d, int ksplit,
+                                                  double *__restrict__ Cpart)
+{
+    __shared__ double As[GK][GT + 1];
+    __shared__ double Bs[GK][GT + 1];
+    // upper-triangular tile index -> (bi, bj)
+    const int nt = (d + GT - 1) / GT;
+    int t = blockIdx.x, bi = 0;
+    while (t >= nt - bi) {
+        t -= nt - bi;
+        ++bi;
+    }
+    const int bj = bi + t;
+    const int slice = (n + ksplit - 1) / ksplit;
+    const int k0 = blockIdx.y * slice, k1 = min(n, k0 + slice);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    const int lv = threadIdx.x >> 2;            // 0..63 variable within tile
+    const int lk = (threadIdx.x & 3) * 4;       // 0,4,8,12 sample within chunk
+    for (int kc = k0; kc < k1; kc += GK) {
+        const int va = bi * GT + lv, vb = bj * GT + lv;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = kc + lk + q;
+            As[lk + q][lv] = (va < d && k < k1) ? R[(int64_t)va * ldr + k] : 0.0;
+            Bs[lk + q][lv] = (vb < d && k < k1) ? R[(int64_t)vb * ldr + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[k][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[k][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double *out = Cpart + (size_t)blockIdx.y * d * d;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = bi * GT + ty + 16 * r, j = bj * GT + tx + 16 * c;
+            if (i < d && j < d) out[(size_t)i * d + j] = acc[r][c];
+        }
+}
+
+__global__ void k_gram_reduce(const double *__restrict__ Cpart, int ksplit, int n, int d,
+                              double *__restrict__ C, int64_t ldc, double *ref_var)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= d) return;
+    // read the entry from the upper-triangular tile that computed it
+    int a = i, b = j;
+    if (i / GT > j / GT || (i / GT == j / GT && i > j)) {
+        a = j;
+        b = i;
+    }
+    double s = 0.0;
+    for (int z = 0; z < ksplit; ++z) s += Cpart[(size_t)z * d * d + (size_t)a * d + b];
+    const double v = s / (double)n;
+    C[(int64_t)i * ldc + j] = v;
+    if (i == j && ref_var) ref_var[i] = v;
+}
+
+int gram_ksplit(int n, int d, int num_sms)
+{
+    const int nt = (d + GT - 1) / GT;
+    const int tiles = nt * (nt + 1) / 2;
+    int ks = (2 * num_sms + tiles - 1) / tiles;
+    ks = max(1, min(ks, n / 256));
+    return max(1, min(ks, 64));
+}
+
+cudaError_t launch_gram_f64(const double *R, int64_t ldr, int n, int d, double *Cpart, int ksplit,
+                            double *C, int64_t ldc, double *ref_var, cudaStream_t s)
+{
+    const int nt = (d + GT - 1) / GT;
+    dim3 grid(nt * (nt + 1) / 2, ksplit);
+    k_gram_f64<<<grid, 256, 0, s>>>(R, ldr, n, d, ksplit, Cpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g2((d + 127) / 128, d);
+    k_gram_reduce<<<g2, 128, 0, s>>>(Cpart, ksplit, n, d, C, ldc, ref_var);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- state ---
+__global__ void k_iota(int32_t *U, int d, DevState *state)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) U[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // status is cleared by the host before pack
+        state->m_pos = 0;
+        state->ncand = 0;
+        state->refined_steps = 0;
+        state->genuine_ties = 0;
+        state->cand_max = 0;
+        state->cand_overflow = 0;
+    }
+}
+
+cudaError_t launch_iota(int32_t *U, int d, DevState *state, cudaStream_t s)
+{
+    k_iota<<<(d + 255) / 256, 256, 0, s>>>(U, d, state);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------- regress-out + stats ---
+// Sec. 2.2: the chosen variable m is regressed out of every other remaining
+// variable by least squares, R_i <- R_i - (C_im / C_mm) R_m (FP64).  Fused in
+// the same pass: the new column is standardised with its downdated variance
+// C_ii - C_im^2 / C_mm, written as FP32 to its compacted position for the
+// next pair-moment kernel, and its own entropy moments are accumulated
+// (accurate FP32 functions, FP64 block sums).  INIT=true only standardises
+// (first step, no regression).
+template <bool INIT>
+__global__ void __launch_bounds__(256) k_regress(const RegressParams P)
+{
+    __shared__ double sh[32];
+    const int col = blockIdx.x;
+    int pos = col, m = -1, mpos = -1;
+    double coef = 0.0, var;
+    if (!INIT) {
+        mpos = P.state->m_pos;
+        m = P.U[mpos];
+        pos = col + (col >= mpos ? 1 : 0);
+    }
+    const int i = P.U[pos];
+    const double cii = P.C[(int64_t)i * P.ldc + i];
+    if (INIT) {
+        var = cii;
+    } else {
+        const double cmm = P.C[(int64_t)m * P.ldc + m];
+        const double cim = P.C[(int64_t)i * P.ldc + m];
+        coef = cim / cmm;
+        var = cii - (cim * cim) / cmm;
+    }
+    if (!(var > 1e-12 * P.ref_var[i])) {
+        if (threadIdx.x == 0) set_status(P.status, ST_DEGENERATE);
+        var = 1.0;
+    }
+    const double isd = 1.0 / sqrt(var);
+    double *ri = P.R + (int64_t)i * P.ldr;
+    const double *rm = INIT ? nullptr : P.R + (int64_t)m * P.ldr;
+    float *zo = P.z + (int64_t)col * P.ldz;
+    const int s0 = blockIdx.y * P.sps, s1 = min(P.n, s0 + P.sps);
+    float a1 = 0.0f, a2 = 0.0f;
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        double r = ri[s];
+        if (!INIT) {
+            r = r - coef * rm[s];
+            ri[s] = r;
+        }
+        const float z = (float)(r * isd);
+        zo[s] = z;
+        const float az = fabsf(z);
+        a1 += az + log1pf(expf(-2.0f * az));
+        a2 += z * expf(-0.5f * z * z);
+    }
+    const double t1 = block_sum((double)a1, sh);
+    const double t2 = block_sum((double)a2, sh);
+    if (threadIdx.x == 0) {
+        const int np = INIT ? P.p : P.p - 1;
+        double *o = P.hzpart + ((size_t)blockIdx.y * np + col) * 2;
+        o[0] = t1;
+        o[1] = t2;
+        if (!INIT && blockIdx.y == 0) {
+            P.Unext[col] = i;
+            if (P.lcoef) P.lcoef[(int64_t)i * P.ldl + m] = coef;
+            if (col == 0) P.order[P.t] = m;
+        }
+    }
+}
+
+cudaError_t launch_regress(const RegressParams &P, bool init, int nsplit, cudaStream_t s)
+{
+    dim3 grid(init ? P.p : P.p - 1, nsplit);
+    if (init)
+        k_regress<true><<<grid, 256, 0, s>>>(P);
+    else
+        k_regress<false><<<grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+// Rank-1 downdate of the covariance of the remaining variables (FP64):
+// C_ij <- C_ij - C_im C_jm / C_mm, written symmetric-exact.
+__global__ void k_downdate(double *C, int64_t ldc, const int32_t *U, int p, const DevState *state)
+{
+    const int mpos = state->m_pos;
+    const int m = U[mpos];
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p - 1 || c >= p - 1) return;
+    const int i = U[r + (r >= mpos ? 1 : 0)];
+    const int j = U[c + (c >= mpos ? 1 : 0)];
+    const double cmm = C[(int64_t)m * ldc + m];
+    const double cim = C[(int64_t)i * ldc + m], cjm = C[(int64_t)j * ldc + m];
+    C[(int64_t)i * ldc + j] -= (cim * cjm) / cmm;
+}
+
+cudaError_t launch_downdate(double *C, int64_t ldc, const int32_t *U, int p, const DevState *state,
+                            cudaStream_t s)
+{
+    dim3 block(32, 8), grid((p - 1 + 31) / 32, (p - 1 + 7) / 8);
+    k_downdate<<<grid, block, 0, s>>>(C, ldc, U, p, state);
+    return cudaGetLastError();
+}
+
+__global__ void k_finish(const int32_t *U, int32_t *order, int d, double *hist_row)
+{
+    order[d - 1] = U[0];
+    if (hist_row) hist_row[U[0]] = 0.0;
+}
+
+cudaError_t launch_finish(const int32_t *U, int32_t *order, int d, double *hist_row, cudaStream_t s)
+{
+    k_finish<<<1, 1, 0, s>>>(U, order, d, hist_row);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------- adjacency (LDL) -
+// One elimination step of L D L^T in a caller-given pivot order (FP64):
+// pivot m = pivots[t]; L[i][m] = C_im / C_mm for the not-yet-eliminated i,
+// then the Schur complement C_ij -= C_im C_jm / C_mm.  Rows and columns of
+// eliminated variables are never read again.  The coefficient column is
+// written before the update by the same thread that reads C_im, and the
+// update of (i, j) only reads column m, which no thread writes.
+__global__ void k_ldl_step(double *C, int64_t ldc, const int32_t *pivots, int t, int d, double *L,
+                           int64_t ldl)
+{
+    const int m = pivots[t];
+    const int rem = d - t - 1;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rem || c >= rem) return;
+    const int i = pivots[t + 1 + r], j = pivots[t + 1 + c];
+    const double cmm = C[(int64_t)m * ldc + m];
+    const double cim = C[(int64_t)i * ldc + m], cjm = C[(int64_t)j * ldc + m];
+    if (c == 0) L[(int64_t)i * ldl + m] = cim / cmm;
+    C[(int64_t)i * ldc + j] -= (cim * cjm) / cmm;
+}
+
+cudaError_t launch_ldl_step(double *C, int64_t ldc, const int32_t *pivots, int t, int d, double *L,
+                            int64_t ldl, cudaStream_t s)
+{
+    const int rem = d - t - 1;
+    if (rem <= 0) return cudaSuccess;
+    dim3 block(32, 8), grid((rem + 31) / 32, (rem + 7) / 8);
+    k_ldl_step<<<grid, block, 0, s>>>(C, ldc, pivots, t, d, L, ldl);
+    return cudaGetLastError();
+}
+
+// W = I - L^{-1} in the permuted order, scattered to original indices:
+// Lp[k][q] = L[perm[k]][perm[q]] (unit lower triangular).  One block solves
+// column q of Lp^{-1} by forward substitution; each row's dot product is a
+// block reduction.  W[perm[k]][perm[q]] = -(Lp^{-1})[k][q] for k > q.
+__global__ void __launch_bounds__(256) k_unit_lower_inverse(const double *L, int64_t ldl,
+                                                           const int32_t *perm, int d, double *W,
+                                                           int64_t ldw)
+{
+    extern __shared__ double x[];   // x[k] for k >= q (column q of Lp^{-1})
+    __shared__ double sh[32];
+    const int q = blockIdx.x;
+    if (threadIdx.x == 0) x[0] = 1.0;
+    __syncthreads();
+    for (int k = q + 1; k < d; ++k) {
+        const int ok = perm[k];
+        double acc = 0.0;
+        for (int r = q + threadIdx.x; r < k; r += blockDim.x)
+            acc += L[(int64_t)ok * ldl + perm[r]] * x[r - q];
+        const double tot = block_sum(acc, sh);
+        if (threadIdx.x == 0) x[k - q] = -tot;
+        __syncthreads();
+    }
+    const int oq = perm[q];
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        const int ok = perm[k];
+        W[(int64_t)ok * ldw + oq] = (k > q) ? -x[k - q] : 0.0;
+    }
+}
+
+cudaError_t launch_unit_lower_inverse(const double *L, int64_t ldl, const int32_t *perm, int d,
+                                      double *W, int64_t ldw, cudaStream_t s)
+{
+    k_unit_lower_inverse<<<d, 256, sizeof(double) * d, s>>>(L, ldl, perm, d, W, ldw);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- peak probes ---
+// Dependent-chain-free loops that keep one functional unit busy; the host
+// divides the operation count by the elapsed device time.
+__global__ void __launch_bounds__(256) k_probe(int which, int iters, unsigned long long *cycles,
+                                               unsigned long long *ns, float *sink)
+{
+    unsigned long long c0 = clock64(), t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    float v[8];
+    double dv[8];
+    for (int k = 0; k < 8; ++k) {
+        v[k] = 1.0f + 1e-3f * (threadIdx.x + k);
+        dv[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    }
+    const float a = 0.999999f, b = 1e-7f;
+    if (which == 0) {
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = fmaf(v[k], a, b);
+    } else if (which == 1) {
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = ex2_approx(v[k]) * 1e-30f + 0.5f;
+    } else if (which == 2) {
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = lg2_approx(v[k]) + 1.5f;
+    } else {
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dv[k] = fma(dv[k], 0.999999, 1e-7);
+    }
+    float acc = 0.0f;
+    for (int k = 0; k < 8; ++k) acc += v[k] + (float)dv[k];
+    if (acc == 12345.678f) sink[0] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c1 = clock64(), t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        cycles[blockIdx.x] = c1 - c0;
+        ns[blockIdx.x] = t1 - t0;
+    }
+}
+
+cudaError_t launch_peak_probe(int which, int blocks, int iters, unsigned long long *cycles,
+                              unsigned long long *ns, float *sink, cudaStream_t s)
+{
+    k_probe<<<blocks, 256, 0, s>>>(which, iters, cycles, ns, sink);
+    return cudaGetLastError();
+}
+
+}  // namespace lg
