@@ -176,7 +176,8 @@ typedef struct {
     int32_t candidates_max;   /* largest candidate set re-scored */
     int32_t graph_nodes;      /* kernel nodes in the step graph */
     double graph_build_ms;    /* capture + instantiate time (0 if cached) */
-    int32_t reserved[6];
+    int32_t fp64_candidates;  /* candidates re-scored in FP64 over the run */
+    int32_t reserved[5];
 } lingam_stats;
 
 lingam_status lingam_get_stats(const lingam_ctx *ctx, lingam_stats *out);

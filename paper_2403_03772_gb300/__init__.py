@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
                 ("pair_launches", ctypes.c_int64), ("pair_units", ctypes.c_double),
                 ("refined_steps", ctypes.c_int32), ("genuine_ties", ctypes.c_int32),
                 ("candidates_max", ctypes.c_int32), ("graph_nodes", ctypes.c_int32),
-                ("graph_build_ms", ctypes.c_double), ("reserved", ctypes.c_int32 * 6)]
+                ("graph_build_ms", ctypes.c_double), ("fp64_candidates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class Instance(ctypes.Structure):

@@ -23,13 +23,19 @@ constexpr int MAXC = 64;
 struct DevState {
     uint32_t status;
     int32_t m_pos;          // position (in U) chosen at the current step
-    int32_t ncand;          // candidates selected for FP64 re-scoring
+    int32_t ncand;          // candidates for FP64 re-scoring (1 = decided in FP32)
     int32_t refined_steps;
     int32_t genuine_ties;
     int32_t cand_max;
     int32_t cand_overflow;
+    int32_t pass_begin;     // candidate index range of the current FP64 pass
+    int32_t pass_end;
+    int32_t resolved;       // 1 once the step's argmax is decided
+    int32_t fp64_candidates;  // candidates re-scored in FP64 over the run
     int32_t pad;
-    int32_t cand[MAXC];     // candidate positions, ascending
+    int32_t cand[MAXC];     // candidate positions, by upper bound M + E descending
+    double ub[MAXC];        // M + E of each candidate
+    double m64[MAXC];       // FP64 score of each re-scored candidate
 };
 
 // ------------------------------------------------ entropy approximation ----

@@ -43,6 +43,7 @@ struct F64Params {
     const int32_t *U;
     int p, n;
     int mode;             // 0: all pairs + variables; 1: FP64 re-score of candidates
+    int pass;             // mode 1: 1 = first pass (also variable moments), 2 = second
     const DevState *state;
     double *mom;          // mode 0: [p][p][2]; mode 1: [MAXC][p][4]
     double *hz;           // [p][2] variable moment sums
@@ -69,6 +70,7 @@ struct SelectParams {
     const int32_t *U;
     int p;
     DevState *state;
+    int32_t *scratch;     // [p] candidate list workspace
 };
 
 struct RefineSelectParams {
@@ -78,6 +80,7 @@ struct RefineSelectParams {
     const int32_t *U;
     DevState *state;
     double *hist;         // optional row of the score history
+    int pass;             // 1 or 2
 };
 
 struct RegressParams {
@@ -129,6 +132,14 @@ cudaError_t launch_ldl_step(double *C, int64_t ldc, const int32_t *pivots, int t
                             double *L, int64_t ldl, cudaStream_t s);
 cudaError_t launch_unit_lower_inverse(const double *L, int64_t ldl, const int32_t *perm, int d,
                                       double *W, int64_t ldw, cudaStream_t s);
+
+cudaError_t launch_regress_cols(double *R, int64_t ldr, const double *L, int64_t ldl, int t, int q,
+                                int n, int nsplit, cudaStream_t s);
+cudaError_t launch_var_coefficients(const double *L, int64_t ldl, int nz, int d, double *M,
+                                    cudaStream_t s);
+cudaError_t launch_var_transform(const double *B0, const double *M, int lags, int d, double *Bt,
+                                 cudaStream_t s);
+cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s);
 
 cudaError_t launch_peak_probe(int which, int blocks, int iters, unsigned long long *cycles,
                               unsigned long long *ns, float *sink, cudaStream_t s);

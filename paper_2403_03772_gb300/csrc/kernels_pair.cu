@@ -354,16 +354,20 @@ __global__ void __launch_bounds__(256) k_pairs_f64(const F64Params P)
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    int ncand = 0;
+    int cbeg = 0;
     int64_t npair_items;
+    bool with_vars = true;
     if (P.mode == 1) {
-        ncand = P.state->ncand;
-        if (ncand < 2) return;
-        npair_items = (int64_t)ncand * P.p;
+        if (P.state->resolved) return;
+        cbeg = P.state->pass_begin;
+        const int cend = P.state->pass_end;
+        if (cend <= cbeg) return;
+        npair_items = (int64_t)(cend - cbeg) * P.p;
+        with_vars = (P.pass == 1);
     } else {
         npair_items = (int64_t)P.p * (P.p - 1) / 2;
     }
-    const int64_t nitems = npair_items + P.p;
+    const int64_t nitems = npair_items + (with_vars ? P.p : 0);
 
     for (int64_t q = gw; q < nitems; q += nw) {
         if (q >= npair_items) {
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(256) k_pairs_f64(const F64Params P)
         }
         int a, b, cidx = 0;
         if (P.mode == 1) {
-            cidx = (int)(q / P.p);
+            cidx = cbeg + (int)(q / P.p);
             a = P.state->cand[cidx];
             b = (int)(q % P.p);
             if (a == b) {
@@ -403,6 +407,7 @@ __global__ void __launch_bounds__(256) k_pairs_f64(const F64Params P)
                                          sqrt((2.0 * pp - 1.0) * (2.0 * pp - 1.0) - 8.0 * (double)q)) /
                                         2.0);
             auto first = [&](int64_t x) { return x * (2 * (int64_t)P.p - x - 1) / 2; };
+            if (aa < 0) aa = 0;
             while (aa > 0 && first(aa) > q) --aa;
             while (first(aa + 1) <= q) ++aa;
             a = (int)aa;
@@ -537,8 +542,7 @@ __global__ void __launch_bounds__(1024) k_select(const SelectParams P)
 {
     __shared__ double sm[32];
     __shared__ int su[32], sp[32];
-    __shared__ int s_top;
-    __shared__ int s_cnt[1024];
+    __shared__ int s_top, s_cnt;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     double bm = -INFINITY;
     int bu = 0x7fffffff, bp = -1;
@@ -566,6 +570,7 @@ __global__ void __launch_bounds__(1024) k_select(const SelectParams P)
         su[w] = bu;
         sp[w] = bp;
     }
+    if (tid == 0) s_cnt = 0;
     __syncthreads();
     if (tid == 0) {
         int best = -1;
@@ -576,70 +581,48 @@ __global__ void __launch_bounds__(1024) k_select(const SelectParams P)
     __syncthreads();
     const int top = s_top;
     const double thr = P.M[top] - P.E[top];
-    // contiguous position ranges per thread keep candidates in ascending order
-    const int per = (P.p + blockDim.x - 1) / blockDim.x;
-    const int q0 = tid * per, q1 = min(P.p, q0 + per);
-    int cnt = 0;
-    for (int q = q0; q < q1; ++q)
-        if (P.M[q] + P.E[q] >= thr) ++cnt;
-    s_cnt[tid] = cnt;
+    // unordered compaction of the candidates (their order is fixed below)
+    for (int q = tid; q < P.p; q += blockDim.x)
+        if (P.M[q] + P.E[q] >= thr) P.scratch[atomicAdd(&s_cnt, 1)] = q;
     __syncthreads();
-    if (tid == 0) {
-        int run = 0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            const int c = s_cnt[k];
-            s_cnt[k] = run;
-            run += c;
+    const int cnt = s_cnt;
+    DevState *st = P.state;
+    if (cnt <= 1) {
+        if (tid == 0) {
+            st->m_pos = top;
+            st->ncand = 1;
+            st->resolved = 1;
+            st->pass_begin = st->pass_end = 0;
         }
-        DevState *st = P.state;
-        st->m_pos = top;
-        st->ncand = run;
-        if (run > st->cand_max) st->cand_max = run;
-        if (run > MAXC) st->cand_overflow += 1;
+        return;
     }
-    __syncthreads();
-    int off = s_cnt[tid];
-    for (int q = q0; q < q1; ++q)
-        if (P.M[q] + P.E[q] >= thr) {
-            if (off < MAXC) P.state->cand[off] = q;
-            ++off;
+    // rank by upper bound M + E descending, ties to the smaller original index;
+    // keep the first MAXC
+    for (int k = tid; k < cnt; k += blockDim.x) {
+        const int q = P.scratch[k];
+        const double ub = P.M[q] + P.E[q];
+        const int u = P.U[q];
+        int rank = 0;
+        for (int k2 = 0; k2 < cnt; ++k2) {
+            const int q2 = P.scratch[k2];
+            const double ub2 = P.M[q2] + P.E[q2];
+            rank += (ub2 > ub) || (ub2 == ub && P.U[q2] < u);
         }
-    __syncthreads();
-    if (tid == 0 && P.state->ncand > MAXC) {
-        // keep the MAXC candidates with the highest upper bound M + E
-        // (rare; a plain selection by repeated scans)
-        int chosen = 0;
-        double last = INFINITY;
-        int lastq = -1;
-        while (chosen < MAXC) {
-            int bq = -1;
-            double bv = -INFINITY;
-            for (int q = 0; q < P.p; ++q) {
-                const double v = P.M[q] + P.E[q];
-                if (v < thr) continue;
-                const bool after_last = (v < last) || (v == last && q > lastq);
-                if (!after_last) continue;
-                if (bq < 0 || v > bv || (v == bv && q < bq)) {
-                    bv = v;
-                    bq = q;
-                }
-            }
-            if (bq < 0) break;
-            P.state->cand[chosen++] = bq;
-            last = bv;
-            lastq = bq;
+        if (rank < MAXC) {
+            st->cand[rank] = q;
+            st->ub[rank] = ub;
         }
-        // ascending position order
-        for (int a = 1; a < chosen; ++a) {
-            const int x = P.state->cand[a];
-            int b = a - 1;
-            while (b >= 0 && P.state->cand[b] > x) {
-                P.state->cand[b + 1] = P.state->cand[b];
-                --b;
-            }
-            P.state->cand[b + 1] = x;
-        }
-        P.state->ncand = chosen;
+    }
+    if (tid == 0) {
+        const int nc = min(cnt, MAXC);
+        st->m_pos = top;
+        st->ncand = nc;
+        st->resolved = 0;
+        st->pass_begin = 0;
+        st->pass_end = min(2, nc);
+        st->refined_steps += 1;
+        if (cnt > st->cand_max) st->cand_max = cnt;
+        if (cnt > MAXC) st->cand_overflow += 1;
     }
 }
 
@@ -649,20 +632,22 @@ cudaError_t launch_select(const SelectParams &P, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// FP64 re-score of the candidates and the final argmax among them.
+// FP64 re-score of a pass of candidates.  Pass 1 scores the two candidates
+// with the highest upper bounds; if the better of them beats every remaining
+// upper bound the step is decided, otherwise pass 2 scores the rest and the
+// argmax is taken over all FP64 scores (ties to the smallest original index).
 __global__ void __launch_bounds__(256) k_refine_select(const RefineSelectParams P)
 {
     extern __shared__ double h64[];
-    __shared__ double mc[MAXC];
     DevState *st = P.state;
-    const int ncand = st->ncand;
-    if (ncand < 2) return;
+    if (st->resolved) return;
+    const int cb = st->pass_begin, ce = st->pass_end, nc = st->ncand;
     const double invn = 1.0 / (double)P.n;
     for (int j = threadIdx.x; j < P.p; j += blockDim.x)
         h64[j] = neg_entropy_part(P.hz[(size_t)j * 2] * invn - LN2_D, P.hz[(size_t)j * 2 + 1] * invn);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = w; c < ncand; c += nw) {
+    for (int c = cb + w; c < ce; c += nw) {
         const int pc = st->cand[c];
         double acc = 0.0;
         for (int j = lane; j < P.p; j += 32) {
@@ -675,23 +660,28 @@ __global__ void __launch_bounds__(256) k_refine_select(const RefineSelectParams 
             acc += v * v;
         }
         acc = warp_sum_xor(acc);
-        if (lane == 0) mc[c] = -acc;
+        if (lane == 0) st->m64[c] = -acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int best = 0;
-        double mx = 0.0;
-        for (int c = 0; c < ncand; ++c) mx = fmax(mx, fabs(mc[c]));
-        for (int c = 1; c < ncand; ++c)
-            if (better(mc[c], P.U[st->cand[c]], mc[best], P.U[st->cand[best]])) best = c;
-        double gap = INFINITY;
-        for (int c = 0; c < ncand; ++c)
-            if (c != best) gap = fmin(gap, mc[best] - mc[c]);
+        for (int c = 1; c < ce; ++c)
+            if (better(st->m64[c], P.U[st->cand[c]], st->m64[best], P.U[st->cand[best]])) best = c;
+        st->fp64_candidates += ce - cb;
+        if (P.hist)
+            for (int c = cb; c < ce; ++c) P.hist[P.U[st->cand[c]]] = st->m64[c];
+        if (ce < nc && !(st->m64[best] > st->ub[ce])) {
+            st->pass_begin = ce;       // undecided: score the rest in pass 2
+            st->pass_end = nc;
+            return;
+        }
+        double mx = 0.0, gap = INFINITY;
+        for (int c = 0; c < ce; ++c) mx = fmax(mx, fabs(st->m64[c]));
+        for (int c = 0; c < ce; ++c)
+            if (c != best) gap = fmin(gap, st->m64[best] - st->m64[c]);
         if (gap <= 1e-9 * mx) st->genuine_ties += 1;
         st->m_pos = st->cand[best];
-        st->refined_steps += 1;
-        if (P.hist)
-            for (int c = 0; c < ncand; ++c) P.hist[P.U[st->cand[c]]] = mc[c];
+        st->resolved = 1;
     }
 }
 

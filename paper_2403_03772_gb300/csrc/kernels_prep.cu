@@ -406,6 +406,95 @@ cudaError_t launch_unit_lower_inverse(const double *L, int64_t ldl, const int32_
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------ VAR helpers --
+// Regress pivot column m = t (natural order) out of the data columns
+// t+1..q-1 with the coefficient the LDL step just stored: R_i -= L[i][m] R_m
+// (modified Gram-Schmidt on the design [Z | Y] of the VAR least squares).
+__global__ void __launch_bounds__(256) k_regress_cols(double *R, int64_t ldr, const double *L,
+                                                      int64_t ldl, int t, int n, int sps)
+{
+    const int i = t + 1 + blockIdx.x;
+    const double c = L[(int64_t)i * ldl + t];
+    double *ri = R + (int64_t)i * ldr;
+    const double *rm = R + (int64_t)t * ldr;
+    const int s0 = blockIdx.y * sps, s1 = min(n, s0 + sps);
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) ri[s] -= c * rm[s];
+}
+
+cudaError_t launch_regress_cols(double *R, int64_t ldr, const double *L, int64_t ldl, int t, int q,
+                                int n, int nsplit, cudaStream_t s)
+{
+    const int cols = q - t - 1;
+    if (cols <= 0) return cudaSuccess;
+    const int sps = (n + nsplit - 1) / nsplit;
+    dim3 grid(cols, (n + sps - 1) / sps);
+    k_regress_cols<<<grid, 256, 0, s>>>(R, ldr, L, ldl, t, n, sps);
+    return cudaGetLastError();
+}
+
+// VAR coefficients from the elimination of the nz regressor pivots:
+// for response y (column nz + y), the coefficients beta on the original
+// regressors solve Lzz^T beta = ly, ly[t] = L[nz + y][t] (unit upper
+// triangular back substitution).  M[tau][y][j] = beta[(tau-1) d + j].
+__global__ void __launch_bounds__(256) k_var_coefficients(const double *L, int64_t ldl, int nz,
+                                                          int d, double *M)
+{
+    extern __shared__ double beta[];
+    __shared__ double sh[32];
+    const int y = blockIdx.x;
+    const int64_t row = (int64_t)(nz + y) * ldl;
+    for (int t = nz - 1; t >= 0; --t) {
+        double acc = 0.0;
+        for (int u = t + 1 + threadIdx.x; u < nz; u += blockDim.x)
+            acc += L[(int64_t)u * ldl + t] * beta[u];
+        const double tot = block_sum(acc, sh);
+        if (threadIdx.x == 0) beta[t] = L[row + t] - tot;
+        __syncthreads();
+    }
+    for (int u = threadIdx.x; u < nz; u += blockDim.x) {
+        const int tau = u / d, j = u % d;
+        M[((int64_t)tau * d + y) * d + j] = beta[u];
+    }
+}
+
+cudaError_t launch_var_coefficients(const double *L, int64_t ldl, int nz, int d, double *M,
+                                    cudaStream_t s)
+{
+    k_var_coefficients<<<d, 256, sizeof(double) * nz, s>>>(L, ldl, nz, d, M);
+    return cudaGetLastError();
+}
+
+// B_tau = (I - B0) M_tau for every lag (FP64): Bt[i][j] = M[i][j] - sum_k B0[i][k] M[k][j].
+__global__ void k_var_transform(const double *B0, const double *M, int lags, int d, double *Bt)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y, tau = blockIdx.z;
+    if (j >= d) return;
+    const double *Mt = M + (int64_t)tau * d * d;
+    double acc = Mt[(int64_t)i * d + j];
+    for (int k = 0; k < d; ++k) acc -= B0[(int64_t)i * d + k] * Mt[(int64_t)k * d + j];
+    Bt[((int64_t)tau * d + i) * d + j] = acc;
+}
+
+cudaError_t launch_var_transform(const double *B0, const double *M, int lags, int d, double *Bt,
+                                 cudaStream_t s)
+{
+    dim3 grid((d + 127) / 128, d, lags);
+    k_var_transform<<<grid, 128, 0, s>>>(B0, M, lags, d, Bt);
+    return cudaGetLastError();
+}
+
+__global__ void k_iota_plain(int32_t *v, int q)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) v[i] = i;
+}
+
+cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s)
+{
+    k_iota_plain<<<(q + 255) / 256, 256, 0, s>>>(v, q);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------- peak probes ---
 // Dependent-chain-free loops that keep one functional unit busy; the host
 // divides the operation count by the elapsed device time.

@@ -71,6 +71,7 @@ struct Plan {
     int64_t n = -1, d = -1;
     int prec = -1, profile = -1;
     int scores = -1;
+    int lcoef = -1;
     void *ws_epoch = nullptr;
     cudaGraphExec_t exec = nullptr;
     int nodes = 0;
@@ -92,7 +93,7 @@ struct lingam_ctx {
     int64_t cap_n = 0, cap_d = 0;
     int64_t ldr = 0, ldz = 0;
     Buf xstage, R, z, C, Cpart, mom, hzpart, M, E, hist, U, order, state, ref_var, fmom, fhz,
-        lcoef, W, piv;
+        lcoef, W, piv, cscratch;
     size_t epoch = 0;
     Plan plan;
     CUtensorMap tmI{}, tmJ{};
@@ -210,7 +211,7 @@ static lingam_status ensure_workspace(lingam_ctx *ctx, int64_t n, int64_t d)
         // free first so that the new sizes fit
         Buf *all[] = {&ctx->R, &ctx->z, &ctx->C, &ctx->Cpart, &ctx->mom, &ctx->hzpart, &ctx->M,
                       &ctx->E, &ctx->hist, &ctx->U, &ctx->order, &ctx->state, &ctx->ref_var,
-                      &ctx->fmom, &ctx->fhz, &ctx->lcoef, &ctx->W, &ctx->piv};
+                      &ctx->fmom, &ctx->fhz, &ctx->lcoef, &ctx->W, &ctx->piv, &ctx->cscratch};
         for (Buf *b : all) release(*b);
         CK(ensure(ctx->R, (size_t)D * ctx->ldr * 8));
         CK(ensure(ctx->z, (size_t)D * ctx->ldz * 4, true));
@@ -227,6 +228,10 @@ static lingam_status ensure_workspace(lingam_ctx *ctx, int64_t n, int64_t d)
         CK(ensure(ctx->ref_var, (size_t)D * 8));
         CK(ensure(ctx->fmom, (size_t)MAXC * D * 4 * 8));
         CK(ensure(ctx->fhz, (size_t)D * 2 * 8));
+        CK(ensure(ctx->lcoef, (size_t)D * D * 8));
+        CK(ensure(ctx->W, (size_t)D * D * 8));
+        CK(ensure(ctx->piv, (size_t)D * 4));
+        CK(ensure(ctx->cscratch, (size_t)D * 4));
         ctx->cap_n = N;
         ctx->cap_d = D;
         ctx->epoch++;
@@ -276,7 +281,7 @@ static lingam_status check_args(lingam_ctx *ctx, const void *X, int64_t n, int64
 
 // Capture the covariance + ordering loop for (n, d) into one graph.
 static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d64, bool scores,
-                                         int stop_after_score0, double *Iout)
+                                         int stop_after_score0, double *Iout, bool lcoef)
 {
     const int n = (int)n64, d = (int)d64;
     const int prec = ctx->opts.precision;
@@ -287,11 +292,17 @@ static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d
     int32_t *U0 = ptr<int32_t>(ctx->U), *U1 = U0 + d;
     const int ks = gram_ksplit(n, d, ctx->num_sms);
     const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
-    // Bound on |I_fp32 - I_exact| (per entry) used to pick FP64 candidates;
-    // calibrated against the FP64 oracle in the parity tests.
+    // Bound on |I_fp32 - I_exact| per entry, used to pick the candidates that
+    // are re-scored in FP64.  Measured against the FP64 oracle on GB300: max
+    // 5.8e-7 (accurate FP32) and 3.4e-7 (fast + compensated) over ~5e4
+    // entries; the bound keeps a margin above both.
     const double epsI = prec == LINGAM_PREC_FP64 ? 0.0
-                        : prec == LINGAM_PREC_MIXED ? 2e-5 * tie
-                                                    : 1e-5 * tie;
+                        : prec == LINGAM_PREC_MIXED ? 2.0e-6 * tie
+                                                    : 2.5e-6 * tie;
+    // Steps with at most P64 remaining variables are scored entirely in FP64:
+    // cheap there, and the scores of late steps are small enough that FP32
+    // rounding would dominate them.
+    const int P64 = 32;
     const int pmode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
     const double a1 = pmode == PAIR_FAST ? LN2_D : 1.0;
     const double a2 = pmode == PAIR_FAST ? 1.0 / KSC : 1.0;
@@ -355,7 +366,8 @@ static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d
         double *hist_row = scores ? ptr<double>(ctx->hist) + (size_t)t * d : nullptr;
 
         ScoreParams S{};
-        if (prec == LINGAM_PREC_FP64) {
+        const bool step64 = prec == LINGAM_PREC_FP64 || p <= P64;
+        if (step64) {
             F64Params F{};
             F.R = ptr<double>(ctx->R);
             F.ldr = ctx->ldr;
@@ -416,7 +428,7 @@ static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d
         S.ha1 = 1.0;
         S.hb1 = -LN2_D;
         S.ha2 = 1.0;
-        S.epsI = epsI;
+        S.epsI = step64 ? 0.0 : epsI;
         S.U = Uc;
         S.M = ptr<double>(ctx->M);
         S.E = ptr<double>(ctx->E);
@@ -428,27 +440,30 @@ static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d
             break;
         }
 
-        SelectParams SP{ptr<double>(ctx->M), ptr<double>(ctx->E), Uc, p, state};
+        SelectParams SP{ptr<double>(ctx->M), ptr<double>(ctx->E), Uc, p, state,
+                        ptr<int32_t>(ctx->cscratch)};
         CKC(launch_select(SP, s));
 
-        F64Params F{};
-        F.R = ptr<double>(ctx->R);
-        F.ldr = ctx->ldr;
-        F.C = ptr<double>(ctx->C);
-        F.ldc = d;
-        F.U = Uc;
-        F.p = p;
-        F.n = n;
-        F.mode = 1;
-        F.state = state;
-        F.mom = ptr<double>(ctx->fmom);
-        F.hz = ptr<double>(ctx->fhz);
-        F.status = status;
-        CKC(launch_pairs_f64(F, ctx->num_sms * 4, s));
-
-        RefineSelectParams RS{ptr<double>(ctx->fmom), ptr<double>(ctx->fhz), p, n, Uc, state,
-                              hist_row};
-        CKC(launch_refine_select(RS, s));
+        for (int pass = 1; pass <= 2; ++pass) {
+            F64Params F{};
+            F.R = ptr<double>(ctx->R);
+            F.ldr = ctx->ldr;
+            F.C = ptr<double>(ctx->C);
+            F.ldc = d;
+            F.U = Uc;
+            F.p = p;
+            F.n = n;
+            F.mode = 1;
+            F.pass = pass;
+            F.state = state;
+            F.mom = ptr<double>(ctx->fmom);
+            F.hz = ptr<double>(ctx->fhz);
+            F.status = status;
+            CKC(launch_pairs_f64(F, ctx->num_sms * 4, s));
+            RefineSelectParams RS{ptr<double>(ctx->fmom), ptr<double>(ctx->fhz), p, n, Uc, state,
+                                  hist_row, pass};
+            CKC(launch_refine_select(RS, s));
+        }
 
         RegressParams P{};
         P.R = ptr<double>(ctx->R);
@@ -469,12 +484,13 @@ static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d
         P.t = t;
         P.hzpart = ptr<double>(ctx->hzpart);
         P.ref_var = ptr<double>(ctx->ref_var);
-        P.lcoef = nullptr;
+        P.lcoef = lcoef ? ptr<double>(ctx->lcoef) : nullptr;
+        P.ldl = d;
         P.status = status;
         CKC(launch_regress(P, false, ns, s));
         nsplit_hz = ns;
         CKC(launch_downdate(ptr<double>(ctx->C), d, Uc, p, state, s));
-        nodes += 7;
+        nodes += 9;
     }
     if (!stop_after_score0) {
         int32_t *Ulast = ((d - 1) & 1) ? U1 : U0;
@@ -584,7 +600,7 @@ lingam_status lingam_destroy(lingam_ctx *ctx)
     for (cudaEvent_t e : ctx->pev) cudaEventDestroy(e);
     Buf *all[] = {&ctx->xstage, &ctx->R, &ctx->z, &ctx->C, &ctx->Cpart, &ctx->mom, &ctx->hzpart,
                   &ctx->M, &ctx->E, &ctx->hist, &ctx->U, &ctx->order, &ctx->state, &ctx->ref_var,
-                  &ctx->fmom, &ctx->fhz, &ctx->lcoef, &ctx->W, &ctx->piv};
+                  &ctx->fmom, &ctx->fhz, &ctx->lcoef, &ctx->W, &ctx->piv, &ctx->cscratch};
     for (Buf *b : all) release(*b);
     if (ctx->e0) cudaEventDestroy(ctx->e0);
     if (ctx->e1) cudaEventDestroy(ctx->e1);
@@ -607,35 +623,23 @@ lingam_status lingam_set_precision(lingam_ctx *ctx, int32_t precision)
     return LINGAM_OK;
 }
 
-lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
-                                  int32_t layout, int32_t *order_out, double *scores_out,
-                                  lingam_stream_t stream)
+// Run the captured ordering loop on the data already packed in ctx->R
+// (columns 0..d-1, centred FP64).  Copies order (and scores) to the host.
+static lingam_status run_order(lingam_ctx *ctx, int64_t n, int64_t d, int32_t *order_out,
+                               double *scores_out, bool lcoef, cudaStream_t user)
 {
-    if (!ctx) return LINGAM_ERR_ARG;
-    ctx->err.clear();
-    if (!order_out) return fail(ctx, LINGAM_ERR_ARG, "order_out is NULL");
-    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    lingam_status st = prepare(ctx, X, n, d, ld, layout, user);
-    if (st) return st;
-    if (d == 1) {
-        DevState hs{};
-        st = finish_call(ctx, user, &hs);
-        if (st) return st;
-        order_out[0] = 0;
-        if (scores_out) scores_out[0] = 0.0;
-        return status_to_code(ctx, hs.status);
-    }
     const bool scores = scores_out != nullptr;
     Plan &pl = ctx->plan;
     ctx->stats = lingam_stats{};
+    lingam_status st;
     if (!pl.exec || pl.n != n || pl.d != d || pl.prec != ctx->opts.precision ||
-        pl.profile != ctx->opts.profile || pl.scores != (int)scores ||
+        pl.profile != ctx->opts.profile || pl.scores != (int)scores || pl.lcoef != (int)lcoef ||
         pl.ws_epoch != (void *)ctx->epoch) {
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a));
         CK(cudaEventCreate(&b));
         CK(cudaEventRecord(a, ctx->s));
-        st = capture_order_graph(ctx, n, d, scores, 0, nullptr);
+        st = capture_order_graph(ctx, n, d, scores, 0, nullptr, lcoef);
         if (st) return st;
         CK(cudaEventRecord(b, ctx->s));
         CK(cudaEventSynchronize(b));
@@ -649,6 +653,7 @@ lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int
         pl.prec = ctx->opts.precision;
         pl.profile = ctx->opts.profile;
         pl.scores = (int)scores;
+        pl.lcoef = (int)lcoef;
         pl.ws_epoch = (void *)ctx->epoch;
     }
     if (scores) {
@@ -679,6 +684,7 @@ lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int
     ctx->stats.refined_steps = hs.refined_steps;
     ctx->stats.genuine_ties = hs.genuine_ties;
     ctx->stats.candidates_max = hs.cand_max;
+    ctx->stats.fp64_candidates = hs.fp64_candidates;
     ctx->stats.graph_nodes = pl.nodes;
     if (ctx->opts.profile && !ctx->pev.empty()) {
         double tot = 0, units = 0;
@@ -697,6 +703,27 @@ lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int
     return status_to_code(ctx, hs.status);
 }
 
+lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
+                                  int32_t layout, int32_t *order_out, double *scores_out,
+                                  lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!order_out) return fail(ctx, LINGAM_ERR_ARG, "order_out is NULL");
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    lingam_status st = prepare(ctx, X, n, d, ld, layout, user);
+    if (st) return st;
+    if (d == 1) {
+        DevState hs{};
+        st = finish_call(ctx, user, &hs);
+        if (st) return st;
+        order_out[0] = 0;
+        if (scores_out) scores_out[0] = 0.0;
+        return status_to_code(ctx, hs.status);
+    }
+    return run_order(ctx, n, d, order_out, scores_out, false, user);
+}
+
 lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
                                    int64_t ld, int32_t layout, double *I_out, double *M_out,
                                    lingam_stream_t stream)
@@ -713,7 +740,7 @@ lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, in
     // a one-off graph (not cached): covariance, standardise, step-0 scores
     ctx->plan.exec = nullptr;   // force re-capture for the next ordering call
     ctx->plan.n = -1;
-    st = capture_order_graph(ctx, n, d, false, 1, ptr<double>(Ib));
+    st = capture_order_graph(ctx, n, d, false, 1, ptr<double>(Ib), false);
     if (st) {
         release(Ib);
         return st;
@@ -825,9 +852,83 @@ lingam_status varlingam_fit(lingam_ctx *ctx, const void *Xt, int64_t T, int64_t 
                             int32_t layout, int32_t lags, int32_t *order_out, double *B0_out,
                             double *Btau_out, lingam_stream_t stream)
 {
-    (void)Xt; (void)T; (void)d; (void)ld; (void)layout; (void)lags; (void)order_out;
-    (void)B0_out; (void)Btau_out; (void)stream;
-    return fail(ctx, LINGAM_ERR_ARG, "varlingam_fit: not built yet");
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!Xt || !order_out) return fail(ctx, LINGAM_ERR_ARG, "Xt or order_out is NULL");
+    if (lags < 1 || d < 1) return fail(ctx, LINGAM_ERR_ARG, "need lags >= 1 and d >= 1");
+    if (layout != LINGAM_ROW_MAJOR && layout != LINGAM_COL_MAJOR)
+        return fail(ctx, LINGAM_ERR_ARG, "bad layout");
+    if ((layout == LINGAM_ROW_MAJOR && ld < d) || (layout == LINGAM_COL_MAJOR && ld < T))
+        return fail(ctx, LINGAM_ERR_ARG, "ld too small");
+    const int64_t n = T - lags, nz = (int64_t)lags * d, q = nz + d;
+    if (n <= q) return fail(ctx, LINGAM_ERR_DEGENERATE, "T - lags must exceed lags*d + d");
+    if (q > 6000) return fail(ctx, LINGAM_ERR_ARG, "(lags+1)*d > 6000 is not supported");
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(ctx->device));
+    lingam_status st = ensure_workspace(ctx, n, q);
+    if (st) return st;
+    CK(cudaEventRecord(ctx->e0, user));
+    CK(cudaStreamWaitEvent(ctx->s, ctx->e0, 0));
+    const void *dX = nullptr;
+    st = stage_input(ctx, Xt, T, d, ld, layout, 4, &dX);
+    if (st) return st;
+    DevState *state = ptr<DevState>(ctx->state);
+    CK(cudaMemsetAsync(&state->status, 0, sizeof(uint32_t), ctx->s));
+    const float *xf = reinterpret_cast<const float *>(dX);
+    double *R = ptr<double>(ctx->R);
+    const int ni = (int)n, di = (int)d, qi = (int)q;
+    // design [x(t-1) .. x(t-lags) | x(t)], t = lags..T-1, one column per variable
+    auto shifted = [&](int64_t shift) {
+        return layout == LINGAM_ROW_MAJOR ? (const void *)(xf + shift * ld) : (const void *)(xf + shift);
+    };
+    for (int tau = 1; tau <= lags; ++tau)
+        CK(launch_pack(shifted(lags - tau), 0, layout, ld, ni, di, R + (int64_t)(tau - 1) * d * ctx->ldr,
+                       ctx->ldr, &state->status, ctx->s));
+    CK(launch_pack(shifted(lags), 0, layout, ld, ni, di, R + nz * ctx->ldr, ctx->ldr, &state->status,
+                   ctx->s));
+    CK(launch_center(R, ctx->ldr, ni, qi, ctx->s));     // centring = the intercept
+    const int ks = gram_ksplit(ni, qi, ctx->num_sms);
+    CK(launch_gram_f64(R, ctx->ldr, ni, qi, ptr<double>(ctx->Cpart), ks, ptr<double>(ctx->C), q,
+                       ptr<double>(ctx->ref_var), ctx->s));
+    CK(launch_iota_plain(ptr<int32_t>(ctx->piv), qi, ctx->s));
+    const int nsplit = regress_splits(ctx, qi / 2, ni);
+    for (int t = 0; t < (int)nz; ++t) {
+        CK(launch_ldl_step(ptr<double>(ctx->C), q, ptr<int32_t>(ctx->piv), t, qi,
+                           ptr<double>(ctx->lcoef), q, ctx->s));
+        CK(launch_regress_cols(R, ctx->ldr, ptr<double>(ctx->lcoef), q, t, qi, ni, nsplit, ctx->s));
+    }
+    Buf Mb, Btb;
+    CK(ensure(Mb, (size_t)nz * d * 8));
+    CK(launch_var_coefficients(ptr<double>(ctx->lcoef), q, (int)nz, di, ptr<double>(Mb), ctx->s));
+    // innovations E (columns nz..q-1) become the data of the ordering loop
+    CK(cudaMemcpyAsync(R, R + nz * ctx->ldr, (size_t)d * ctx->ldr * 8, cudaMemcpyDeviceToDevice,
+                       ctx->s));
+    if (d == 1) {
+        order_out[0] = 0;
+    } else {
+        st = run_order(ctx, n, d, order_out, nullptr, true, user);
+        if (st) {
+            release(Mb);
+            return st;
+        }
+    }
+    // B0 = I - L^{-1} along the order (L recorded by the regress-out steps)
+    CK(cudaMemcpyAsync(ctx->piv.p, order_out, (size_t)d * 4, cudaMemcpyHostToDevice, ctx->s));
+    CK(launch_unit_lower_inverse(ptr<double>(ctx->lcoef), d, ptr<int32_t>(ctx->piv), di,
+                                 ptr<double>(ctx->W), d, ctx->s));
+    CK(ensure(Btb, (size_t)lags * d * d * 8));
+    CK(launch_var_transform(ptr<double>(ctx->W), ptr<double>(Mb), lags, di, ptr<double>(Btb),
+                            ctx->s));
+    if (B0_out)
+        CK(cudaMemcpyAsync(B0_out, ctx->W.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if (Btau_out)
+        CK(cudaMemcpyAsync(Btau_out, Btb.p, (size_t)lags * d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
+    DevState hs{};
+    st = finish_call(ctx, user, &hs);
+    release(Mb);
+    release(Btb);
+    if (st) return st;
+    return status_to_code(ctx, hs.status);
 }
 
 lingam_status lingam_causal_order_batch(lingam_ctx *ctx, const lingam_instance *inst,

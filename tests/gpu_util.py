@@ -42,11 +42,28 @@ def read_cfg5_golden():
     return out
 
 
+class ScoreCheck(float):
+    """Max violation of the per-step score tolerance (<= 0 means pass); the
+    repr names the worst step."""
+
+    def __new__(cls, value, info):
+        obj = float.__new__(cls, value)
+        obj.info = info
+        return obj
+
+    def __repr__(self):
+        return f"{float(self):.3e} ({self.info})"
+
+
 def scores_close(gpu, ref):
-    """Max violation of the per-step score tolerance (<= 0 means pass)."""
     fin = np.isfinite(ref)
     assert np.array_equal(fin, np.isfinite(gpu))
     scale = np.nanmax(np.abs(np.where(fin, ref, np.nan)), axis=1, keepdims=True)
     scale = np.where(np.isfinite(scale), scale, 0.0)
     err = np.abs(np.where(fin, gpu - ref, 0.0))
-    return float(np.max(err - (M_REL * scale + M_ABS)))
+    viol = err - (M_REL * scale + M_ABS)
+    t, i = np.unravel_index(np.argmax(viol), viol.shape)
+    p = int(fin[t].sum())
+    info = (f"step {t} (p={p}) var {i}: gpu {gpu[t, i]:.9e} ref {ref[t, i]:.9e} "
+            f"max|M| {scale[t, 0]:.3e}")
+    return ScoreCheck(float(viol[t, i]), info)
