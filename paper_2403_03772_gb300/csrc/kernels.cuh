@@ -33,6 +33,7 @@ struct PairParams {
     int nsplit;
     double *mom;          // out [nsplit][p][p][2] moment sums of entry (i, j)
     uint32_t *status;
+    int row0;             // first row of this instance in the z tensor
 };
 
 struct F64Params {
@@ -104,28 +105,64 @@ struct RegressParams {
     uint32_t *status;
 };
 
+struct GramParams {
+    const double *R;
+    int64_t ldr;
+    int n, d, ksplit;
+    double *Cpart;        // [ksplit][d][d]
+    double *C;            // [d][ldc]
+    int64_t ldc;
+    double *ref_var;      // diag(C) of the original data
+};
+
+struct IotaParams {
+    int32_t *U;
+    int d;
+    DevState *state;
+};
+
+struct DowndateParams {
+    double *C;
+    int64_t ldc;
+    const int32_t *U;
+    int p;
+    const DevState *state;
+};
+
+struct FinishParams {
+    const int32_t *U;
+    int32_t *order;
+    int d;
+    double *hist_row;
+};
+
 // ---- launchers (return the launch error) ----
+// Batched launchers take a device array of per-instance parameters.
 cudaError_t launch_pack(const void *X, int is_f64, int layout, int64_t ld, int n, int d,
                         double *R, int64_t ldr, uint32_t *status, cudaStream_t s);
 cudaError_t launch_center(double *R, int64_t ldr, int n, int d, cudaStream_t s);
 cudaError_t launch_gram_f64(const double *R, int64_t ldr, int n, int d, double *Cpart,
                             int ksplit, double *C, int64_t ldc, double *ref_var,
                             cudaStream_t s);
+cudaError_t launch_gram_b(const GramParams *P, int count, int maxd, int maxksplit, cudaStream_t s);
 int gram_ksplit(int n, int d, int num_sms);
-cudaError_t launch_iota(int32_t *U, int d, DevState *state, cudaStream_t s);
-cudaError_t launch_regress(const RegressParams &P, bool init, int nsplit, cudaStream_t s);
-cudaError_t launch_downdate(double *C, int64_t ldc, const int32_t *U, int p,
-                            const DevState *state, cudaStream_t s);
-cudaError_t launch_finish(const int32_t *U, int32_t *order, int d, double *hist_row,
-                          cudaStream_t s);
+cudaError_t launch_iota_b(const IotaParams *P, int count, int maxd, cudaStream_t s);
+cudaError_t launch_regress_b(const RegressParams *P, int count, bool init, int maxcols,
+                             int maxsplit, cudaStream_t s);
+cudaError_t launch_downdate_b(const DowndateParams *P, int count, int maxp, cudaStream_t s);
+cudaError_t launch_finish_b(const FinishParams *P, int count, cudaStream_t s);
 
 cudaError_t pair_kernel_setup();
-cudaError_t launch_pair(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
-                        const PairParams &P, cudaStream_t s);
-cudaError_t launch_pairs_f64(const F64Params &P, int grid, cudaStream_t s);
-cudaError_t launch_score(const ScoreParams &P, cudaStream_t s);
-cudaError_t launch_select(const SelectParams &P, cudaStream_t s);
-cudaError_t launch_refine_select(const RefineSelectParams &P, cudaStream_t s);
+cudaError_t launch_pair_b(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
+                          const PairParams *P, const int *prefix, int count, int total_ctas,
+                          cudaStream_t s);
+cudaError_t launch_pairs_f64_b(const F64Params *P, int count, int blocks_per_inst, cudaStream_t s);
+cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream_t s);
+cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s);
+cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp,
+                                   cudaStream_t s);
+cudaError_t launch_pack_gather(const float *X, int64_t ld, const int32_t *rows, int n, int d,
+                               double *R, int64_t ldr, uint32_t *status, cudaStream_t s);
 
 // Adjacency / VAR helpers
 cudaError_t launch_ldl_step(double *C, int64_t ldc, const int32_t *pivots, int t, int d,

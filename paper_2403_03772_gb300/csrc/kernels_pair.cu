@@ -116,9 +116,9 @@ __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
 // The compensated fast form keeps three FP32 words per accumulator; it runs
 // one CTA per SM with the register budget that allows, the accurate form two.
 template <int MODE>
-__global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
-    k_pair_moments(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
-                   const PairParams P)
+__device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtensorMap *tmJ,
+                                           const PairParams &P, const int ti, const int tj,
+                                           const int split)
 {
     constexpr int WI = PAIR_WI, WJ = PAIR_WJ, WGJ = PAIR_WGJ;
     constexpr int NCW = PAIR_WGI * PAIR_WGJ;
@@ -134,8 +134,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
     float *buf = reinterpret_cast<float *>(smem + 1024);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ti = blockIdx.x / P.tiles_j, tj = blockIdx.x % P.tiles_j;
-    const int c0 = blockIdx.y * P.cps;
+    const int c0 = split * P.cps;
     const int c1 = min(c0 + P.cps, P.nchunks);
     const int nck = c1 - c0;
 
@@ -154,8 +153,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
     if (warp == NCW) {
         // ---------------- producer warp: one elected lane issues the TMA ----
         if (lane == 0) {
-            prefetch_tensormap(&tmI);
-            prefetch_tensormap(&tmJ);
+            prefetch_tensormap(tmI);
+            prefetch_tensormap(tmJ);
             int issued = 0;
             for (int k = 0; k < nck; ++k) {
                 const int st = k % STAGES;
@@ -171,8 +170,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
                 float *dst = buf + st * STAGE_FLOATS;
                 const int x = (c0 + k) * S;
                 mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-                tma_load_2d(dst, &tmI, x, ti * TI, &full[st]);
-                tma_load_2d(dst + TI * S, &tmJ, x, tj * TJ, &full[st]);
+                tma_load_2d(dst, tmI, x, P.row0 + ti * TI, &full[st]);
+                tma_load_2d(dst + TI * S, tmJ, x, P.row0 + tj * TJ, &full[st]);
                 issued = k + 1;
             }
             // never leave with a copy in flight: wait (bounded) for the last
@@ -273,7 +272,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
     }
 
     // ---------------- cross-lane reduction (fixed xor tree) ------------------
-    double *mom = P.mom + (size_t)blockIdx.y * P.p * P.p * 2;
+    double *mom = P.mom + (size_t)split * P.p * P.p * 2;
 #pragma unroll
     for (int r = 0; r < WI; ++r) {
 #pragma unroll
@@ -308,6 +307,27 @@ __global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
     }
 }
 
+// One launch covers the tiles of every instance in the batch: prefix[k] is the
+// first CTA of instance k (tiles_i * tiles_j * nsplit CTAs each).
+template <int MODE>
+__global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
+    k_pair_moments_b(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
+                     const PairParams *__restrict__ Ps, const int *__restrict__ prefix, int count)
+{
+    int lo = 0, hi = count - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const PairParams P = Ps[lo];
+    const int local = b - prefix[lo];
+    const int tiles = P.tiles_i * P.tiles_j;
+    const int split = local / tiles, tile = local % tiles;
+    pair_block<MODE>(&tmI, &tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
+}
+
 static size_t pair_smem_bytes()
 {
     return 1024 + (size_t)PAIR_STAGES * (PAIR_TI + PAIR_TJ) * PAIR_S * 4;
@@ -315,23 +335,26 @@ static size_t pair_smem_bytes()
 
 cudaError_t pair_kernel_setup()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_moments<PAIR_ACCURATE>,
+    cudaError_t e = cudaFuncSetAttribute(k_pair_moments_b<PAIR_ACCURATE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pair_smem_bytes());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pair_moments<PAIR_FAST>,
+    return cudaFuncSetAttribute(k_pair_moments_b<PAIR_FAST>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pair_smem_bytes());
 }
 
-cudaError_t launch_pair(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
-                        const PairParams &P, cudaStream_t s)
+cudaError_t launch_pair_b(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
+                          const PairParams *P, const int *prefix, int count, int total_ctas,
+                          cudaStream_t s)
 {
-    dim3 grid(P.tiles_i * P.tiles_j, P.nsplit);
+    if (total_ctas <= 0 || count <= 0) return cudaSuccess;
     if (mode == PAIR_FAST)
-        k_pair_moments<PAIR_FAST><<<grid, PAIR_THREADS, pair_smem_bytes(), s>>>(*tmI, *tmJ, P);
+        k_pair_moments_b<PAIR_FAST><<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(
+            *tmI, *tmJ, P, prefix, count);
     else
-        k_pair_moments<PAIR_ACCURATE><<<grid, PAIR_THREADS, pair_smem_bytes(), s>>>(*tmI, *tmJ, P);
+        k_pair_moments_b<PAIR_ACCURATE><<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(
+            *tmI, *tmJ, P, prefix, count);
     return cudaGetLastError();
 }
 
@@ -349,7 +372,7 @@ __device__ __forceinline__ void f64_terms(double u, double &t1, double &t2)
     t2 = u * exp(-0.5 * u * u);
 }
 
-__global__ void __launch_bounds__(256) k_pairs_f64(const F64Params P)
+__device__ __forceinline__ void pairs_f64_body(const F64Params &P)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -459,9 +482,17 @@ __global__ void __launch_bounds__(256) k_pairs_f64(const F64Params P)
     }
 }
 
-cudaError_t launch_pairs_f64(const F64Params &P, int grid, cudaStream_t s)
+// blockIdx.y selects the instance; the x blocks stride its work items.
+__global__ void __launch_bounds__(256) k_pairs_f64_b(const F64Params *__restrict__ Ps)
 {
-    k_pairs_f64<<<grid, 256, 0, s>>>(P);
+    const F64Params P = Ps[blockIdx.y];
+    pairs_f64_body(P);
+}
+
+cudaError_t launch_pairs_f64_b(const F64Params *P, int count, int blocks_per_inst, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_pairs_f64_b<<<dim3(blocks_per_inst, count), 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -473,9 +504,11 @@ cudaError_t launch_pairs_f64(const F64Params &P, int grid, cudaStream_t s)
 // M(i) = -sum_{j != i} min(0, I(i, j))^2, summed by each lane over j in
 // ascending order and across lanes by a fixed xor tree.  E(i) bounds |M(i) -
 // M_exact(i)| given |I - I_exact| <= epsI.
-__global__ void __launch_bounds__(256) k_score(const ScoreParams P)
+__global__ void __launch_bounds__(256) k_score_b(const ScoreParams *__restrict__ Ps)
 {
     extern __shared__ double hsh[];   // h(z_j), j < p
+    const ScoreParams P = Ps[blockIdx.y];
+    if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= P.p) return;
     const double invn = 1.0 / (double)P.n;
     for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
         double S1 = 0.0, S2 = 0.0;
@@ -521,11 +554,12 @@ __global__ void __launch_bounds__(256) k_score(const ScoreParams P)
     }
 }
 
-cudaError_t launch_score(const ScoreParams &P, cudaStream_t s)
+cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream_t s)
 {
+    if (count <= 0) return cudaSuccess;
     const int rows_per_block = 8;
-    dim3 grid((P.p + rows_per_block - 1) / rows_per_block);
-    k_score<<<grid, 256, sizeof(double) * P.p, s>>>(P);
+    dim3 grid((maxp + rows_per_block - 1) / rows_per_block, count);
+    k_score_b<<<grid, 256, sizeof(double) * maxp, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -538,8 +572,9 @@ __device__ __forceinline__ bool better(double m, int u, double bm, int bu)
     return (m > bm) || (m == bm && u < bu);
 }
 
-__global__ void __launch_bounds__(1024) k_select(const SelectParams P)
+__global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restrict__ Ps)
 {
+    const SelectParams P = Ps[blockIdx.x];
     __shared__ double sm[32];
     __shared__ int su[32], sp[32];
     __shared__ int s_top, s_cnt;
@@ -626,9 +661,10 @@ __global__ void __launch_bounds__(1024) k_select(const SelectParams P)
     }
 }
 
-cudaError_t launch_select(const SelectParams &P, cudaStream_t s)
+cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s)
 {
-    k_select<<<1, 1024, 0, s>>>(P);
+    if (count <= 0) return cudaSuccess;
+    k_select_b<<<count, 1024, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -636,9 +672,10 @@ cudaError_t launch_select(const SelectParams &P, cudaStream_t s)
 // with the highest upper bounds; if the better of them beats every remaining
 // upper bound the step is decided, otherwise pass 2 scores the rest and the
 // argmax is taken over all FP64 scores (ties to the smallest original index).
-__global__ void __launch_bounds__(256) k_refine_select(const RefineSelectParams P)
+__global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParams *__restrict__ Ps)
 {
     extern __shared__ double h64[];
+    const RefineSelectParams P = Ps[blockIdx.x];
     DevState *st = P.state;
     if (st->resolved) return;
     const int cb = st->pass_begin, ce = st->pass_end, nc = st->ncand;
@@ -685,9 +722,10 @@ __global__ void __launch_bounds__(256) k_refine_select(const RefineSelectParams 
     }
 }
 
-cudaError_t launch_refine_select(const RefineSelectParams &P, cudaStream_t s)
+cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp, cudaStream_t s)
 {
-    k_refine_select<<<1, 256, sizeof(double) * P.p, s>>>(P);
+    if (count <= 0) return cudaSuccess;
+    k_refine_select_b<<<count, 256, sizeof(double) * maxp, s>>>(P);
     return cudaGetLastError();
 }
 

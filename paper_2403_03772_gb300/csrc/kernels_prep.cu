@@ -70,6 +70,41 @@ cudaError_t launch_pack(const void *X, int is_f64, int layout, int64_t ld, int n
     return cudaGetLastError();
 }
 
+// Row-major FP32 rows X[rows[s]] (rows == nullptr: X[s]) -> R [d][ldr] FP64
+// (bootstrap resampling gathers the sampled rows while transposing).
+__global__ void k_pack_gather(const float *__restrict__ X, int64_t ld, const int32_t *__restrict__ rows,
+                              int n, int d, double *__restrict__ R, int64_t ldr, uint32_t *status)
+{
+    __shared__ double tile[32][33];
+    const int s0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    bool bad = false;
+    for (int k = ty; k < 32; k += 8) {
+        const int s = s0 + k, v = v0 + tx;
+        double x = 0.0;
+        if (s < n && v < d) {
+            const int64_t src = rows ? (int64_t)rows[s] : (int64_t)s;
+            x = (double)X[src * ld + v];
+            bad |= !isfinite(x);
+        }
+        tile[k][tx] = x;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int v = v0 + k, s = s0 + tx;
+        if (s < n && v < d) R[(int64_t)v * ldr + s] = tile[tx][k];
+    }
+    if (bad) set_status(status, ST_NONFINITE);
+}
+
+cudaError_t launch_pack_gather(const float *X, int64_t ld, const int32_t *rows, int n, int d,
+                               double *R, int64_t ldr, uint32_t *status, cudaStream_t s)
+{
+    dim3 grid((n + 31) / 32, (d + 31) / 32), block(32, 8);
+    k_pack_gather<<<grid, block, 0, s>>>(X, ld, rows, n, d, R, ldr, status);
+    return cudaGetLastError();
+}
+
 // Block-wide FP64 sum with a fixed reduction tree (deterministic).
 __device__ double block_sum(double v, double *sh)
 {
@@ -112,22 +147,22 @@ cudaError_t launch_center(double *R, int64_t ldr, int n, int d, cudaStream_t s)
 // is exactly symmetric.
 constexpr int GT = 64, GK = 16;
 
-__global__ void __launch_bounds__(256) k_gram_f64(const double *__restrict__ R, int64_t ldr,
-                                                  int n, int d, int ksplit,
-                                                  double *__restrict__ Cpart)
+__device__ __forceinline__ void gram_block(const double *__restrict__ R, int64_t ldr, int n, int d,
+                                           int ksplit, double *__restrict__ Cpart, int tile,
+                                           int kslice)
 {
     __shared__ double As[GK][GT + 1];
     __shared__ double Bs[GK][GT + 1];
     // upper-triangular tile index -> (bi, bj)
     const int nt = (d + GT - 1) / GT;
-    int t = blockIdx.x, bi = 0;
+    int t = tile, bi = 0;
     while (t >= nt - bi) {
         t -= nt - bi;
         ++bi;
     }
     const int bj = bi + t;
     const int slice = (n + ksplit - 1) / ksplit;
-    const int k0 = blockIdx.y * slice, k1 = min(n, k0 + slice);
+    const int k0 = kslice * slice, k1 = min(n, k0 + slice);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double acc[4][4] = {};
     const int lv = threadIdx.x >> 2;            // 0..63 variable within tile
@@ -155,7 +190,7 @@ __global__ void __launch_bounds__(256) k_gram_f64(const double *__restrict__ R, 
         }
         __syncthreads();
     }
-    double *out = Cpart + (size_t)blockIdx.y * d * d;
+    double *out = Cpart + (size_t)kslice * d * d;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -165,10 +200,10 @@ __global__ void __launch_bounds__(256) k_gram_f64(const double *__restrict__ R, 
         }
 }
 
-__global__ void k_gram_reduce(const double *__restrict__ Cpart, int ksplit, int n, int d,
-                              double *__restrict__ C, int64_t ldc, double *ref_var)
+__device__ __forceinline__ void gram_reduce_row(const double *__restrict__ Cpart, int ksplit, int n,
+                                                int d, double *__restrict__ C, int64_t ldc,
+                                                double *ref_var, int i, int j)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
     if (j >= d) return;
     // read the entry from the upper-triangular tile that computed it
     int a = i, b = j;
@@ -181,6 +216,47 @@ __global__ void k_gram_reduce(const double *__restrict__ Cpart, int ksplit, int 
     const double v = s / (double)n;
     C[(int64_t)i * ldc + j] = v;
     if (i == j && ref_var) ref_var[i] = v;
+}
+
+__global__ void __launch_bounds__(256) k_gram_f64(const double *__restrict__ R, int64_t ldr, int n,
+                                                  int d, int ksplit, double *__restrict__ Cpart)
+{
+    gram_block(R, ldr, n, d, ksplit, Cpart, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_gram_reduce(const double *__restrict__ Cpart, int ksplit, int n, int d,
+                              double *__restrict__ C, int64_t ldc, double *ref_var)
+{
+    gram_reduce_row(Cpart, ksplit, n, d, C, ldc, ref_var, blockIdx.y,
+                    blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Batched covariance: blockIdx.z selects the instance.
+__global__ void __launch_bounds__(256) k_gram_b(const GramParams *__restrict__ Ps)
+{
+    const GramParams P = Ps[blockIdx.z];
+    const int nt = (P.d + GT - 1) / GT;
+    if ((int)blockIdx.x >= nt * (nt + 1) / 2 || (int)blockIdx.y >= P.ksplit) return;
+    gram_block(P.R, P.ldr, P.n, P.d, P.ksplit, P.Cpart, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_gram_reduce_b(const GramParams *__restrict__ Ps)
+{
+    const GramParams P = Ps[blockIdx.z];
+    if ((int)blockIdx.y >= P.d) return;
+    gram_reduce_row(P.Cpart, P.ksplit, P.n, P.d, P.C, P.ldc, P.ref_var, blockIdx.y,
+                    blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+cudaError_t launch_gram_b(const GramParams *P, int count, int maxd, int maxksplit, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int nt = (maxd + GT - 1) / GT;
+    k_gram_b<<<dim3(nt * (nt + 1) / 2, maxksplit, count), 256, 0, s>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gram_reduce_b<<<dim3((maxd + 127) / 128, maxd, count), 128, 0, s>>>(P);
+    return cudaGetLastError();
 }
 
 int gram_ksplit(int n, int d, int num_sms)
@@ -206,22 +282,29 @@ cudaError_t launch_gram_f64(const double *R, int64_t ldr, int n, int d, double *
 }
 
 // ----------------------------------------------------------------- state ---
-__global__ void k_iota(int32_t *U, int d, DevState *state)
+__global__ void k_iota_b(const IotaParams *__restrict__ Ps)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) U[i] = i;
+    const IotaParams P = Ps[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.d; i += gridDim.x * blockDim.x)
+        P.U[i] = i;
     if (blockIdx.x == 0 && threadIdx.x == 0) {   // status is cleared by the host before pack
-        state->m_pos = 0;
-        state->ncand = 0;
-        state->refined_steps = 0;
-        state->genuine_ties = 0;
-        state->cand_max = 0;
-        state->cand_overflow = 0;
+        DevState *st = P.state;
+        st->m_pos = 0;
+        st->ncand = 0;
+        st->refined_steps = 0;
+        st->genuine_ties = 0;
+        st->cand_max = 0;
+        st->cand_overflow = 0;
+        st->resolved = 1;
+        st->pass_begin = st->pass_end = 0;
+        st->fp64_candidates = 0;
     }
 }
 
-cudaError_t launch_iota(int32_t *U, int d, DevState *state, cudaStream_t s)
+cudaError_t launch_iota_b(const IotaParams *P, int count, int maxd, cudaStream_t s)
 {
-    k_iota<<<(d + 255) / 256, 256, 0, s>>>(U, d, state);
+    if (count <= 0) return cudaSuccess;
+    k_iota_b<<<dim3((maxd + 255) / 256, count), 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -234,10 +317,12 @@ cudaError_t launch_iota(int32_t *U, int d, DevState *state, cudaStream_t s)
 // (accurate FP32 functions, FP64 block sums).  INIT=true only standardises
 // (first step, no regression).
 template <bool INIT>
-__global__ void __launch_bounds__(256) k_regress(const RegressParams P)
+__global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restrict__ Ps)
 {
     __shared__ double sh[32];
+    const RegressParams P = Ps[blockIdx.z];
     const int col = blockIdx.x;
+    if (col >= (INIT ? P.p : P.p - 1) || (int)blockIdx.y * P.sps >= P.n) return;
     int pos = col, m = -1, mpos = -1;
     double coef = 0.0, var;
     if (!INIT) {
@@ -292,49 +377,57 @@ __global__ void __launch_bounds__(256) k_regress(const RegressParams P)
     }
 }
 
-cudaError_t launch_regress(const RegressParams &P, bool init, int nsplit, cudaStream_t s)
+cudaError_t launch_regress_b(const RegressParams *P, int count, bool init, int maxcols,
+                             int maxsplit, cudaStream_t s)
 {
-    dim3 grid(init ? P.p : P.p - 1, nsplit);
+    if (count <= 0 || maxcols <= 0) return cudaSuccess;
+    dim3 grid(maxcols, maxsplit, count);
     if (init)
-        k_regress<true><<<grid, 256, 0, s>>>(P);
+        k_regress_b<true><<<grid, 256, 0, s>>>(P);
     else
-        k_regress<false><<<grid, 256, 0, s>>>(P);
+        k_regress_b<false><<<grid, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 // Rank-1 downdate of the covariance of the remaining variables (FP64):
 // C_ij <- C_ij - C_im C_jm / C_mm, written symmetric-exact.
-__global__ void k_downdate(double *C, int64_t ldc, const int32_t *U, int p, const DevState *state)
+__global__ void k_downdate_b(const DowndateParams *__restrict__ Ps)
 {
-    const int mpos = state->m_pos;
-    const int m = U[mpos];
+    const DowndateParams P = Ps[blockIdx.z];
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= p - 1 || c >= p - 1) return;
-    const int i = U[r + (r >= mpos ? 1 : 0)];
-    const int j = U[c + (c >= mpos ? 1 : 0)];
+    if (r >= P.p - 1 || c >= P.p - 1) return;
+    const int mpos = P.state->m_pos;
+    const int m = P.U[mpos];
+    const int i = P.U[r + (r >= mpos ? 1 : 0)];
+    const int j = P.U[c + (c >= mpos ? 1 : 0)];
+    double *C = P.C;
+    const int64_t ldc = P.ldc;
     const double cmm = C[(int64_t)m * ldc + m];
     const double cim = C[(int64_t)i * ldc + m], cjm = C[(int64_t)j * ldc + m];
     C[(int64_t)i * ldc + j] -= (cim * cjm) / cmm;
 }
 
-cudaError_t launch_downdate(double *C, int64_t ldc, const int32_t *U, int p, const DevState *state,
-                            cudaStream_t s)
+cudaError_t launch_downdate_b(const DowndateParams *P, int count, int maxp, cudaStream_t s)
 {
-    dim3 block(32, 8), grid((p - 1 + 31) / 32, (p - 1 + 7) / 8);
-    k_downdate<<<grid, block, 0, s>>>(C, ldc, U, p, state);
+    if (count <= 0 || maxp < 2) return cudaSuccess;
+    dim3 block(32, 8), grid((maxp - 1 + 31) / 32, (maxp - 1 + 7) / 8, count);
+    k_downdate_b<<<grid, block, 0, s>>>(P);
     return cudaGetLastError();
 }
 
-__global__ void k_finish(const int32_t *U, int32_t *order, int d, double *hist_row)
+__global__ void k_finish_b(const FinishParams *__restrict__ Ps)
 {
-    order[d - 1] = U[0];
-    if (hist_row) hist_row[U[0]] = 0.0;
+    const FinishParams P = Ps[blockIdx.x];
+    if (threadIdx.x != 0) return;
+    P.order[P.d - 1] = P.U[0];
+    if (P.hist_row) P.hist_row[P.U[0]] = 0.0;
 }
 
-cudaError_t launch_finish(const int32_t *U, int32_t *order, int d, double *hist_row, cudaStream_t s)
+cudaError_t launch_finish_b(const FinishParams *P, int count, cudaStream_t s)
 {
-    k_finish<<<1, 1, 0, s>>>(U, order, d, hist_row);
+    if (count <= 0) return cudaSuccess;
+    k_finish_b<<<count, 32, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -1,24 +1,28 @@
 // lingam_abi.cu -- host orchestration and the extern "C" entry points
 // declared in include/lingam.h.
 //
-// One ordering run: pack + centre the data (FP64 columns), FP64 covariance,
-// then the d-1 steps of the DirectLiNGAM loop (Sec. 2.2), each running
-// Algorithm 1 on the device:
+// An ordering run is a batch of instances (a single call is a batch of one).
+// Per instance: pack + centre the data (FP64 columns), FP64 covariance, then
+// the d-1 steps of the DirectLiNGAM loop (Sec. 2.2), each running Algorithm 1
+// on the device:
 //   pair moments -> score I, M -> select (argmax + near-tie candidates)
-//   -> FP64 re-score of candidates (no-op unless >= 2) -> regress-out +
+//   -> FP64 re-score passes (no-ops unless candidates) -> regress-out +
 //   standardise + variable moments -> rank-1 covariance downdate.
-// p = d - t is known when the loop is captured, which variables remain is
-// only known on the device, so the whole loop is captured once per shape into
-// one CUDA graph and replayed; the host sees the device only at launch and at
-// the final copy of the order.
+// All instances advance through global step t together: every kernel of a
+// step is one launch over the instances still running, reading per-instance
+// parameters from a device array.  p = d - t of every instance is known when
+// the loop is captured, which variables remain is only known on the device,
+// so the whole loop is captured once per batch shape into one CUDA graph and
+// replayed; the host sees the device only at launch and at the final copies.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
-#include <new>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -63,21 +67,50 @@ T *ptr(Buf &b)
 
 int64_t roundup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-struct PairPlan {
-    int tiles_i, tiles_j, nchunks, cps, nsplit;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+// Steps with at most P64 remaining variables are scored entirely in FP64:
+// cheap there, and the scores of late steps are small enough that FP32
+// rounding would dominate them.
+constexpr int P64 = 32;
+
+struct InstSpec {
+    int64_t n, d;
+    bool operator==(const InstSpec &o) const { return n == o.n && d == o.d; }
+};
+
+// Device layout of one instance inside the plan arena.
+struct InstDev {
+    int64_t n = 0, d = 0, ldr = 0;
+    double *R = nullptr, *C = nullptr, *Cpart = nullptr, *mom = nullptr, *hzpart = nullptr;
+    double *M = nullptr, *E = nullptr, *hist = nullptr, *ref_var = nullptr, *fmom = nullptr;
+    double *fhz = nullptr, *lcoef = nullptr;
+    int32_t *U0 = nullptr, *U1 = nullptr, *order = nullptr, *scratch = nullptr, *rows = nullptr;
+    DevState *state = nullptr;
+    int zrow = 0;
+    int ksplit = 1;
+    size_t mom_elems = 0, hz_elems = 0;
+};
+
+// Sample-split decisions of one global step (shared by sizing and capture).
+struct StepSplit {
+    std::vector<int> pair_nsplit, pair_cps, reg_nsplit, reg_sps;
 };
 
 struct Plan {
-    int64_t n = -1, d = -1;
-    int prec = -1, profile = -1;
-    int scores = -1;
-    int lcoef = -1;
-    void *ws_epoch = nullptr;
+    std::vector<InstSpec> spec;
+    int prec = -1, profile = -1, scores = -1, lcoef = -1, rows = -1;
+    bool partial = false;   // graph holds only the first step's scores
     cudaGraphExec_t exec = nullptr;
     int nodes = 0;
+    Buf arena, zarena, params;
+    std::vector<InstDev> inst;
+    int64_t ldz = 0, zrows = 0;
+    int maxd = 0;
+    CUtensorMap tmI{}, tmJ{};
+    std::vector<cudaEvent_t> pev;
+    std::vector<double> punits;
 };
-
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
 
@@ -87,18 +120,10 @@ struct lingam_ctx {
     lingam_opts opts{};
     std::string err;
     cudaStream_t s = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-
-    // workspace
-    int64_t cap_n = 0, cap_d = 0;
-    int64_t ldr = 0, ldz = 0;
-    Buf xstage, R, z, C, Cpart, mom, hzpart, M, E, hist, U, order, state, ref_var, fmom, fhz,
-        lcoef, W, piv, cscratch;
-    size_t epoch = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, g0 = nullptr, g1 = nullptr;
     Plan plan;
-    CUtensorMap tmI{}, tmJ{};
-    std::vector<cudaEvent_t> pev;
-    std::vector<double> punits;
+    // host-input staging and the buffers of the adjacency / VAR paths
+    Buf xstage, aR, aC, aCpart, aL, aW, aPiv, aM, aBt, aRef, aStatus;
     lingam_stats stats{};
 };
 
@@ -137,41 +162,54 @@ static lingam_status status_to_code(lingam_ctx *ctx, uint32_t st)
     return LINGAM_OK;
 }
 
-// ---------------------------------------------------------------- plans ----
+// ------------------------------------------------------------ planning -----
 
-static PairPlan pair_plan(const lingam_ctx *ctx, int p, int n)
+static bool step_in_fp64(int prec, int p) { return prec == LINGAM_PREC_FP64 || p <= P64; }
+
+static int pair_nchunks(int64_t n) { return (int)((n + PAIR_S - 1) / PAIR_S); }
+
+static int pair_tiles(int p)
 {
-    PairPlan q;
-    q.tiles_i = (p + PAIR_TI - 1) / PAIR_TI;
-    q.tiles_j = (p + PAIR_TJ - 1) / PAIR_TJ;
-    q.nchunks = (n + PAIR_S - 1) / PAIR_S;
-    const int tiles = q.tiles_i * q.tiles_j;
-    const int target = ctx->num_sms * 2 * 2;   // two resident CTAs per SM, two waves
-    int ns = std::max(1, std::min(q.nchunks, (target + tiles - 1) / tiles));
-    q.cps = (q.nchunks + ns - 1) / ns;
-    q.nsplit = (q.nchunks + q.cps - 1) / q.cps;
-    return q;
+    return ((p + PAIR_TI - 1) / PAIR_TI) * ((p + PAIR_TJ - 1) / PAIR_TJ);
 }
 
-static int regress_splits(const lingam_ctx *ctx, int cols, int n)
+// Sample splits of the pair and regress kernels at global step t: enough CTAs
+// in total to fill the GPU, never more splits than chunks.
+static StepSplit step_splits(const lingam_ctx *ctx, const std::vector<InstSpec> &spec, int prec,
+                             int t)
 {
-    const int target = ctx->num_sms * 4;
-    int ns = std::max(1, (target + cols - 1) / std::max(1, cols));
-    ns = std::min(ns, std::max(1, n / 1024));
-    return ns;
-}
-
-static size_t mom_elems(const lingam_ctx *ctx, int64_t n, int64_t d)
-{
-    size_t mx = (size_t)d * d * 2;
-    for (int64_t p = 2; p <= d; ++p) {
-        PairPlan q = pair_plan(ctx, (int)p, (int)n);
-        mx = std::max(mx, (size_t)q.nsplit * p * p * 2);
+    const int K = (int)spec.size();
+    StepSplit ss;
+    ss.pair_nsplit.assign(K, 1);
+    ss.pair_cps.assign(K, 1);
+    ss.reg_nsplit.assign(K, 1);
+    ss.reg_sps.assign(K, 1);
+    int64_t tiles = 0, cols = 0;
+    for (int k = 0; k < K; ++k) {
+        const int p = (int)spec[k].d - t;
+        if (p < 2 && !(t == 0 && p == 1)) continue;
+        if (p >= 2 && !step_in_fp64(prec, p)) tiles += pair_tiles(p);
+        cols += std::max(1, p - 1);
     }
-    return mx;
+    const int64_t target = (int64_t)ctx->num_sms * 4;
+    const int ns_pair = tiles > 0 ? (int)std::max<int64_t>(1, (target + tiles - 1) / tiles) : 1;
+    const int ns_reg = cols > 0 ? (int)std::max<int64_t>(1, (target + cols - 1) / cols) : 1;
+    for (int k = 0; k < K; ++k) {
+        const int64_t n = spec[k].n;
+        const int nch = pair_nchunks(n);
+        const int ns = std::max(1, std::min(ns_pair, nch));
+        const int cps = (nch + ns - 1) / ns;
+        ss.pair_cps[k] = cps;
+        ss.pair_nsplit[k] = (nch + cps - 1) / cps;
+        const int nr = std::max(1, std::min<int>(ns_reg, (int)std::max<int64_t>(1, n / 1024)));
+        const int sps = (int)((n + nr - 1) / nr);
+        ss.reg_sps[k] = sps;
+        ss.reg_nsplit[k] = (int)((n + sps - 1) / sps);
+    }
+    return ss;
 }
 
-static lingam_status make_tensor_maps(lingam_ctx *ctx, int64_t n, int64_t d)
+static lingam_status make_tensor_maps(lingam_ctx *ctx, Plan &pl)
 {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
@@ -182,86 +220,522 @@ static lingam_status make_tensor_maps(lingam_ctx *ctx, int64_t n, int64_t d)
             return fail(ctx, LINGAM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)d};
-    cuuint64_t strides[1] = {(cuuint64_t)(ctx->ldz * sizeof(float))};
+    cuuint64_t dims[2] = {(cuuint64_t)pl.ldz, (cuuint64_t)pl.zrows};
+    cuuint64_t strides[1] = {(cuuint64_t)(pl.ldz * sizeof(float))};
     cuuint32_t elem[2] = {1, 1};
     cuuint32_t boxI[2] = {(cuuint32_t)PAIR_S, (cuuint32_t)PAIR_TI};
     cuuint32_t boxJ[2] = {(cuuint32_t)PAIR_S, (cuuint32_t)PAIR_TJ};
-    CUresult r = g_encode(&ctx->tmI, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ctx->z.p, dims, strides,
+    CUresult r = g_encode(&pl.tmI, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl.zarena.p, dims, strides,
                           boxI, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (rows)");
-    r = g_encode(&ctx->tmJ, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ctx->z.p, dims, strides, boxJ, elem,
+    r = g_encode(&pl.tmJ, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl.zarena.p, dims, strides, boxJ, elem,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (cols)");
     return LINGAM_OK;
 }
 
-// Workspace for problems up to (n, d); reallocation invalidates the graph.
-static lingam_status ensure_workspace(lingam_ctx *ctx, int64_t n, int64_t d)
+static void destroy_plan(Plan &pl)
 {
-    const bool grow = n > ctx->cap_n || d > ctx->cap_d;
-    const int64_t N = grow ? std::max(n, ctx->cap_n) : ctx->cap_n;
-    const int64_t D = grow ? std::max(d, ctx->cap_d) : ctx->cap_d;
-    if (grow) {
-        ctx->ldr = roundup(N, 32);
-        ctx->ldz = roundup(N, 64);
-        const int ks = gram_ksplit((int)N, (int)D, ctx->num_sms);
-        // free first so that the new sizes fit
-        Buf *all[] = {&ctx->R, &ctx->z, &ctx->C, &ctx->Cpart, &ctx->mom, &ctx->hzpart, &ctx->M,
-                      &ctx->E, &ctx->hist, &ctx->U, &ctx->order, &ctx->state, &ctx->ref_var,
-                      &ctx->fmom, &ctx->fhz, &ctx->lcoef, &ctx->W, &ctx->piv, &ctx->cscratch};
-        for (Buf *b : all) release(*b);
-        CK(ensure(ctx->R, (size_t)D * ctx->ldr * 8));
-        CK(ensure(ctx->z, (size_t)D * ctx->ldz * 4, true));
-        CK(ensure(ctx->C, (size_t)D * D * 8));
-        CK(ensure(ctx->Cpart, (size_t)std::max(ks, 1) * D * D * 8));
-        CK(ensure(ctx->mom, mom_elems(ctx, N, D) * 8));
-        CK(ensure(ctx->hzpart, (size_t)regress_splits(ctx, 1, (int)N) * D * 2 * 8));
-        CK(ensure(ctx->M, (size_t)D * 8));
-        CK(ensure(ctx->E, (size_t)D * 8));
-        CK(ensure(ctx->hist, (size_t)D * D * 8));
-        CK(ensure(ctx->U, (size_t)2 * D * 4));
-        CK(ensure(ctx->order, (size_t)D * 4));
-        CK(ensure(ctx->state, sizeof(DevState), true));
-        CK(ensure(ctx->ref_var, (size_t)D * 8));
-        CK(ensure(ctx->fmom, (size_t)MAXC * D * 4 * 8));
-        CK(ensure(ctx->fhz, (size_t)D * 2 * 8));
-        CK(ensure(ctx->lcoef, (size_t)D * D * 8));
-        CK(ensure(ctx->W, (size_t)D * D * 8));
-        CK(ensure(ctx->piv, (size_t)D * 4));
-        CK(ensure(ctx->cscratch, (size_t)D * 4));
-        ctx->cap_n = N;
-        ctx->cap_d = D;
-        ctx->epoch++;
-        lingam_status st = make_tensor_maps(ctx, N, D);
-        if (st) return st;
+    if (pl.exec) cudaGraphExecDestroy(pl.exec);
+    pl.exec = nullptr;
+    for (cudaEvent_t e : pl.pev) cudaEventDestroy(e);
+    pl.pev.clear();
+    release(pl.arena);
+    release(pl.zarena);
+    release(pl.params);
+    pl.inst.clear();
+    pl.spec.clear();
+    pl.prec = pl.profile = pl.scores = pl.lcoef = pl.rows = -1;
+    pl.partial = false;
+}
+
+// Lay out and allocate the arenas of a batch (no graph yet).
+static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<InstSpec> &spec,
+                                 int prec, bool scores, bool lcoef, bool rows)
+{
+    const int K = (int)spec.size();
+    pl.spec = spec;
+    pl.prec = prec;
+    pl.scores = scores;
+    pl.lcoef = lcoef;
+    pl.rows = rows;
+    pl.inst.assign(K, InstDev{});
+    pl.maxd = 0;
+    int64_t maxn = 0;
+    for (auto &s : spec) {
+        pl.maxd = std::max<int>(pl.maxd, (int)s.d);
+        maxn = std::max(maxn, s.n);
     }
+    for (int k = 0; k < K; ++k) {
+        pl.inst[k].n = spec[k].n;
+        pl.inst[k].d = spec[k].d;
+        pl.inst[k].ldr = roundup(spec[k].n, 32);
+        pl.inst[k].ksplit = gram_ksplit((int)spec[k].n, (int)spec[k].d, ctx->num_sms);
+        pl.inst[k].mom_elems = (size_t)spec[k].d * spec[k].d * 2;
+    }
+    for (int t = 0; t + 1 < std::max(2, pl.maxd); ++t) {
+        StepSplit ss = step_splits(ctx, spec, prec, t);
+        for (int k = 0; k < K; ++k) {
+            const int64_t p = spec[k].d - t;
+            if (t == 0)
+                pl.inst[k].hz_elems = std::max(
+                    pl.inst[k].hz_elems, (size_t)ss.reg_nsplit[k] * (size_t)spec[k].d * 2);
+            if (p < 2) continue;
+            if (!step_in_fp64(prec, (int)p))
+                pl.inst[k].mom_elems =
+                    std::max(pl.inst[k].mom_elems, (size_t)ss.pair_nsplit[k] * p * p * 2);
+            pl.inst[k].hz_elems =
+                std::max(pl.inst[k].hz_elems, (size_t)ss.reg_nsplit[k] * (size_t)p * 2);
+        }
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (size_t)roundup((int64_t)std::max<size_t>(bytes, 8), 256);
+        return o;
+    };
+    struct Off {
+        size_t R, C, Cpart, mom, hz, M, E, hist, ref, fmom, fhz, lcoef, U, order, scratch, rows,
+            state;
+    };
+    std::vector<Off> o(K);
+    for (int k = 0; k < K; ++k) {
+        const int64_t n = spec[k].n, d = spec[k].d, ldr = pl.inst[k].ldr;
+        o[k].R = take((size_t)d * ldr * 8);
+        o[k].C = take((size_t)d * d * 8);
+        o[k].Cpart = take((size_t)pl.inst[k].ksplit * d * d * 8);
+        o[k].mom = take(pl.inst[k].mom_elems * 8);
+        o[k].hz = take(pl.inst[k].hz_elems * 8);
+        o[k].M = take((size_t)d * 8);
+        o[k].E = take((size_t)d * 8);
+        o[k].hist = scores ? take((size_t)d * d * 8) : 0;
+        o[k].ref = take((size_t)d * 8);
+        o[k].fmom = take((size_t)MAXC * d * 4 * 8);
+        o[k].fhz = take((size_t)d * 2 * 8);
+        o[k].lcoef = lcoef ? take((size_t)d * d * 8) : 0;
+        o[k].U = take((size_t)2 * d * 4);
+        o[k].order = take((size_t)d * 4);
+        o[k].scratch = take((size_t)d * 4);
+        o[k].rows = rows ? take((size_t)n * 4) : 0;
+        o[k].state = take(sizeof(DevState));
+    }
+    CK(ensure(pl.arena, off));
+    CK(cudaMemset(pl.arena.p, 0, off));
+    pl.ldz = roundup(std::max<int64_t>(maxn, PAIR_S), 64);
+    pl.zrows = 0;
+    for (int k = 0; k < K; ++k) {
+        pl.inst[k].zrow = (int)pl.zrows;
+        pl.zrows += spec[k].d;
+    }
+    CK(ensure(pl.zarena, (size_t)pl.zrows * pl.ldz * 4, true));
+    char *base = reinterpret_cast<char *>(pl.arena.p);
+    for (int k = 0; k < K; ++k) {
+        InstDev &I = pl.inst[k];
+        const int64_t d = spec[k].d;
+        I.R = reinterpret_cast<double *>(base + o[k].R);
+        I.C = reinterpret_cast<double *>(base + o[k].C);
+        I.Cpart = reinterpret_cast<double *>(base + o[k].Cpart);
+        I.mom = reinterpret_cast<double *>(base + o[k].mom);
+        I.hzpart = reinterpret_cast<double *>(base + o[k].hz);
+        I.M = reinterpret_cast<double *>(base + o[k].M);
+        I.E = reinterpret_cast<double *>(base + o[k].E);
+        I.hist = scores ? reinterpret_cast<double *>(base + o[k].hist) : nullptr;
+        I.ref_var = reinterpret_cast<double *>(base + o[k].ref);
+        I.fmom = reinterpret_cast<double *>(base + o[k].fmom);
+        I.fhz = reinterpret_cast<double *>(base + o[k].fhz);
+        I.lcoef = lcoef ? reinterpret_cast<double *>(base + o[k].lcoef) : nullptr;
+        I.U0 = reinterpret_cast<int32_t *>(base + o[k].U);
+        I.U1 = I.U0 + d;
+        I.order = reinterpret_cast<int32_t *>(base + o[k].order);
+        I.scratch = reinterpret_cast<int32_t *>(base + o[k].scratch);
+        I.rows = rows ? reinterpret_cast<int32_t *>(base + o[k].rows) : nullptr;
+        I.state = reinterpret_cast<DevState *>(base + o[k].state);
+    }
+    return make_tensor_maps(ctx, pl);
+}
+
+// Parameter arrays of every launch, gathered host-side and uploaded at once.
+struct ParamBlob {
+    std::vector<char> bytes;
+    template <typename T>
+    size_t add(const std::vector<T> &v)
+    {
+        size_t o = (size_t)roundup((int64_t)bytes.size(), 64);
+        bytes.resize(o + sizeof(T) * std::max<size_t>(v.size(), 1));
+        if (!v.empty()) memcpy(bytes.data() + o, v.data(), sizeof(T) * v.size());
+        return o;
+    }
+};
+
+enum LaunchKind {
+    K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_F64_ALL, K_SCORE, K_SELECT, K_F64_PASS, K_REFINE,
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT
+};
+
+struct Launch {
+    LaunchKind kind;
+    size_t off = 0, off2 = 0;
+    int count = 0, a = 0, b = 0, c = 0;
+};
+
+// Capture the covariance + ordering loop of the current plan into one graph.
+// stop_after_score0 captures only the first step up to its scores (and writes
+// I(i, j) of the single instance to Iout).
+static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, double *Iout)
+{
+    Plan &pl = ctx->plan;
+    const int K = (int)pl.inst.size();
+    const int prec = pl.prec;
+    const bool profile = ctx->opts.profile != 0 && !stop_after_score0;
+    cudaStream_t s = ctx->s;
+    const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
+    // Bound on |I_fp32 - I_exact| per entry, used to pick the candidates that
+    // are re-scored in FP64.  Measured against the FP64 oracle on GB300: max
+    // 5.8e-7 (accurate FP32) and 3.4e-7 (fast + compensated) over ~5e4
+    // entries; the bound keeps a margin above both.
+    const double epsI = prec == LINGAM_PREC_MIXED ? 2.0e-6 * tie : 2.5e-6 * tie;
+    const int pmode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
+    const double a1 = pmode == PAIR_FAST ? LN2_D : 1.0;
+    const double a2 = pmode == PAIR_FAST ? 1.0 / KSC : 1.0;
+    const int last_t = stop_after_score0 ? 0 : pl.maxd - 2;
+    float *zbase = ptr<float>(pl.zarena);
+
+    ParamBlob blob;
+    std::vector<Launch> L;
+    {
+        std::vector<GramParams> g(K);
+        std::vector<IotaParams> io(K);
+        int maxks = 1;
+        for (int k = 0; k < K; ++k) {
+            InstDev &I = pl.inst[k];
+            g[k] = GramParams{I.R, I.ldr, (int)I.n, (int)I.d, I.ksplit, I.Cpart, I.C, I.d, I.ref_var};
+            io[k] = IotaParams{I.U0, (int)I.d, I.state};
+            maxks = std::max(maxks, I.ksplit);
+        }
+        Launch lg_{K_GRAM};
+        lg_.off = blob.add(g);
+        lg_.count = K;
+        lg_.a = pl.maxd;
+        lg_.b = maxks;
+        L.push_back(lg_);
+        Launch li{K_IOTA};
+        li.off = blob.add(io);
+        li.count = K;
+        li.a = pl.maxd;
+        L.push_back(li);
+    }
+    std::vector<int> nsplit_hz(K, 1);
+    auto regress_params = [&](InstDev &I, int t, int p, int32_t *Uc, int32_t *Un, int sps,
+                              bool init) {
+        RegressParams P{};
+        P.R = I.R;
+        P.ldr = I.ldr;
+        P.z = zbase + (int64_t)I.zrow * pl.ldz;
+        P.ldz = pl.ldz;
+        P.C = I.C;
+        P.ldc = I.d;
+        P.U = Uc;
+        P.Unext = Un;
+        P.p = p;
+        P.n = (int)I.n;
+        P.sps = sps;
+        P.state = I.state;
+        P.order = I.order;
+        P.t = t;
+        P.hzpart = I.hzpart;
+        P.ref_var = I.ref_var;
+        P.lcoef = init ? nullptr : I.lcoef;
+        P.ldl = I.d;
+        P.status = &I.state->status;
+        return P;
+    };
+    {
+        StepSplit ss0 = step_splits(ctx, pl.spec, prec, 0);
+        std::vector<RegressParams> r(K);
+        int maxsplit = 1;
+        for (int k = 0; k < K; ++k) {
+            InstDev &I = pl.inst[k];
+            r[k] = regress_params(I, 0, (int)I.d, I.U0, I.U1, ss0.reg_sps[k], true);
+            nsplit_hz[k] = ss0.reg_nsplit[k];
+            maxsplit = std::max(maxsplit, ss0.reg_nsplit[k]);
+        }
+        Launch lr{K_REG_INIT};
+        lr.off = blob.add(r);
+        lr.count = K;
+        lr.a = pl.maxd;
+        lr.b = maxsplit;
+        L.push_back(lr);
+    }
+    if (profile) {
+        for (cudaEvent_t e : pl.pev) cudaEventDestroy(e);
+        pl.pev.assign(2 * (size_t)std::max(1, pl.maxd - 1), nullptr);
+        for (auto &e : pl.pev) CK(cudaEventCreate(&e));
+        pl.punits.assign((size_t)std::max(1, pl.maxd - 1), 0.0);
+    }
+    for (int t = 0; t <= last_t; ++t) {
+        StepSplit ss = step_splits(ctx, pl.spec, prec, t);
+        std::vector<PairParams> pp;
+        std::vector<int> prefix(1, 0);
+        std::vector<F64Params> fa, f1, f2;
+        std::vector<ScoreParams> sc;
+        std::vector<SelectParams> se;
+        std::vector<RefineSelectParams> r1, r2;
+        std::vector<RegressParams> rg;
+        std::vector<DowndateParams> dd;
+        int maxp = 0, maxcols = 0, maxsplit = 1;
+        double units = 0;
+        for (int k = 0; k < K; ++k) {
+            InstDev &I = pl.inst[k];
+            const int p = (int)I.d - t;
+            if (p < 2) continue;
+            const int n = (int)I.n;
+            maxp = std::max(maxp, p);
+            units += (double)p * (p - 1) * n;
+            int32_t *Uc = (t & 1) ? I.U1 : I.U0;
+            int32_t *Un = (t & 1) ? I.U0 : I.U1;
+            double *hist_row = I.hist ? I.hist + (size_t)t * I.d : nullptr;
+            auto f64p = [&](int mode, int pass, double *mom) {
+                F64Params F{};
+                F.R = I.R;
+                F.ldr = I.ldr;
+                F.C = I.C;
+                F.ldc = I.d;
+                F.U = Uc;
+                F.p = p;
+                F.n = n;
+                F.mode = mode;
+                F.pass = pass;
+                F.state = I.state;
+                F.mom = mom;
+                F.hz = I.fhz;
+                F.status = &I.state->status;
+                return F;
+            };
+            ScoreParams S{};
+            if (step_in_fp64(prec, p)) {
+                fa.push_back(f64p(0, 0, I.mom));
+                S.mom = I.mom;
+                S.nsplit = 1;
+                S.hz = I.fhz;
+                S.nsplit_hz = 1;
+                S.a1 = 1.0;
+                S.b1 = -LN2_D;
+                S.a2 = 1.0;
+                S.epsI = 0.0;
+            } else {
+                PairParams P{};
+                P.C = I.C;
+                P.ldc = I.d;
+                P.U = Uc;
+                P.p = p;
+                P.n = n;
+                P.tiles_i = (p + PAIR_TI - 1) / PAIR_TI;
+                P.tiles_j = (p + PAIR_TJ - 1) / PAIR_TJ;
+                P.nchunks = pair_nchunks(n);
+                P.cps = ss.pair_cps[k];
+                P.nsplit = ss.pair_nsplit[k];
+                P.mom = I.mom;
+                P.status = &I.state->status;
+                P.row0 = I.zrow;
+                pp.push_back(P);
+                prefix.push_back(prefix.back() + P.tiles_i * P.tiles_j * P.nsplit);
+                S.mom = I.mom;
+                S.nsplit = P.nsplit;
+                S.hz = I.hzpart;
+                S.nsplit_hz = nsplit_hz[k];
+                S.a1 = a1;
+                S.b1 = -LN2_D;
+                S.a2 = a2;
+                S.epsI = epsI;
+            }
+            S.p = p;
+            S.n = n;
+            S.ha1 = 1.0;
+            S.hb1 = -LN2_D;
+            S.ha2 = 1.0;
+            S.U = Uc;
+            S.M = I.M;
+            S.E = I.E;
+            S.hist = hist_row;
+            S.Iout = stop_after_score0 ? Iout : nullptr;
+            sc.push_back(S);
+            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch});
+            f1.push_back(f64p(1, 1, I.fmom));
+            f2.push_back(f64p(1, 2, I.fmom));
+            r1.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 1});
+            r2.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 2});
+            rg.push_back(regress_params(I, t, p, Uc, Un, ss.reg_sps[k], false));
+            nsplit_hz[k] = ss.reg_nsplit[k];
+            maxcols = std::max(maxcols, p - 1);
+            maxsplit = std::max(maxsplit, ss.reg_nsplit[k]);
+            dd.push_back(DowndateParams{I.C, I.d, Uc, p, I.state});
+        }
+        if (sc.empty()) break;
+        const int cnt = (int)sc.size();
+        if (profile) {
+            Launch ev{K_EVENT};
+            ev.a = 2 * t;
+            L.push_back(ev);
+            pl.punits[t] = units;
+        }
+        if (!pp.empty()) {
+            Launch l{K_PAIR};
+            l.off = blob.add(pp);
+            l.off2 = blob.add(prefix);
+            l.count = (int)pp.size();
+            l.a = prefix.back();
+            l.c = pmode;
+            L.push_back(l);
+        }
+        if (!fa.empty()) {
+            Launch l{K_F64_ALL};
+            l.off = blob.add(fa);
+            l.count = (int)fa.size();
+            l.a = std::max(1, ctx->num_sms * 8 / (int)fa.size());
+            L.push_back(l);
+        }
+        if (profile) {
+            Launch ev{K_EVENT};
+            ev.a = 2 * t + 1;
+            L.push_back(ev);
+        }
+        Launch ls{K_SCORE};
+        ls.off = blob.add(sc);
+        ls.count = cnt;
+        ls.a = maxp;
+        L.push_back(ls);
+        if (stop_after_score0) break;
+        Launch lse{K_SELECT};
+        lse.off = blob.add(se);
+        lse.count = cnt;
+        L.push_back(lse);
+        for (int pass = 1; pass <= 2; ++pass) {
+            Launch lf{K_F64_PASS};
+            lf.off = blob.add(pass == 1 ? f1 : f2);
+            lf.count = cnt;
+            lf.a = std::max(1, ctx->num_sms * 4 / cnt);
+            L.push_back(lf);
+            Launch lrs{K_REFINE};
+            lrs.off = blob.add(pass == 1 ? r1 : r2);
+            lrs.count = cnt;
+            lrs.a = maxp;
+            L.push_back(lrs);
+        }
+        Launch lr{K_REGRESS};
+        lr.off = blob.add(rg);
+        lr.count = cnt;
+        lr.a = maxcols;
+        lr.b = maxsplit;
+        L.push_back(lr);
+        Launch ld{K_DOWNDATE};
+        ld.off = blob.add(dd);
+        ld.count = cnt;
+        ld.a = maxp;
+        L.push_back(ld);
+    }
+    if (!stop_after_score0) {
+        std::vector<FinishParams> fp(K);
+        for (int k = 0; k < K; ++k) {
+            InstDev &I = pl.inst[k];
+            const int d = (int)I.d;
+            fp[k] = FinishParams{((d - 1) & 1) ? I.U1 : I.U0, I.order, d,
+                                 I.hist ? I.hist + (size_t)(d - 1) * d : nullptr};
+        }
+        Launch lf{K_FINISH};
+        lf.off = blob.add(fp);
+        lf.count = K;
+        L.push_back(lf);
+    }
+    CK(ensure(pl.params, blob.bytes.size()));
+    CK(cudaMemcpy(pl.params.p, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice));
+    char *pb = reinterpret_cast<char *>(pl.params.p);
+
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int nodes = 0;
+    cudaError_t e = cudaSuccess;
+    for (const Launch &l : L) {
+        void *P = pb + l.off;
+        switch (l.kind) {
+        case K_GRAM: e = launch_gram_b((const GramParams *)P, l.count, l.a, l.b, s); ++nodes; break;
+        case K_IOTA: e = launch_iota_b((const IotaParams *)P, l.count, l.a, s); break;
+        case K_REG_INIT:
+            e = launch_regress_b((const RegressParams *)P, l.count, true, l.a, l.b, s);
+            break;
+        case K_PAIR:
+            e = launch_pair_b(l.c, &pl.tmI, &pl.tmJ, (const PairParams *)P,
+                              (const int *)(pb + l.off2), l.count, l.a, s);
+            break;
+        case K_F64_ALL: e = launch_pairs_f64_b((const F64Params *)P, l.count, l.a, s); break;
+        case K_SCORE: e = launch_score_b((const ScoreParams *)P, l.count, l.a, s); break;
+        case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
+        case K_F64_PASS: e = launch_pairs_f64_b((const F64Params *)P, l.count, l.a, s); break;
+        case K_REFINE:
+            e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
+            break;
+        case K_REGRESS:
+            e = launch_regress_b((const RegressParams *)P, l.count, false, l.a, l.b, s);
+            break;
+        case K_DOWNDATE: e = launch_downdate_b((const DowndateParams *)P, l.count, l.a, s); break;
+        case K_FINISH: e = launch_finish_b((const FinishParams *)P, l.count, s); break;
+        case K_EVENT:
+            e = cudaEventRecordWithFlags(pl.pev[l.a], s, cudaEventRecordExternal);
+            --nodes;
+            break;
+        }
+        ++nodes;
+        if (e != cudaSuccess) break;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(ctx, e != cudaSuccess ? e : e2, "graph capture", __LINE__);
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    if (pl.exec) cudaGraphExecDestroy(pl.exec);
+    pl.exec = ex;
+    pl.nodes = nodes;
+    pl.profile = profile ? 1 : 0;
+    pl.partial = stop_after_score0;
     return LINGAM_OK;
 }
 
-// Device copy of X (staging host input); returns the device pointer.
-static lingam_status stage_input(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
-                                 int layout, size_t elem, const void **dX)
+// Make ctx->plan match the batch shape (reusing arenas and graph when equal).
+static lingam_status ensure_plan(lingam_ctx *ctx, const std::vector<InstSpec> &spec, bool scores,
+                                 bool lcoef, bool rows, bool stop_after_score0 = false,
+                                 double *Iout = nullptr)
 {
-    cudaPointerAttributes at{};
-    cudaError_t e = cudaPointerGetAttributes(&at, X);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        at.type = cudaMemoryTypeUnregistered;
-    }
-    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
-        *dX = X;
+    Plan &pl = ctx->plan;
+    const int prec = ctx->opts.precision;
+    const bool same_layout = pl.arena.p && pl.spec == spec && pl.prec == prec &&
+                             pl.scores == (int)scores && pl.lcoef == (int)lcoef &&
+                             pl.rows == (int)rows;
+    ctx->stats.graph_build_ms = 0;
+    if (same_layout && pl.exec && !pl.partial && !stop_after_score0 &&
+        pl.profile == (ctx->opts.profile ? 1 : 0))
         return LINGAM_OK;
+    CK(cudaEventRecord(ctx->g0, ctx->s));
+    if (!same_layout) {
+        destroy_plan(pl);
+        lingam_status st = layout_plan(ctx, pl, spec, prec, scores, lcoef, rows);
+        if (st) return st;
     }
-    const size_t count = layout == LINGAM_ROW_MAJOR ? (size_t)((n - 1) * ld + d)
-                                                    : (size_t)((d - 1) * ld + n);
-    CK(ensure(ctx->xstage, count * elem));
-    CK(cudaMemcpyAsync(ctx->xstage.p, X, count * elem, cudaMemcpyHostToDevice, ctx->s));
-    *dX = ctx->xstage.p;
+    lingam_status st = capture_plan(ctx, stop_after_score0, Iout);
+    if (st) return st;
+    CK(cudaEventRecord(ctx->g1, ctx->s));
+    CK(cudaEventSynchronize(ctx->g1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->g0, ctx->g1);
+    ctx->stats.graph_build_ms = ms;
     return LINGAM_OK;
 }
+
+// ---------------------------------------------------------- input side -----
 
 static lingam_status check_args(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
                                 int layout)
@@ -274,272 +748,128 @@ static lingam_status check_args(lingam_ctx *ctx, const void *X, int64_t n, int64
     if (layout == LINGAM_ROW_MAJOR && ld < d) return fail(ctx, LINGAM_ERR_ARG, "ld < d");
     if (layout == LINGAM_COL_MAJOR && ld < n) return fail(ctx, LINGAM_ERR_ARG, "ld < n");
     if (d > 6000) return fail(ctx, LINGAM_ERR_ARG, "d > 6000 is not supported");
-    if (n > (int64_t)1 << 30) return fail(ctx, LINGAM_ERR_ARG, "n > 2^30 is not supported");
+    if (n > ((int64_t)1 << 30)) return fail(ctx, LINGAM_ERR_ARG, "n > 2^30 is not supported");
     if (d > n) return fail(ctx, LINGAM_ERR_DEGENERATE, "d > n: the covariance is singular");
     return LINGAM_OK;
 }
 
-// Capture the covariance + ordering loop for (n, d) into one graph.
-static lingam_status capture_order_graph(lingam_ctx *ctx, int64_t n64, int64_t d64, bool scores,
-                                         int stop_after_score0, double *Iout, bool lcoef)
+static bool is_device_ptr(const void *p)
 {
-    const int n = (int)n64, d = (int)d64;
-    const int prec = ctx->opts.precision;
-    const bool profile = ctx->opts.profile != 0;
-    cudaStream_t s = ctx->s;
-    DevState *state = ptr<DevState>(ctx->state);
-    uint32_t *status = &state->status;
-    int32_t *U0 = ptr<int32_t>(ctx->U), *U1 = U0 + d;
-    const int ks = gram_ksplit(n, d, ctx->num_sms);
-    const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
-    // Bound on |I_fp32 - I_exact| per entry, used to pick the candidates that
-    // are re-scored in FP64.  Measured against the FP64 oracle on GB300: max
-    // 5.8e-7 (accurate FP32) and 3.4e-7 (fast + compensated) over ~5e4
-    // entries; the bound keeps a margin above both.
-    const double epsI = prec == LINGAM_PREC_FP64 ? 0.0
-                        : prec == LINGAM_PREC_MIXED ? 2.0e-6 * tie
-                                                    : 2.5e-6 * tie;
-    // Steps with at most P64 remaining variables are scored entirely in FP64:
-    // cheap there, and the scores of late steps are small enough that FP32
-    // rounding would dominate them.
-    const int P64 = 32;
-    const int pmode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
-    const double a1 = pmode == PAIR_FAST ? LN2_D : 1.0;
-    const double a2 = pmode == PAIR_FAST ? 1.0 / KSC : 1.0;
-
-    if (profile && !stop_after_score0) {
-        for (cudaEvent_t e : ctx->pev) cudaEventDestroy(e);
-        ctx->pev.assign(2 * (size_t)(d - 1), nullptr);
-        for (auto &e : ctx->pev) CK(cudaEventCreate(&e));
-        ctx->punits.assign((size_t)(d - 1), 0.0);
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
 
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    auto abort_capture = [&](cudaError_t e, const char *what, int line) {
-        cudaGraph_t g = nullptr;
-        cudaStreamEndCapture(s, &g);
-        if (g) cudaGraphDestroy(g);
-        return fail_cuda(ctx, e, what, line);
-    };
-#define CKC(expr)                                                    \
-    do {                                                             \
-        cudaError_t _e = (expr);                                     \
-        if (_e != cudaSuccess) return abort_capture(_e, #expr, __LINE__); \
-    } while (0)
-
-    CKC(launch_gram_f64(ptr<double>(ctx->R), ctx->ldr, n, d, ptr<double>(ctx->Cpart), ks,
-                        ptr<double>(ctx->C), d, ptr<double>(ctx->ref_var), s));
-    CKC(launch_iota(U0, d, state, s));
-    {
-        RegressParams P{};
-        P.R = ptr<double>(ctx->R);
-        P.ldr = ctx->ldr;
-        P.z = ptr<float>(ctx->z);
-        P.ldz = ctx->ldz;
-        P.C = ptr<double>(ctx->C);
-        P.ldc = d;
-        P.U = U0;
-        P.Unext = U1;
-        P.p = d;
-        P.n = n;
-        const int ns = regress_splits(ctx, d, n);
-        P.sps = (n + ns - 1) / ns;
-        P.state = state;
-        P.order = ptr<int32_t>(ctx->order);
-        P.t = 0;
-        P.hzpart = ptr<double>(ctx->hzpart);
-        P.ref_var = ptr<double>(ctx->ref_var);
-        P.status = status;
-        CKC(launch_regress(P, true, (n + P.sps - 1) / P.sps, s));
+// Device view of X; host data is copied into ctx->xstage at byte offset *off.
+static lingam_status stage(lingam_ctx *ctx, const void *X, size_t bytes, size_t *off,
+                           const void **dX)
+{
+    if (is_device_ptr(X)) {
+        *dX = X;
+        return LINGAM_OK;
     }
-    int nsplit_hz = regress_splits(ctx, d, n);
-    {
-        const int sps = (n + nsplit_hz - 1) / nsplit_hz;
-        nsplit_hz = (n + sps - 1) / sps;
-    }
-    int nodes = 3;
-    const int last_t = stop_after_score0 ? 0 : d - 2;
-    for (int t = 0; t <= last_t && d >= 2; ++t) {
-        const int p = d - t;
-        int32_t *Uc = (t & 1) ? U1 : U0;
-        int32_t *Un = (t & 1) ? U0 : U1;
-        double *hist_row = scores ? ptr<double>(ctx->hist) + (size_t)t * d : nullptr;
-
-        ScoreParams S{};
-        const bool step64 = prec == LINGAM_PREC_FP64 || p <= P64;
-        if (step64) {
-            F64Params F{};
-            F.R = ptr<double>(ctx->R);
-            F.ldr = ctx->ldr;
-            F.C = ptr<double>(ctx->C);
-            F.ldc = d;
-            F.U = Uc;
-            F.p = p;
-            F.n = n;
-            F.mode = 0;
-            F.state = state;
-            F.mom = ptr<double>(ctx->mom);
-            F.hz = ptr<double>(ctx->fhz);
-            F.status = status;
-            if (profile && !stop_after_score0) CKC(cudaEventRecordWithFlags(ctx->pev[2 * t], s, cudaEventRecordExternal));
-            CKC(launch_pairs_f64(F, ctx->num_sms * 8, s));
-            if (profile && !stop_after_score0) {
-                CKC(cudaEventRecordWithFlags(ctx->pev[2 * t + 1], s, cudaEventRecordExternal));
-                ctx->punits[t] = (double)p * (p - 1) * n;
-            }
-            S.mom = F.mom;
-            S.nsplit = 1;
-            S.hz = F.hz;
-            S.nsplit_hz = 1;
-            S.a1 = 1.0;
-            S.b1 = -LN2_D;
-            S.a2 = 1.0;
-        } else {
-            PairPlan q = pair_plan(ctx, p, n);
-            PairParams P{};
-            P.C = ptr<double>(ctx->C);
-            P.ldc = d;
-            P.U = Uc;
-            P.p = p;
-            P.n = n;
-            P.tiles_i = q.tiles_i;
-            P.tiles_j = q.tiles_j;
-            P.nchunks = q.nchunks;
-            P.cps = q.cps;
-            P.nsplit = q.nsplit;
-            P.mom = ptr<double>(ctx->mom);
-            P.status = status;
-            if (profile && !stop_after_score0) CKC(cudaEventRecordWithFlags(ctx->pev[2 * t], s, cudaEventRecordExternal));
-            CKC(launch_pair(pmode, &ctx->tmI, &ctx->tmJ, P, s));
-            if (profile && !stop_after_score0) {
-                CKC(cudaEventRecordWithFlags(ctx->pev[2 * t + 1], s, cudaEventRecordExternal));
-                ctx->punits[t] = (double)p * (p - 1) * n;
-            }
-            S.mom = P.mom;
-            S.nsplit = q.nsplit;
-            S.hz = ptr<double>(ctx->hzpart);
-            S.nsplit_hz = nsplit_hz;
-            S.a1 = a1;
-            S.b1 = -LN2_D;
-            S.a2 = a2;
-        }
-        S.p = p;
-        S.n = n;
-        S.ha1 = 1.0;
-        S.hb1 = -LN2_D;
-        S.ha2 = 1.0;
-        S.epsI = step64 ? 0.0 : epsI;
-        S.U = Uc;
-        S.M = ptr<double>(ctx->M);
-        S.E = ptr<double>(ctx->E);
-        S.hist = hist_row;
-        S.Iout = (stop_after_score0 ? Iout : nullptr);
-        CKC(launch_score(S, s));
-        if (stop_after_score0) {
-            nodes += 2;
-            break;
-        }
-
-        SelectParams SP{ptr<double>(ctx->M), ptr<double>(ctx->E), Uc, p, state,
-                        ptr<int32_t>(ctx->cscratch)};
-        CKC(launch_select(SP, s));
-
-        for (int pass = 1; pass <= 2; ++pass) {
-            F64Params F{};
-            F.R = ptr<double>(ctx->R);
-            F.ldr = ctx->ldr;
-            F.C = ptr<double>(ctx->C);
-            F.ldc = d;
-            F.U = Uc;
-            F.p = p;
-            F.n = n;
-            F.mode = 1;
-            F.pass = pass;
-            F.state = state;
-            F.mom = ptr<double>(ctx->fmom);
-            F.hz = ptr<double>(ctx->fhz);
-            F.status = status;
-            CKC(launch_pairs_f64(F, ctx->num_sms * 4, s));
-            RefineSelectParams RS{ptr<double>(ctx->fmom), ptr<double>(ctx->fhz), p, n, Uc, state,
-                                  hist_row, pass};
-            CKC(launch_refine_select(RS, s));
-        }
-
-        RegressParams P{};
-        P.R = ptr<double>(ctx->R);
-        P.ldr = ctx->ldr;
-        P.z = ptr<float>(ctx->z);
-        P.ldz = ctx->ldz;
-        P.C = ptr<double>(ctx->C);
-        P.ldc = d;
-        P.U = Uc;
-        P.Unext = Un;
-        P.p = p;
-        P.n = n;
-        int ns = regress_splits(ctx, p - 1, n);
-        P.sps = (n + ns - 1) / ns;
-        ns = (n + P.sps - 1) / P.sps;
-        P.state = state;
-        P.order = ptr<int32_t>(ctx->order);
-        P.t = t;
-        P.hzpart = ptr<double>(ctx->hzpart);
-        P.ref_var = ptr<double>(ctx->ref_var);
-        P.lcoef = lcoef ? ptr<double>(ctx->lcoef) : nullptr;
-        P.ldl = d;
-        P.status = status;
-        CKC(launch_regress(P, false, ns, s));
-        nsplit_hz = ns;
-        CKC(launch_downdate(ptr<double>(ctx->C), d, Uc, p, state, s));
-        nodes += 9;
-    }
-    if (!stop_after_score0) {
-        int32_t *Ulast = ((d - 1) & 1) ? U1 : U0;
-        double *hist_row = scores ? ptr<double>(ctx->hist) + (size_t)(d - 1) * d : nullptr;
-        CKC(launch_finish(Ulast, ptr<int32_t>(ctx->order), d, hist_row, s));
-        nodes += 1;
-    }
-#undef CKC
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamEndCapture(s, &g));
-    cudaGraphExec_t ex = nullptr;
-    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    CK(e);
-    if (ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
-    ctx->plan.exec = ex;
-    ctx->plan.nodes = nodes;
+    char *dst = reinterpret_cast<char *>(ctx->xstage.p) + *off;
+    CK(cudaMemcpyAsync(dst, X, bytes, cudaMemcpyHostToDevice, ctx->s));
+    *dX = dst;
+    *off += (size_t)roundup((int64_t)bytes, 256);
     return LINGAM_OK;
 }
 
-// Shared front half of every ordering call: validate, stage, pack, centre.
-static lingam_status prepare(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
-                             int layout, cudaStream_t user)
+static size_t matrix_bytes(int64_t n, int64_t d, int64_t ld, int layout, size_t elem)
 {
-    lingam_status st = check_args(ctx, X, n, d, ld, layout);
-    if (st) return st;
+    return (layout == LINGAM_ROW_MAJOR ? (size_t)((n - 1) * ld + d) : (size_t)((d - 1) * ld + n)) *
+           elem;
+}
+
+static lingam_status begin_call(lingam_ctx *ctx, cudaStream_t user)
+{
     CK(cudaSetDevice(ctx->device));
-    st = ensure_workspace(ctx, n, d);
-    if (st) return st;
     CK(cudaEventRecord(ctx->e0, user));
     CK(cudaStreamWaitEvent(ctx->s, ctx->e0, 0));
-    const int is64 = ctx->opts.precision == LINGAM_PREC_FP64;
-    const void *dX = nullptr;
-    st = stage_input(ctx, X, n, d, ld, layout, is64 ? 8 : 4, &dX);
-    if (st) return st;
-    DevState *state = ptr<DevState>(ctx->state);
-    CK(cudaMemsetAsync(&state->status, 0, sizeof(uint32_t), ctx->s));
-    CK(launch_pack(dX, is64, layout, ld, (int)n, (int)d, ptr<double>(ctx->R), ctx->ldr,
-                   &state->status, ctx->s));
-    CK(launch_center(ptr<double>(ctx->R), ctx->ldr, (int)n, (int)d, ctx->s));
     return LINGAM_OK;
 }
 
-static lingam_status finish_call(lingam_ctx *ctx, cudaStream_t user, DevState *hs)
+static lingam_status end_call(lingam_ctx *ctx, cudaStream_t user)
 {
-    CK(cudaMemcpyAsync(hs, ctx->state.p, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaEventRecord(ctx->e1, ctx->s));
     CK(cudaStreamWaitEvent(user, ctx->e1, 0));
     CK(cudaEventSynchronize(ctx->e1));
+    return LINGAM_OK;
+}
+
+// Launch the plan graph and read back orders, scores and states.
+static lingam_status run_plan(lingam_ctx *ctx, int32_t *const *orders_out, double *scores_out,
+                              std::vector<DevState> &hs)
+{
+    Plan &pl = ctx->plan;
+    const int K = (int)pl.inst.size();
+    CK(cudaEventRecord(ctx->g0, ctx->s));
+    CK(cudaGraphLaunch(pl.exec, ctx->s));
+    CK(cudaEventRecord(ctx->g1, ctx->s));
+    for (int k = 0; k < K; ++k)
+        if (orders_out && orders_out[k])
+            CK(cudaMemcpyAsync(orders_out[k], pl.inst[k].order, (size_t)pl.inst[k].d * 4,
+                               cudaMemcpyDeviceToHost, ctx->s));
+    if (scores_out && pl.inst[0].hist)
+        CK(cudaMemcpyAsync(scores_out, pl.inst[0].hist,
+                           (size_t)pl.inst[0].d * pl.inst[0].d * 8, cudaMemcpyDeviceToHost,
+                           ctx->s));
+    hs.assign(K, DevState{});
+    for (int k = 0; k < K; ++k)
+        CK(cudaMemcpyAsync(&hs[k], pl.inst[k].state, sizeof(DevState), cudaMemcpyDeviceToHost,
+                           ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    float gms = 0;
+    cudaEventElapsedTime(&gms, ctx->g0, ctx->g1);
+    lingam_stats st{};
+    st.graph_build_ms = ctx->stats.graph_build_ms;
+    st.total_ms = gms;
+    for (auto &h : hs) {
+        st.refined_steps += h.refined_steps;
+        st.genuine_ties += h.genuine_ties;
+        st.candidates_max = std::max(st.candidates_max, h.cand_max);
+        st.fp64_candidates += h.fp64_candidates;
+    }
+    st.graph_nodes = pl.nodes;
+    if (pl.profile && !pl.pev.empty()) {
+        double tot = 0, units = 0;
+        int64_t launches = 0;
+        for (size_t t = 0; t < pl.punits.size(); ++t) {
+            float ms = 0;
+            if (pl.punits[t] > 0 &&
+                cudaEventElapsedTime(&ms, pl.pev[2 * t], pl.pev[2 * t + 1]) == cudaSuccess) {
+                tot += ms;
+                units += pl.punits[t];
+                ++launches;
+            }
+        }
+        cudaGetLastError();
+        st.pair_ms = tot;
+        st.pair_launches = launches;
+        st.pair_units = units;
+    }
+    ctx->stats = st;
+    return LINGAM_OK;
+}
+
+// Fill the single-instance plan from X (validate, stage, pack, centre).
+static lingam_status load_single(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
+                                 int layout)
+{
+    InstDev &I = ctx->plan.inst[0];
+    const int is64 = ctx->opts.precision == LINGAM_PREC_FP64;
+    const size_t bytes = matrix_bytes(n, d, ld, layout, is64 ? 8 : 4);
+    if (!is_device_ptr(X)) CK(ensure(ctx->xstage, bytes));
+    size_t off = 0;
+    const void *dX = nullptr;
+    lingam_status st = stage(ctx, X, bytes, &off, &dX);
+    if (st) return st;
+    CK(cudaMemsetAsync(&I.state->status, 0, sizeof(uint32_t), ctx->s));
+    CK(launch_pack(dX, is64, layout, ld, (int)n, (int)d, I.R, I.ldr, &I.state->status, ctx->s));
+    CK(launch_center(I.R, I.ldr, (int)n, (int)d, ctx->s));
     return LINGAM_OK;
 }
 
@@ -584,8 +914,9 @@ lingam_status lingam_create(lingam_ctx **out, int device, const lingam_opts *opt
     }
     ctx->num_sms = prop.multiProcessorCount;
     if ((e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
-    if ((e = cudaEventCreate(&ctx->e0)) != cudaSuccess) return bad(e);
-    if ((e = cudaEventCreate(&ctx->e1)) != cudaSuccess) return bad(e);
+    cudaEvent_t *evs[] = {&ctx->e0, &ctx->e1, &ctx->g0, &ctx->g1};
+    for (cudaEvent_t *ev : evs)
+        if ((e = cudaEventCreate(ev)) != cudaSuccess) return bad(e);
     if ((e = pair_kernel_setup()) != cudaSuccess) return bad(e);
     *out = ctx;
     return LINGAM_OK;
@@ -596,14 +927,13 @@ lingam_status lingam_destroy(lingam_ctx *ctx)
     if (!ctx) return LINGAM_OK;
     cudaSetDevice(ctx->device);
     if (ctx->s) cudaStreamSynchronize(ctx->s);
-    if (ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
-    for (cudaEvent_t e : ctx->pev) cudaEventDestroy(e);
-    Buf *all[] = {&ctx->xstage, &ctx->R, &ctx->z, &ctx->C, &ctx->Cpart, &ctx->mom, &ctx->hzpart,
-                  &ctx->M, &ctx->E, &ctx->hist, &ctx->U, &ctx->order, &ctx->state, &ctx->ref_var,
-                  &ctx->fmom, &ctx->fhz, &ctx->lcoef, &ctx->W, &ctx->piv, &ctx->cscratch};
-    for (Buf *b : all) release(*b);
-    if (ctx->e0) cudaEventDestroy(ctx->e0);
-    if (ctx->e1) cudaEventDestroy(ctx->e1);
+    destroy_plan(ctx->plan);
+    Buf *aux[] = {&ctx->xstage, &ctx->aR, &ctx->aC, &ctx->aCpart, &ctx->aL, &ctx->aW,
+                  &ctx->aPiv, &ctx->aM, &ctx->aBt, &ctx->aRef, &ctx->aStatus};
+    for (Buf *b : aux) release(*b);
+    cudaEvent_t evs[] = {ctx->e0, ctx->e1, ctx->g0, ctx->g1};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->s) cudaStreamDestroy(ctx->s);
     delete ctx;
     return LINGAM_OK;
@@ -623,86 +953,6 @@ lingam_status lingam_set_precision(lingam_ctx *ctx, int32_t precision)
     return LINGAM_OK;
 }
 
-// Run the captured ordering loop on the data already packed in ctx->R
-// (columns 0..d-1, centred FP64).  Copies order (and scores) to the host.
-static lingam_status run_order(lingam_ctx *ctx, int64_t n, int64_t d, int32_t *order_out,
-                               double *scores_out, bool lcoef, cudaStream_t user)
-{
-    const bool scores = scores_out != nullptr;
-    Plan &pl = ctx->plan;
-    ctx->stats = lingam_stats{};
-    lingam_status st;
-    if (!pl.exec || pl.n != n || pl.d != d || pl.prec != ctx->opts.precision ||
-        pl.profile != ctx->opts.profile || pl.scores != (int)scores || pl.lcoef != (int)lcoef ||
-        pl.ws_epoch != (void *)ctx->epoch) {
-        cudaEvent_t a, b;
-        CK(cudaEventCreate(&a));
-        CK(cudaEventCreate(&b));
-        CK(cudaEventRecord(a, ctx->s));
-        st = capture_order_graph(ctx, n, d, scores, 0, nullptr, lcoef);
-        if (st) return st;
-        CK(cudaEventRecord(b, ctx->s));
-        CK(cudaEventSynchronize(b));
-        float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        ctx->stats.graph_build_ms = ms;
-        pl.n = n;
-        pl.d = d;
-        pl.prec = ctx->opts.precision;
-        pl.profile = ctx->opts.profile;
-        pl.scores = (int)scores;
-        pl.lcoef = (int)lcoef;
-        pl.ws_epoch = (void *)ctx->epoch;
-    }
-    if (scores) {
-        // NaN marks variables already ordered
-        std::vector<double> nanrow((size_t)d * d, __builtin_nan(""));
-        CK(cudaMemcpyAsync(ctx->hist.p, nanrow.data(), nanrow.size() * 8, cudaMemcpyHostToDevice,
-                           ctx->s));
-        CK(cudaStreamSynchronize(ctx->s));
-    }
-    cudaEvent_t g0, g1;
-    CK(cudaEventCreate(&g0));
-    CK(cudaEventCreate(&g1));
-    CK(cudaEventRecord(g0, ctx->s));
-    CK(cudaGraphLaunch(pl.exec, ctx->s));
-    CK(cudaEventRecord(g1, ctx->s));
-    CK(cudaMemcpyAsync(order_out, ctx->order.p, (size_t)d * 4, cudaMemcpyDeviceToHost, ctx->s));
-    if (scores)
-        CK(cudaMemcpyAsync(scores_out, ctx->hist.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost,
-                           ctx->s));
-    DevState hs{};
-    st = finish_call(ctx, user, &hs);
-    if (st) return st;
-    float gms = 0;
-    cudaEventElapsedTime(&gms, g0, g1);
-    cudaEventDestroy(g0);
-    cudaEventDestroy(g1);
-    ctx->stats.total_ms = gms;
-    ctx->stats.refined_steps = hs.refined_steps;
-    ctx->stats.genuine_ties = hs.genuine_ties;
-    ctx->stats.candidates_max = hs.cand_max;
-    ctx->stats.fp64_candidates = hs.fp64_candidates;
-    ctx->stats.graph_nodes = pl.nodes;
-    if (ctx->opts.profile && !ctx->pev.empty()) {
-        double tot = 0, units = 0;
-        for (size_t t = 0; t + 1 < (size_t)d; ++t) {
-            float ms = 0;
-            if (cudaEventElapsedTime(&ms, ctx->pev[2 * t], ctx->pev[2 * t + 1]) == cudaSuccess) {
-                tot += ms;
-                units += ctx->punits[t];
-            }
-        }
-        cudaGetLastError();
-        ctx->stats.pair_ms = tot;
-        ctx->stats.pair_launches = d - 1;
-        ctx->stats.pair_units = units;
-    }
-    return status_to_code(ctx, hs.status);
-}
-
 lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
                                   int32_t layout, int32_t *order_out, double *scores_out,
                                   lingam_stream_t stream)
@@ -710,18 +960,18 @@ lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int
     if (!ctx) return LINGAM_ERR_ARG;
     ctx->err.clear();
     if (!order_out) return fail(ctx, LINGAM_ERR_ARG, "order_out is NULL");
-    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    lingam_status st = prepare(ctx, X, n, d, ld, layout, user);
+    lingam_status st = check_args(ctx, X, n, d, ld, layout);
     if (st) return st;
-    if (d == 1) {
-        DevState hs{};
-        st = finish_call(ctx, user, &hs);
-        if (st) return st;
-        order_out[0] = 0;
-        if (scores_out) scores_out[0] = 0.0;
-        return status_to_code(ctx, hs.status);
-    }
-    return run_order(ctx, n, d, order_out, scores_out, false, user);
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = begin_call(ctx, user))) return st;
+    std::vector<InstSpec> spec{{n, d}};
+    if ((st = ensure_plan(ctx, spec, scores_out != nullptr, false, false))) return st;
+    if ((st = load_single(ctx, X, n, d, ld, layout))) return st;
+    std::vector<DevState> hs;
+    int32_t *outs[1] = {order_out};
+    if ((st = run_plan(ctx, outs, scores_out, hs))) return st;
+    if ((st = end_call(ctx, user))) return st;
+    return status_to_code(ctx, hs[0].status);
 }
 
 lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
@@ -731,30 +981,22 @@ lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, in
     if (!ctx) return LINGAM_ERR_ARG;
     ctx->err.clear();
     if (d < 2) return fail(ctx, LINGAM_ERR_ARG, "step measures need d >= 2");
+    lingam_status st = check_args(ctx, X, n, d, ld, layout);
+    if (st) return st;
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    lingam_status st = prepare(ctx, X, n, d, ld, layout, user);
-    if (st) return st;
-    Buf Ib;
-    CK(ensure(Ib, (size_t)d * d * 8));
-    CK(cudaMemsetAsync(Ib.p, 0, (size_t)d * d * 8, ctx->s));
-    // a one-off graph (not cached): covariance, standardise, step-0 scores
-    ctx->plan.exec = nullptr;   // force re-capture for the next ordering call
-    ctx->plan.n = -1;
-    st = capture_order_graph(ctx, n, d, false, 1, ptr<double>(Ib), false);
-    if (st) {
-        release(Ib);
-        return st;
-    }
-    CK(cudaGraphLaunch(ctx->plan.exec, ctx->s));
-    if (I_out) CK(cudaMemcpyAsync(I_out, Ib.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
-    if (M_out) CK(cudaMemcpyAsync(M_out, ctx->M.p, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->s));
-    DevState hs{};
-    st = finish_call(ctx, user, &hs);
-    cudaGraphExecDestroy(ctx->plan.exec);
-    ctx->plan.exec = nullptr;
-    release(Ib);
-    if (st) return st;
-    return status_to_code(ctx, hs.status);
+    if ((st = begin_call(ctx, user))) return st;
+    CK(ensure(ctx->aW, (size_t)d * d * 8));
+    CK(cudaMemsetAsync(ctx->aW.p, 0, (size_t)d * d * 8, ctx->s));
+    std::vector<InstSpec> spec{{n, d}};
+    if ((st = ensure_plan(ctx, spec, false, false, false, true, ptr<double>(ctx->aW)))) return st;
+    if ((st = load_single(ctx, X, n, d, ld, layout))) return st;
+    std::vector<DevState> hs;
+    if ((st = run_plan(ctx, nullptr, nullptr, hs))) return st;
+    if (I_out) CK(cudaMemcpyAsync(I_out, ctx->aW.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if (M_out)
+        CK(cudaMemcpyAsync(M_out, ctx->plan.inst[0].M, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    return status_to_code(ctx, hs[0].status);
 }
 
 lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
@@ -764,8 +1006,10 @@ lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, in
     if (!ctx) return LINGAM_ERR_ARG;
     ctx->err.clear();
     if (!order || !B_out) return fail(ctx, LINGAM_ERR_ARG, "order or B_out is NULL");
+    lingam_status st = check_args(ctx, X, n, d, ld, layout);
+    if (st) return st;
     {
-        std::vector<char> seen((size_t)std::max<int64_t>(d, 1), 0);
+        std::vector<char> seen((size_t)d, 0);
         for (int64_t k = 0; k < d; ++k) {
             if (order[k] < 0 || order[k] >= d || seen[order[k]])
                 return fail(ctx, LINGAM_ERR_ARG, "order is not a permutation of 0..d-1");
@@ -773,31 +1017,225 @@ lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, in
         }
     }
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    const int32_t prec_save = ctx->opts.precision;
-    ctx->opts.precision = LINGAM_PREC_FP32;   // adjacency input is FP32 data
-    lingam_status st = prepare(ctx, X, n, d, ld, layout, user);
-    ctx->opts.precision = prec_save;
-    if (st) return st;
+    if ((st = begin_call(ctx, user))) return st;
     const int di = (int)d, ni = (int)n;
-    CK(ensure(ctx->lcoef, (size_t)d * d * 8));
-    CK(ensure(ctx->W, (size_t)d * d * 8));
-    CK(ensure(ctx->piv, (size_t)d * 4));
-    CK(cudaMemcpyAsync(ctx->piv.p, order, (size_t)d * 4, cudaMemcpyHostToDevice, ctx->s));
+    const int64_t ldr = roundup(n, 32);
     const int ks = gram_ksplit(ni, di, ctx->num_sms);
-    CK(launch_gram_f64(ptr<double>(ctx->R), ctx->ldr, ni, di, ptr<double>(ctx->Cpart), ks,
-                       ptr<double>(ctx->C), d, ptr<double>(ctx->ref_var), ctx->s));
-    CK(cudaMemsetAsync(ctx->lcoef.p, 0, (size_t)d * d * 8, ctx->s));
+    CK(ensure(ctx->aR, (size_t)d * ldr * 8));
+    CK(ensure(ctx->aC, (size_t)d * d * 8));
+    CK(ensure(ctx->aCpart, (size_t)ks * d * d * 8));
+    CK(ensure(ctx->aL, (size_t)d * d * 8));
+    CK(ensure(ctx->aW, (size_t)d * d * 8));
+    CK(ensure(ctx->aPiv, (size_t)d * 4));
+    CK(ensure(ctx->aRef, (size_t)d * 8));
+    CK(ensure(ctx->aStatus, 256));
+    const size_t bytes = matrix_bytes(n, d, ld, layout, 4);
+    if (!is_device_ptr(X)) CK(ensure(ctx->xstage, bytes));
+    size_t off = 0;
+    const void *dX = nullptr;
+    if ((st = stage(ctx, X, bytes, &off, &dX))) return st;
+    uint32_t *status = ptr<uint32_t>(ctx->aStatus);
+    CK(cudaMemsetAsync(status, 0, 4, ctx->s));
+    CK(cudaMemcpyAsync(ctx->aPiv.p, order, (size_t)d * 4, cudaMemcpyHostToDevice, ctx->s));
+    CK(launch_pack(dX, 0, layout, ld, ni, di, ptr<double>(ctx->aR), ldr, status, ctx->s));
+    CK(launch_center(ptr<double>(ctx->aR), ldr, ni, di, ctx->s));
+    CK(launch_gram_f64(ptr<double>(ctx->aR), ldr, ni, di, ptr<double>(ctx->aCpart), ks,
+                       ptr<double>(ctx->aC), d, ptr<double>(ctx->aRef), ctx->s));
     for (int t = 0; t + 1 < di; ++t)
-        CK(launch_ldl_step(ptr<double>(ctx->C), d, ptr<int32_t>(ctx->piv), t, di,
-                           ptr<double>(ctx->lcoef), d, ctx->s));
-    CK(launch_unit_lower_inverse(ptr<double>(ctx->lcoef), d, ptr<int32_t>(ctx->piv), di,
-                                 ptr<double>(ctx->W), d, ctx->s));
-    CK(cudaMemcpyAsync(B_out, ctx->W.p, (size_t)d * d * 8,
+        CK(launch_ldl_step(ptr<double>(ctx->aC), d, ptr<int32_t>(ctx->aPiv), t, di,
+                           ptr<double>(ctx->aL), d, ctx->s));
+    CK(launch_unit_lower_inverse(ptr<double>(ctx->aL), d, ptr<int32_t>(ctx->aPiv), di,
+                                 ptr<double>(ctx->aW), d, ctx->s));
+    CK(cudaMemcpyAsync(B_out, ctx->aW.p, (size_t)d * d * 8,
                        B_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
-    DevState hs{};
-    st = finish_call(ctx, user, &hs);
-    if (st) return st;
-    return status_to_code(ctx, hs.status);
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    return status_to_code(ctx, hst);
+}
+
+lingam_status varlingam_fit(lingam_ctx *ctx, const void *Xt, int64_t T, int64_t d, int64_t ld,
+                            int32_t layout, int32_t lags, int32_t *order_out, double *B0_out,
+                            double *Btau_out, lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!Xt || !order_out) return fail(ctx, LINGAM_ERR_ARG, "Xt or order_out is NULL");
+    if (lags < 1 || d < 1) return fail(ctx, LINGAM_ERR_ARG, "need lags >= 1 and d >= 1");
+    if (layout != LINGAM_ROW_MAJOR && layout != LINGAM_COL_MAJOR)
+        return fail(ctx, LINGAM_ERR_ARG, "bad layout");
+    if ((layout == LINGAM_ROW_MAJOR && ld < d) || (layout == LINGAM_COL_MAJOR && ld < T))
+        return fail(ctx, LINGAM_ERR_ARG, "ld too small");
+    const int64_t n = T - lags, nz = (int64_t)lags * d, q = nz + d;
+    if (n <= q) return fail(ctx, LINGAM_ERR_DEGENERATE, "T - lags must exceed lags*d + d");
+    if (q > 6000) return fail(ctx, LINGAM_ERR_ARG, "(lags+1)*d > 6000 is not supported");
+    if (ctx->opts.precision == LINGAM_PREC_FP64)
+        return fail(ctx, LINGAM_ERR_ARG, "varlingam_fit takes FP32 data; use FP32 or MIXED");
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    lingam_status st;
+    if ((st = begin_call(ctx, user))) return st;
+    const int ni = (int)n, di = (int)d, qi = (int)q;
+    const int64_t ldr = roundup(n, 32);
+    const int ks = gram_ksplit(ni, qi, ctx->num_sms);
+    CK(ensure(ctx->aR, (size_t)q * ldr * 8));
+    CK(ensure(ctx->aC, (size_t)q * q * 8));
+    CK(ensure(ctx->aCpart, (size_t)ks * q * q * 8));
+    CK(ensure(ctx->aL, (size_t)q * q * 8));
+    CK(ensure(ctx->aW, (size_t)d * d * 8));
+    CK(ensure(ctx->aPiv, (size_t)q * 4));
+    CK(ensure(ctx->aM, (size_t)nz * d * 8));
+    CK(ensure(ctx->aBt, (size_t)lags * d * d * 8));
+    CK(ensure(ctx->aRef, (size_t)q * 8));
+    CK(ensure(ctx->aStatus, 256));
+    std::vector<InstSpec> spec{{n, d}};
+    if ((st = ensure_plan(ctx, spec, false, true, false))) return st;
+    InstDev &I = ctx->plan.inst[0];
+    const size_t bytes = matrix_bytes(T, d, ld, layout, 4);
+    if (!is_device_ptr(Xt)) CK(ensure(ctx->xstage, bytes));
+    size_t off = 0;
+    const void *dX = nullptr;
+    if ((st = stage(ctx, Xt, bytes, &off, &dX))) return st;
+    uint32_t *status = &I.state->status;
+    CK(cudaMemsetAsync(status, 0, 4, ctx->s));
+    const float *xf = reinterpret_cast<const float *>(dX);
+    double *R = ptr<double>(ctx->aR);
+    auto shifted = [&](int64_t shift) {
+        return layout == LINGAM_ROW_MAJOR ? (const void *)(xf + shift * ld) : (const void *)(xf + shift);
+    };
+    // design [x(t-1) .. x(t-lags) | x(t)], t = lags..T-1, one column per variable
+    for (int tau = 1; tau <= lags; ++tau)
+        CK(launch_pack(shifted(lags - tau), 0, layout, ld, ni, di, R + (int64_t)(tau - 1) * d * ldr,
+                       ldr, status, ctx->s));
+    CK(launch_pack(shifted(lags), 0, layout, ld, ni, di, R + nz * ldr, ldr, status, ctx->s));
+    CK(launch_center(R, ldr, ni, qi, ctx->s));     // centring = the intercept
+    CK(launch_gram_f64(R, ldr, ni, qi, ptr<double>(ctx->aCpart), ks, ptr<double>(ctx->aC), q,
+                       ptr<double>(ctx->aRef), ctx->s));
+    CK(launch_iota_plain(ptr<int32_t>(ctx->aPiv), qi, ctx->s));
+    const int nsplit = std::max(1, std::min(ni / 1024, (ctx->num_sms * 4 + qi - 1) / qi));
+    for (int t = 0; t < (int)nz; ++t) {
+        CK(launch_ldl_step(ptr<double>(ctx->aC), q, ptr<int32_t>(ctx->aPiv), t, qi,
+                           ptr<double>(ctx->aL), q, ctx->s));
+        CK(launch_regress_cols(R, ldr, ptr<double>(ctx->aL), q, t, qi, ni, nsplit, ctx->s));
+    }
+    CK(launch_var_coefficients(ptr<double>(ctx->aL), q, (int)nz, di, ptr<double>(ctx->aM), ctx->s));
+    // the innovations (columns nz..q-1) are the data of the ordering loop
+    CK(cudaMemcpy2DAsync(I.R, I.ldr * 8, R + nz * ldr, ldr * 8, (size_t)n * 8, (size_t)d,
+                         cudaMemcpyDeviceToDevice, ctx->s));
+    std::vector<DevState> hs;
+    int32_t *outs[1] = {order_out};
+    if ((st = run_plan(ctx, outs, nullptr, hs))) return st;
+    // B0 = I - L^{-1} along the order (L recorded by the regress-out steps)
+    CK(launch_unit_lower_inverse(I.lcoef, d, I.order, di, ptr<double>(ctx->aW), d, ctx->s));
+    CK(launch_var_transform(ptr<double>(ctx->aW), ptr<double>(ctx->aM), lags, di,
+                            ptr<double>(ctx->aBt), ctx->s));
+    if (B0_out)
+        CK(cudaMemcpyAsync(B0_out, ctx->aW.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if (Btau_out)
+        CK(cudaMemcpyAsync(Btau_out, ctx->aBt.p, (size_t)lags * d * d * 8, cudaMemcpyDeviceToHost,
+                           ctx->s));
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    return status_to_code(ctx, hst | hs[0].status);
+}
+
+lingam_status lingam_causal_order_batch(lingam_ctx *ctx, const lingam_instance *inst,
+                                        int32_t count, int32_t *const *orders_out,
+                                        double *const *B_out, int32_t *failed_index,
+                                        lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (failed_index) *failed_index = -1;
+    if (!inst || count < 1 || !orders_out)
+        return fail(ctx, LINGAM_ERR_ARG, "need instances, count >= 1 and orders_out");
+    if (ctx->opts.precision == LINGAM_PREC_FP64)
+        return fail(ctx, LINGAM_ERR_ARG, "batched ordering takes FP32 data; use FP32 or MIXED");
+    bool any_rows = false;
+    std::vector<InstSpec> spec(count);
+    for (int k = 0; k < count; ++k) {
+        const lingam_instance &a = inst[k];
+        char msg[160];
+        snprintf(msg, sizeof msg, "instance %d: ", k);
+        auto bad = [&](lingam_status s, const char *why) {
+            if (failed_index) *failed_index = k;
+            return fail(ctx, s, std::string(msg) + why);
+        };
+        if (!a.X || !orders_out[k]) return bad(LINGAM_ERR_ARG, "X or orders_out[k] is NULL");
+        if (a.d < 1 || a.n < 2 || a.ld < a.d) return bad(LINGAM_ERR_ARG, "bad n, d or ld");
+        if (a.d > 6000) return bad(LINGAM_ERR_ARG, "d > 6000 is not supported");
+        if (a.d > a.n) return bad(LINGAM_ERR_DEGENERATE, "d > n");
+        if (!a.rows && a.n > a.n_src) return bad(LINGAM_ERR_ARG, "n > n_src without rows");
+        if (a.rows) {
+            any_rows = true;
+            for (int64_t s = 0; s < a.n; ++s)
+                if (a.rows[s] < 0 || a.rows[s] >= a.n_src)
+                    return bad(LINGAM_ERR_ARG, "row index out of range");
+        }
+        spec[k] = InstSpec{a.n, a.d};
+    }
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    lingam_status st;
+    if ((st = begin_call(ctx, user))) return st;
+    if ((st = ensure_plan(ctx, spec, false, B_out != nullptr, any_rows))) return st;
+    // stage every distinct host source once
+    std::map<const void *, size_t> seen;
+    size_t need = 0;
+    for (int k = 0; k < count; ++k)
+        if (!is_device_ptr(inst[k].X) && !seen.count(inst[k].X)) {
+            seen[inst[k].X] = 0;
+            need += (size_t)roundup((int64_t)matrix_bytes(inst[k].n_src, inst[k].d, inst[k].ld,
+                                                          LINGAM_ROW_MAJOR, 4),
+                                    256);
+        }
+    if (need) CK(ensure(ctx->xstage, need));
+    std::map<const void *, const void *> dev;
+    size_t off = 0;
+    for (int k = 0; k < count; ++k) {
+        const lingam_instance &a = inst[k];
+        if (!dev.count(a.X)) {
+            const void *dX = nullptr;
+            if ((st = stage(ctx, a.X, matrix_bytes(a.n_src, a.d, a.ld, LINGAM_ROW_MAJOR, 4), &off,
+                            &dX)))
+                return st;
+            dev[a.X] = dX;
+        }
+        InstDev &I = ctx->plan.inst[k];
+        CK(cudaMemsetAsync(&I.state->status, 0, sizeof(uint32_t), ctx->s));
+        const int32_t *rows = nullptr;
+        if (a.rows) {
+            CK(cudaMemcpyAsync(I.rows, a.rows, (size_t)a.n * 4, cudaMemcpyHostToDevice, ctx->s));
+            rows = I.rows;
+        }
+        CK(launch_pack_gather((const float *)dev[a.X], a.ld, rows, (int)a.n, (int)a.d, I.R, I.ldr,
+                              &I.state->status, ctx->s));
+        CK(launch_center(I.R, I.ldr, (int)a.n, (int)a.d, ctx->s));
+    }
+    std::vector<DevState> hs;
+    if ((st = run_plan(ctx, orders_out, nullptr, hs))) return st;
+    if (B_out) {
+        for (int k = 0; k < count; ++k) {
+            if (!B_out[k]) continue;
+            InstDev &I = ctx->plan.inst[k];
+            CK(ensure(ctx->aW, (size_t)I.d * I.d * 8));
+            CK(launch_unit_lower_inverse(I.lcoef, I.d, I.order, (int)I.d, ptr<double>(ctx->aW),
+                                         I.d, ctx->s));
+            CK(cudaMemcpyAsync(B_out[k], ctx->aW.p, (size_t)I.d * I.d * 8, cudaMemcpyDeviceToHost,
+                               ctx->s));
+        }
+    }
+    if ((st = end_call(ctx, user))) return st;
+    for (int k = 0; k < count; ++k) {
+        lingam_status sk = status_to_code(ctx, hs[k].status);
+        if (sk) {
+            if (failed_index) *failed_index = k;
+            char msg[64];
+            snprintf(msg, sizeof msg, "instance %d: ", k);
+            ctx->err = msg + ctx->err;
+            return sk;
+        }
+    }
+    return LINGAM_OK;
 }
 
 lingam_status lingam_get_stats(const lingam_ctx *ctx, lingam_stats *out)
@@ -821,7 +1259,6 @@ lingam_status lingam_peak_probe(lingam_ctx *ctx, int32_t which, double *ops_per_
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
-    // warm-up, then timed
     CK(launch_peak_probe(which, blocks, iters / 10, ptr<unsigned long long>(cyc),
                          ptr<unsigned long long>(ns), ptr<float>(sink), ctx->s));
     CK(cudaEventRecord(a, ctx->s));
@@ -846,98 +1283,6 @@ lingam_status lingam_peak_probe(lingam_ctx *ctx, int32_t which, double *ops_per_
     release(ns);
     release(sink);
     return LINGAM_OK;
-}
-
-lingam_status varlingam_fit(lingam_ctx *ctx, const void *Xt, int64_t T, int64_t d, int64_t ld,
-                            int32_t layout, int32_t lags, int32_t *order_out, double *B0_out,
-                            double *Btau_out, lingam_stream_t stream)
-{
-    if (!ctx) return LINGAM_ERR_ARG;
-    ctx->err.clear();
-    if (!Xt || !order_out) return fail(ctx, LINGAM_ERR_ARG, "Xt or order_out is NULL");
-    if (lags < 1 || d < 1) return fail(ctx, LINGAM_ERR_ARG, "need lags >= 1 and d >= 1");
-    if (layout != LINGAM_ROW_MAJOR && layout != LINGAM_COL_MAJOR)
-        return fail(ctx, LINGAM_ERR_ARG, "bad layout");
-    if ((layout == LINGAM_ROW_MAJOR && ld < d) || (layout == LINGAM_COL_MAJOR && ld < T))
-        return fail(ctx, LINGAM_ERR_ARG, "ld too small");
-    const int64_t n = T - lags, nz = (int64_t)lags * d, q = nz + d;
-    if (n <= q) return fail(ctx, LINGAM_ERR_DEGENERATE, "T - lags must exceed lags*d + d");
-    if (q > 6000) return fail(ctx, LINGAM_ERR_ARG, "(lags+1)*d > 6000 is not supported");
-    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    CK(cudaSetDevice(ctx->device));
-    lingam_status st = ensure_workspace(ctx, n, q);
-    if (st) return st;
-    CK(cudaEventRecord(ctx->e0, user));
-    CK(cudaStreamWaitEvent(ctx->s, ctx->e0, 0));
-    const void *dX = nullptr;
-    st = stage_input(ctx, Xt, T, d, ld, layout, 4, &dX);
-    if (st) return st;
-    DevState *state = ptr<DevState>(ctx->state);
-    CK(cudaMemsetAsync(&state->status, 0, sizeof(uint32_t), ctx->s));
-    const float *xf = reinterpret_cast<const float *>(dX);
-    double *R = ptr<double>(ctx->R);
-    const int ni = (int)n, di = (int)d, qi = (int)q;
-    // design [x(t-1) .. x(t-lags) | x(t)], t = lags..T-1, one column per variable
-    auto shifted = [&](int64_t shift) {
-        return layout == LINGAM_ROW_MAJOR ? (const void *)(xf + shift * ld) : (const void *)(xf + shift);
-    };
-    for (int tau = 1; tau <= lags; ++tau)
-        CK(launch_pack(shifted(lags - tau), 0, layout, ld, ni, di, R + (int64_t)(tau - 1) * d * ctx->ldr,
-                       ctx->ldr, &state->status, ctx->s));
-    CK(launch_pack(shifted(lags), 0, layout, ld, ni, di, R + nz * ctx->ldr, ctx->ldr, &state->status,
-                   ctx->s));
-    CK(launch_center(R, ctx->ldr, ni, qi, ctx->s));     // centring = the intercept
-    const int ks = gram_ksplit(ni, qi, ctx->num_sms);
-    CK(launch_gram_f64(R, ctx->ldr, ni, qi, ptr<double>(ctx->Cpart), ks, ptr<double>(ctx->C), q,
-                       ptr<double>(ctx->ref_var), ctx->s));
-    CK(launch_iota_plain(ptr<int32_t>(ctx->piv), qi, ctx->s));
-    const int nsplit = regress_splits(ctx, qi / 2, ni);
-    for (int t = 0; t < (int)nz; ++t) {
-        CK(launch_ldl_step(ptr<double>(ctx->C), q, ptr<int32_t>(ctx->piv), t, qi,
-                           ptr<double>(ctx->lcoef), q, ctx->s));
-        CK(launch_regress_cols(R, ctx->ldr, ptr<double>(ctx->lcoef), q, t, qi, ni, nsplit, ctx->s));
-    }
-    Buf Mb, Btb;
-    CK(ensure(Mb, (size_t)nz * d * 8));
-    CK(launch_var_coefficients(ptr<double>(ctx->lcoef), q, (int)nz, di, ptr<double>(Mb), ctx->s));
-    // innovations E (columns nz..q-1) become the data of the ordering loop
-    CK(cudaMemcpyAsync(R, R + nz * ctx->ldr, (size_t)d * ctx->ldr * 8, cudaMemcpyDeviceToDevice,
-                       ctx->s));
-    if (d == 1) {
-        order_out[0] = 0;
-    } else {
-        st = run_order(ctx, n, d, order_out, nullptr, true, user);
-        if (st) {
-            release(Mb);
-            return st;
-        }
-    }
-    // B0 = I - L^{-1} along the order (L recorded by the regress-out steps)
-    CK(cudaMemcpyAsync(ctx->piv.p, order_out, (size_t)d * 4, cudaMemcpyHostToDevice, ctx->s));
-    CK(launch_unit_lower_inverse(ptr<double>(ctx->lcoef), d, ptr<int32_t>(ctx->piv), di,
-                                 ptr<double>(ctx->W), d, ctx->s));
-    CK(ensure(Btb, (size_t)lags * d * d * 8));
-    CK(launch_var_transform(ptr<double>(ctx->W), ptr<double>(Mb), lags, di, ptr<double>(Btb),
-                            ctx->s));
-    if (B0_out)
-        CK(cudaMemcpyAsync(B0_out, ctx->W.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
-    if (Btau_out)
-        CK(cudaMemcpyAsync(Btau_out, Btb.p, (size_t)lags * d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
-    DevState hs{};
-    st = finish_call(ctx, user, &hs);
-    release(Mb);
-    release(Btb);
-    if (st) return st;
-    return status_to_code(ctx, hs.status);
-}
-
-lingam_status lingam_causal_order_batch(lingam_ctx *ctx, const lingam_instance *inst,
-                                        int32_t count, int32_t *const *orders_out,
-                                        double *const *B_out, int32_t *failed_index,
-                                        lingam_stream_t stream)
-{
-    (void)inst; (void)count; (void)orders_out; (void)B_out; (void)failed_index; (void)stream;
-    return fail(ctx, LINGAM_ERR_ARG, "lingam_causal_order_batch: not built yet");
 }
 
 }  // extern "C"
