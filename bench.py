@@ -212,6 +212,50 @@ def run_ours(args, rank, world):
                            "genuine_ties": stats[-1]["genuine_ties"],
                            "graph_nodes": stats[-1]["graph_nodes"],
                            "order_head": [int(v) for v in order[:8]]}
+    # batched form: the bootstrap workload (128 resamples of d=200, n=4000 plus
+    # 64 uneven instances) in one call, against the same instances ordered one
+    # call at a time with the plain FP32 form
+    batch_info = None
+    if args.batched:
+        insts = gen.cfg5(seed=gen.SEEDS[5] + 7919 * rank)
+        batch = [(torch.from_numpy(np.ascontiguousarray(b.X)).to(f"cuda:{dev}"), b.rows)
+                 for b in insts]
+        Wb = sum(gen.residual_samples(b.X.shape[1], b.X.shape[0] if b.rows is None else len(b.rows))
+                 for b in insts)
+        with pkg.Context(dev, "mixed") as ctx:
+            for _ in range(args.warmup):
+                ctx.causal_order_batch(batch)
+            torch.cuda.synchronize()
+            bms = []
+            for _ in range(args.steps):
+                flush.add_(1.0)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.causal_order_batch(batch)
+                b.record()
+                torch.cuda.synchronize()
+                bms.append(a.elapsed_time(b))
+            bst = ctx.stats()
+        seq_ms = None
+        if args.batched_sequential:
+            with pkg.Context(dev, "fp32") as ctx:
+                rows_data = [(X if r is None else X[torch.from_numpy(r).to(X.device).long()].contiguous())
+                             for X, r in batch]
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for X in rows_data:
+                    ctx.causal_order(X)
+                torch.cuda.synchronize()
+                seq_ms = (time.perf_counter() - t0) * 1e3
+        batch_info = {"workload": "bootstrap_128x(d200,n4000)+64x(d50-400,n1000-8000)",
+                      "instances": len(insts), "residual_samples": Wb,
+                      "ms_per_call": sum(bms) / len(bms), "value": Wb / (sum(bms) / len(bms) * 1e-3),
+                      "refined_steps": bst["refined_steps"], "graph_nodes": bst["graph_nodes"],
+                      "sequential_plain_fp32_ms": seq_ms,
+                      "sequential_plain_fp32_value": (Wb / (seq_ms * 1e-3)) if seq_ms else None}
+
     region_s = time.perf_counter() - t_region0
     clk = clocks.stop()
 
@@ -305,6 +349,7 @@ def run_ours(args, rank, world):
                       "refined_steps": forms[p]["refined_steps"],
                       "genuine_ties": forms[p]["genuine_ties"],
                       "order_head": forms[p]["order_head"]} for p in args.forms},
+        "batched": batch_info,
         "timed_region_s": region_s,
     }
     print(json.dumps(line), flush=True)
@@ -323,6 +368,8 @@ def main():
     ap.add_argument("--cpu-p", type=int, default=560)
     ap.add_argument("--ref-p", type=int, default=240)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-sequential", action="store_true")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     rank = _env_int("RANK", 0)

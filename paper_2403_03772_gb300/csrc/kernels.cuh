@@ -34,6 +34,7 @@ struct PairParams {
     double *mom;          // out [nsplit][p][p][2] moment sums of entry (i, j)
     uint32_t *status;
     int row0;             // first row of this instance in the z tensor
+    const double *isd;    // [p] 1 / sqrt(C_ii) by position
 };
 
 struct F64Params {
@@ -49,6 +50,8 @@ struct F64Params {
     double *mom;          // mode 0: [p][p][2]; mode 1: [MAXC][p][4]
     double *hz;           // [p][2] variable moment sums
     uint32_t *status;
+    const float *I32;     // mode 1: [p][p] FP32-path I(i, j), or null
+    double epsI;          // bound on |I32 - I| (entries with I32 >= epsI are skipped)
 };
 
 struct ScoreParams {
@@ -64,6 +67,7 @@ struct ScoreParams {
     double *E;            // out [p] error bound of M
     double *hist;         // optional [d][d] score history (row already offset)
     double *Iout;         // optional [p][p] I(i, j) by position (step-measure calls)
+    float *I32;           // optional [p][p] I(i, j) as FP32, read by the FP64 passes
 };
 
 struct SelectParams {
@@ -103,6 +107,7 @@ struct RegressParams {
     double *lcoef;        // optional [d][d]: lcoef[i*d + m] = regression coefficient (L of LDL^T)
     int64_t ldl;
     uint32_t *status;
+    double *isd_out;      // [p'] 1 / sqrt(variance) of the next step's positions
 };
 
 struct GramParams {

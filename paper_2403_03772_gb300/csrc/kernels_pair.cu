@@ -189,31 +189,30 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
 
     float ca[WI][WJ], cb[WI][WJ];
     {
-        double a = 0.0, b = 0.0;
+        // rho and 1 - rho^2 in FP64 (cancellation near |rho| = 1), the
+        // reciprocal square root in FP32 from that exact-to-rounding value
+        float a = 0.0f, b = 0.0f;
         if (lane < WI * WJ) {
             const int pi = pi0 + lane / WJ, pj = pj0 + lane % WJ;
             if (pi < P.p && pj < P.p && pi != pj) {
                 const int oi = P.U[pi], oj = P.U[pj];
                 const int lo = min(oi, oj), hi = max(oi, oj);
-                const double cij = P.C[(int64_t)lo * P.ldc + hi];
-                const double cii = P.C[(int64_t)oi * P.ldc + oi];
-                const double cjj = P.C[(int64_t)oj * P.ldc + oj];
-                double rho = cij / (sqrt(cii) * sqrt(cjj));
-                double s2 = 1.0 - rho * rho;
-                if (!(s2 > 1e-12)) {
+                const double rho = P.C[(int64_t)lo * P.ldc + hi] * P.isd[pi] * P.isd[pj];
+                const double s2 = fma(-rho, rho, 1.0);
+                if (s2 > 1e-12) {
+                    a = rsqrtf((float)s2);
+                    b = (float)rho * a;
+                } else {
                     set_status(P.status, ST_DEGENERATE);
-                    s2 = 1.0;
-                    rho = 0.0;
+                    a = 1.0f;
                 }
-                a = 1.0 / sqrt(s2);
-                b = rho * a;
                 if (MODE == PAIR_FAST) {
-                    a *= KSC;
-                    b *= KSC;
+                    a *= (float)KSC;
+                    b *= (float)KSC;
                 }
             }
         }
-        const float fa = (float)a, fb = (float)b;
+        const float fa = a, fb = b;
 #pragma unroll
         for (int e = 0; e < WI * WJ; ++e) {
             ca[e / WJ][e % WJ] = __shfl_sync(0xffffffffu, fa, e);
@@ -418,9 +417,14 @@ __device__ __forceinline__ void pairs_f64_body(const F64Params &P)
             cidx = cbeg + (int)(q / P.p);
             a = P.state->cand[cidx];
             b = (int)(q % P.p);
-            if (a == b) {
-                if (lane == 0)
-                    for (int k = 0; k < 4; ++k) P.mom[((size_t)cidx * P.p + b) * 4 + k] = 0.0;
+            // I32(a, b) >= epsI proves I(a, b) >= 0: min(0, I)^2 = 0 exactly,
+            // so the entry needs no FP64 moments (marked by a negative sum)
+            if (a == b || (P.I32 && P.I32[(size_t)a * P.p + b] >= P.epsI)) {
+                if (lane == 0) {
+                    double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
+                    o[0] = -1.0;
+                    o[1] = o[2] = o[3] = 0.0;
+                }
                 continue;
             }
         } else {
@@ -544,6 +548,7 @@ __global__ void __launch_bounds__(256) k_score_b(const ScoreParams *__restrict__
         acc += v * v;
         if (I < eps) err += 2.0 * fabs(v) * eps + eps * eps;
         if (P.Iout) P.Iout[(size_t)i * P.p + j] = I;
+        if (P.I32) P.I32[(size_t)i * P.p + j] = (float)I;
     }
     acc = warp_sum_xor(acc);
     err = warp_sum_xor(err);
@@ -690,6 +695,7 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
         for (int j = lane; j < P.p; j += 32) {
             if (j == pc) continue;
             const double *o = P.mom + ((size_t)c * P.p + j) * 4;
+            if (o[0] < 0.0) continue;
             const double hcj = neg_entropy_part(o[0] * invn - LN2_D, o[1] * invn);
             const double hjc = neg_entropy_part(o[2] * invn - LN2_D, o[3] * invn);
             const double I = (h64[j] + hcj) - (h64[pc] + hjc);

@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
         double *o = P.hzpart + ((size_t)blockIdx.y * np + col) * 2;
         o[0] = t1;
         o[1] = t2;
+        if (blockIdx.y == 0) P.isd_out[col] = isd;
         if (!INIT && blockIdx.y == 0) {
             P.Unext[col] = i;
             if (P.lcoef) P.lcoef[(int64_t)i * P.ldl + m] = coef;
