@@ -152,6 +152,26 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------- ours --
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank orders its own dataset (weak scaling, no data-path collective)."""
+    return base + 7919 * rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank time over all ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job value: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world * steps / (max_ms * 1e-3)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -190,8 +210,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", dev))
-    seed = gen.SEEDS[3] + 7919 * rank
-    ds = gen.cfg3(seed=seed)
+    ds = gen.cfg3(seed=rank_seed(gen.SEEDS[3], rank))
     n, d = ds.X.shape
     W = gen.residual_samples(d, n)
     X = torch.from_numpy(ds.X).to(f"cuda:{dev}")
@@ -217,7 +236,7 @@ def run_ours(args, rank, world):
     # call at a time with the plain FP32 form
     batch_info = None
     if args.batched:
-        insts = gen.cfg5(seed=gen.SEEDS[5] + 7919 * rank)
+        insts = gen.cfg5(seed=rank_seed(gen.SEEDS[5], rank))
         batch = [(torch.from_numpy(np.ascontiguousarray(b.X)).to(f"cuda:{dev}"), b.rows)
                  for b in insts]
         Wb = sum(gen.residual_samples(b.X.shape[1], b.X.shape[0] if b.rows is None else len(b.rows))
@@ -261,12 +280,7 @@ def run_ours(args, rank, world):
 
     # max over ranks of the summed step time
     head = args.forms[0]
-    tot_ms = {p: sum(forms[p]["ms"]) for p in args.forms}
-    if world > 1:
-        for p in args.forms:
-            t = torch.tensor([tot_ms[p]], dtype=torch.float64, device=f"cuda:{dev}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot_ms[p] = float(t.item())
+    tot_ms = {p: max_over_ranks(sum(forms[p]["ms"]), world, f"cuda:{dev}") for p in args.forms}
 
     # e2e: the same call with a pinned host input, copies inside the timed region
     e2e = None
@@ -280,12 +294,8 @@ def run_ours(args, rank, world):
                 torch.distributed.barrier()
             ctx.causal_order(Xh)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{dev}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": W * world * args.steps / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, f"cuda:{dev}")
+        e2e = {"value": job_throughput(W, world, args.steps, e2e_s * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(d * 4)}
 
     if rank != 0:
@@ -331,7 +341,7 @@ def run_ours(args, rank, world):
                          f"1000 variables, n=10000 ({units:.3e} residual-samples, {dt:.1f} s)"}
 
     ms_per_step = tot_ms[head] / args.steps
-    value = W * world * args.steps / (tot_ms[head] * 1e-3)
+    value = job_throughput(W, world, args.steps, tot_ms[head])
     launches_per_step = f["graph_nodes"] + 2
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -344,7 +354,7 @@ def run_ours(args, rank, world):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "forms": {p: {"ms_per_step": tot_ms[p] / args.steps,
-                      "value": W * world * args.steps / (tot_ms[p] * 1e-3),
+                      "value": job_throughput(W, world, args.steps, tot_ms[p]),
                       "pair_kernel_ms_per_step": forms[p]["pair_ms"] / args.steps,
                       "refined_steps": forms[p]["refined_steps"],
                       "genuine_ties": forms[p]["genuine_ties"],

@@ -13,7 +13,6 @@ constexpr int PAIR_TI = PAIR_WI * PAIR_WGI;  // 8 rows  (variables i)
 constexpr int PAIR_TJ = PAIR_WJ * PAIR_WGJ;  // 16 cols (variables j)
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
 constexpr int PAIR_STAGES = 4;
-constexpr int PAIR_VEC = 2;
 constexpr int PAIR_THREADS = 32 * (PAIR_WGI * PAIR_WGJ + 1);
 
 // Scale folded into the fast-form residual: u~ = KSC * u makes

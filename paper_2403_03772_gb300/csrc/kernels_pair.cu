@@ -40,81 +40,90 @@ namespace lg {
 //                  accumulates u~ exp(-u^2/2).  Per-chunk partial sums are
 //                  folded into (hi, lo) pairs with TwoSum (compensated).
 
-template <int MODE>
-struct PairMath;
+// Per-sample terms of the accurate form: log cosh u + ln 2 and u exp(-u^2/2).
+__device__ __forceinline__ void accurate_terms(float u, float &t1, float &t2)
+{
+    const float au = fabsf(u);
+    t1 = au + log1pf(expf(-2.0f * au));
+    t2 = u * expf(-0.5f * u * u);
+}
 
-template <>
-struct PairMath<PAIR_ACCURATE> {
-    __device__ __forceinline__ static void eval(float u, float &t1, float &t2)
-    {
-        float au = fabsf(u);
-        t1 = au + log1pf(expf(-2.0f * au));
-        t2 = u * expf(-0.5f * u * u);
-    }
-};
+// Constants of the fast form: c2 = -2 log2(e) / k, c3 = log2(e) / k.
+constexpr float FAST_C2 = (float)(-2.0 * LOG2E_D / KSC);
+constexpr float FAST_C3 = (float)(LOG2E_D / KSC);
 
-template <>
-struct PairMath<PAIR_FAST> {
-    // c2 = -2 log2(e) / k, c3 = log2(e) / k
-    static constexpr float C2 = (float)(-2.0 * LOG2E_D / KSC);
-    static constexpr float C3 = (float)(LOG2E_D / KSC);
-    __device__ __forceinline__ static void eval(float u, float &t1, float &t2)
-    {
-        float e = ex2_approx(-(u * u));
-        t2 = u * e;
-        float au = fabsf(u);
-        float y = ex2_approx(au * C2);
-        float l = lg2_approx(1.0f + y);
-        t1 = fmaf(au, C3, l);
-    }
-};
-
-template <int MODE, bool TAIL, int WI, int WJ, int S, int VEC>
+// One chunk of S samples for the WI x WJ pairs of a warp: lane l takes the
+// four consecutive samples 128 it + 4 l .. + 3 (one 16-byte shared load per
+// column).  Fast form: sum_s log2(2 cosh u_s) = log2(e)/k sum |u~_s| +
+// sum_s log2(1 + y_s); the second sum is taken as log2 of the product of
+// the four (1 + y_s) in (1, 16], one MUFU lg2 per four samples instead of
+// four (the logarithm of a product is the sum of the logarithms).
+template <int MODE, bool TAIL, int WI, int WJ, int S>
 __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
                                            const float *__restrict__ cols,
                                            const float (&ca)[WI][WJ], const float (&cb)[WI][WJ],
                                            float (&a1)[WI][WJ], float (&a2)[WI][WJ], int lane,
                                            int valid)
 {
-    static_assert(VEC == 2, "VEC");
 #pragma unroll 1
-    for (int it = 0; it < S / (32 * VEC); ++it) {
-        const int s = it * 32 * VEC + lane * VEC;
-        float2 zi[WI], zj[WJ];
+    for (int it = 0; it < S / 128; ++it) {
+        const int s = it * 128 + lane * 4;
+        float4 zi[WI], zj[WJ];
 #pragma unroll
-        for (int r = 0; r < WI; ++r) zi[r] = *reinterpret_cast<const float2 *>(rows + r * S + s);
+        for (int r = 0; r < WI; ++r) zi[r] = *reinterpret_cast<const float4 *>(rows + r * S + s);
 #pragma unroll
-        for (int c = 0; c < WJ; ++c) zj[c] = *reinterpret_cast<const float2 *>(cols + c * S + s);
-        const bool ok0 = !TAIL || (s < valid);
-        const bool ok1 = !TAIL || (s + 1 < valid);
+        for (int c = 0; c < WJ; ++c) zj[c] = *reinterpret_cast<const float4 *>(cols + c * S + s);
+        bool ok[4] = {true, true, true, true};
+        if (TAIL) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ok[v] = (s + v) < valid;
+        }
 #pragma unroll
         for (int r = 0; r < WI; ++r) {
+            const float zr[4] = {zi[r].x, zi[r].y, zi[r].z, zi[r].w};
 #pragma unroll
             for (int c = 0; c < WJ; ++c) {
-                float t1, t2;
-                float u0 = fmaf(ca[r][c], zi[r].x, -(cb[r][c] * zj[c].x));
-                PairMath<MODE>::eval(u0, t1, t2);
-                if (TAIL) {
-                    t1 = ok0 ? t1 : 0.0f;
-                    t2 = ok0 ? t2 : 0.0f;
+                const float zc[4] = {zj[c].x, zj[c].y, zj[c].z, zj[c].w};
+                if (MODE == PAIR_FAST) {
+                    float q[4], au[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float u = fmaf(ca[r][c], zr[v], -(cb[r][c] * zc[v]));
+                        const float e = ex2_approx(-(u * u));        // exp(-u^2/2)
+                        float g = u * e;
+                        float a = fabsf(u);
+                        float y = ex2_approx(a * FAST_C2);           // exp(-2|u|)
+                        if (TAIL && !ok[v]) {
+                            g = 0.0f;
+                            a = 0.0f;
+                            y = 0.0f;
+                        }
+                        a2[r][c] += g;
+                        q[v] = 1.0f + y;
+                        au[v] = a;
+                    }
+                    const float prod = (q[0] * q[1]) * (q[2] * q[3]);
+                    const float asum = (au[0] + au[1]) + (au[2] + au[3]);
+                    a1[r][c] += fmaf(asum, FAST_C3, lg2_approx(prod));
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float u = fmaf(ca[r][c], zr[v], -(cb[r][c] * zc[v]));
+                        float t1, t2;
+                        accurate_terms(u, t1, t2);
+                        if (TAIL && !ok[v]) {
+                            t1 = 0.0f;
+                            t2 = 0.0f;
+                        }
+                        a1[r][c] += t1;
+                        a2[r][c] += t2;
+                    }
                 }
-                a1[r][c] += t1;
-                a2[r][c] += t2;
-                float u1 = fmaf(ca[r][c], zi[r].y, -(cb[r][c] * zj[c].y));
-                PairMath<MODE>::eval(u1, t1, t2);
-                if (TAIL) {
-                    t1 = ok1 ? t1 : 0.0f;
-                    t2 = ok1 ? t2 : 0.0f;
-                }
-                a1[r][c] += t1;
-                a2[r][c] += t2;
             }
         }
     }
 }
 
-// The compensated fast form keeps three FP32 words per accumulator; it runs
-// one CTA per SM with the register budget that allows, the accurate form two.
 template <int MODE>
 __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtensorMap *tmJ,
                                            const PairParams &P, const int ti, const int tj,
@@ -225,6 +234,12 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     for (int r = 0; r < WI; ++r)
 #pragma unroll
         for (int c = 0; c < WJ; ++c) s1[r][c] = s2[r][c] = e1[r][c] = e2[r][c] = 0.0f;
+    float a1[WI][WJ], a2[WI][WJ];    // chunk partial sums (compensated form)
+#pragma unroll
+    for (int r = 0; r < WI; ++r)
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) a1[r][c] = a2[r][c] = 0.0f;
+    constexpr int FOLD = 4;
 
     for (int k = 0; k < nck; ++k) {
         const int st = k % STAGES;
@@ -238,32 +253,31 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
         const float *cols = buf + st * STAGE_FLOATS + TI * S + cj0 * S;
         const int valid = min(S, P.n - (c0 + k) * S);
         if (COMP) {
-            float a1[WI][WJ], a2[WI][WJ];
-#pragma unroll
-            for (int r = 0; r < WI; ++r)
-#pragma unroll
-                for (int c = 0; c < WJ; ++c) a1[r][c] = a2[r][c] = 0.0f;
             if (valid == S)
-                pair_chunk<MODE, false, WI, WJ, S, PAIR_VEC>(rows, cols, ca, cb, a1, a2, lane, valid);
+                pair_chunk<MODE, false, WI, WJ, S>(rows, cols, ca, cb, a1, a2, lane, valid);
             else
-                pair_chunk<MODE, true, WI, WJ, S, PAIR_VEC>(rows, cols, ca, cb, a1, a2, lane, valid);
+                pair_chunk<MODE, true, WI, WJ, S>(rows, cols, ca, cb, a1, a2, lane, valid);
+            // fold the partial sums of FOLD chunks into (hi, lo) pairs
+            if ((k % FOLD) == FOLD - 1 || k == nck - 1) {
 #pragma unroll
-            for (int r = 0; r < WI; ++r)
+                for (int r = 0; r < WI; ++r)
 #pragma unroll
-                for (int c = 0; c < WJ; ++c) {
-                    float t, err;
-                    two_sum(s1[r][c], a1[r][c], t, err);
-                    s1[r][c] = t;
-                    e1[r][c] += err;
-                    two_sum(s2[r][c], a2[r][c], t, err);
-                    s2[r][c] = t;
-                    e2[r][c] += err;
-                }
+                    for (int c = 0; c < WJ; ++c) {
+                        float t, err;
+                        two_sum(s1[r][c], a1[r][c], t, err);
+                        s1[r][c] = t;
+                        e1[r][c] += err;
+                        two_sum(s2[r][c], a2[r][c], t, err);
+                        s2[r][c] = t;
+                        e2[r][c] += err;
+                        a1[r][c] = a2[r][c] = 0.0f;
+                    }
+            }
         } else {
             if (valid == S)
-                pair_chunk<MODE, false, WI, WJ, S, PAIR_VEC>(rows, cols, ca, cb, s1, s2, lane, valid);
+                pair_chunk<MODE, false, WI, WJ, S>(rows, cols, ca, cb, s1, s2, lane, valid);
             else
-                pair_chunk<MODE, true, WI, WJ, S, PAIR_VEC>(rows, cols, ca, cb, s1, s2, lane, valid);
+                pair_chunk<MODE, true, WI, WJ, S>(rows, cols, ca, cb, s1, s2, lane, valid);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -309,9 +323,9 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
 // One launch covers the tiles of every instance in the batch: prefix[k] is the
 // first CTA of instance k (tiles_i * tiles_j * nsplit CTAs each).
 template <int MODE>
-__global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
-    k_pair_moments_b(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
-                     const PairParams *__restrict__ Ps, const int *__restrict__ prefix, int count)
+__device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUtensorMap *tmJ,
+                                              const PairParams *__restrict__ Ps,
+                                              const int *__restrict__ prefix, int count)
 {
     int lo = 0, hi = count - 1;
     const int b = blockIdx.x;
@@ -324,7 +338,25 @@ __global__ void __launch_bounds__(PAIR_THREADS, MODE == PAIR_FAST ? 1 : 2)
     const int local = b - prefix[lo];
     const int tiles = P.tiles_i * P.tiles_j;
     const int split = local / tiles, tile = local % tiles;
-    pair_block<MODE>(&tmI, &tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
+    pair_block<MODE>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
+}
+
+// Register budgets: the compensated fast form keeps three FP32 words per
+// accumulator and runs one CTA (9 warps) per SM with up to 224 registers; the
+// accurate form runs two CTAs per SM with up to 112.
+__global__ void __maxnreg__(224)
+    k_pair_fast_b(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
+                  const PairParams *__restrict__ Ps, const int *__restrict__ prefix, int count)
+{
+    pair_dispatch<PAIR_FAST>(&tmI, &tmJ, Ps, prefix, count);
+}
+
+__global__ void __maxnreg__(112)
+    k_pair_accurate_b(const __grid_constant__ CUtensorMap tmI,
+                      const __grid_constant__ CUtensorMap tmJ, const PairParams *__restrict__ Ps,
+                      const int *__restrict__ prefix, int count)
+{
+    pair_dispatch<PAIR_ACCURATE>(&tmI, &tmJ, Ps, prefix, count);
 }
 
 static size_t pair_smem_bytes()
@@ -334,12 +366,11 @@ static size_t pair_smem_bytes()
 
 cudaError_t pair_kernel_setup()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_moments_b<PAIR_ACCURATE>,
+    cudaError_t e = cudaFuncSetAttribute(k_pair_accurate_b,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pair_smem_bytes());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pair_moments_b<PAIR_FAST>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_pair_fast_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pair_smem_bytes());
 }
 
@@ -349,11 +380,11 @@ cudaError_t launch_pair_b(int mode, const CUtensorMap *tmI, const CUtensorMap *t
 {
     if (total_ctas <= 0 || count <= 0) return cudaSuccess;
     if (mode == PAIR_FAST)
-        k_pair_moments_b<PAIR_FAST><<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(
-            *tmI, *tmJ, P, prefix, count);
+        k_pair_fast_b<<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(*tmI, *tmJ, P, prefix,
+                                                                         count);
     else
-        k_pair_moments_b<PAIR_ACCURATE><<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(
-            *tmI, *tmJ, P, prefix, count);
+        k_pair_accurate_b<<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(*tmI, *tmJ, P,
+                                                                             prefix, count);
     return cudaGetLastError();
 }
 
