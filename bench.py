@@ -226,6 +226,10 @@ def run_ours(args, rank, world):
             pair_ms = sum(s["pair_ms"] for s in stats)
             pair_units = sum(s["pair_units"] for s in stats)
             forms[prec] = {"ms": ms, "pair_ms": pair_ms, "pair_units": pair_units,
+                           "phase_ms_per_step": {
+                               k: sum(s[k] for s in stats) / len(stats)
+                               for k in ("pair_ms", "score_ms", "refine_ms", "regress_ms")},
+                           "fp64_candidates": stats[-1]["fp64_candidates"],
                            "pair_launches": sum(s["pair_launches"] for s in stats),
                            "refined_steps": stats[-1]["refined_steps"],
                            "genuine_ties": stats[-1]["genuine_ties"],
@@ -357,6 +361,8 @@ def run_ours(args, rank, world):
                       "value": job_throughput(W, world, args.steps, tot_ms[p]),
                       "pair_kernel_ms_per_step": forms[p]["pair_ms"] / args.steps,
                       "refined_steps": forms[p]["refined_steps"],
+                      "fp64_candidates": forms[p]["fp64_candidates"],
+                      "phase_ms_per_step": forms[p]["phase_ms_per_step"],
                       "genuine_ties": forms[p]["genuine_ties"],
                       "order_head": forms[p]["order_head"]} for p in args.forms},
         "batched": batch_info,

@@ -178,6 +178,9 @@ typedef struct {
     double graph_build_ms;    /* capture + instantiate time (0 if cached) */
     int32_t fp64_candidates;  /* candidates re-scored in FP64 over the run */
     int32_t reserved[5];
+    double score_ms;          /* summed score + select time (profile=1) */
+    double refine_ms;         /* summed FP64 re-score passes (profile=1) */
+    double regress_ms;        /* summed regress-out + downdate (profile=1) */
 } lingam_stats;
 
 lingam_status lingam_get_stats(const lingam_ctx *ctx, lingam_stats *out);

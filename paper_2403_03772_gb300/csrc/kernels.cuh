@@ -181,6 +181,7 @@ cudaError_t launch_var_coefficients(const double *L, int64_t ldl, int nz, int d,
 cudaError_t launch_var_transform(const double *B0, const double *M, int lags, int d, double *Bt,
                                  cudaStream_t s);
 cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s);
+cudaError_t launch_fill_nan(double *p, size_t count, cudaStream_t s);
 
 cudaError_t launch_peak_probe(int which, int blocks, int iters, unsigned long long *cycles,
                               unsigned long long *ns, float *sink, cudaStream_t s);

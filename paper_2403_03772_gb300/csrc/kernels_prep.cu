@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace lg {
@@ -586,6 +588,23 @@ __global__ void k_iota_plain(int32_t *v, int q)
 cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s)
 {
     k_iota_plain<<<(q + 255) / 256, 256, 0, s>>>(v, q);
+    return cudaGetLastError();
+}
+
+// Fill with NaN (the score history marks variables already ordered with NaN).
+__global__ void k_fill_nan(double *p, size_t count)
+{
+    const double nanv = __longlong_as_double(0x7ff8000000000000ull);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = nanv;
+}
+
+cudaError_t launch_fill_nan(double *p, size_t count, cudaStream_t s)
+{
+    if (!p || count == 0) return cudaSuccess;
+    const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
+    k_fill_nan<<<blocks, 256, 0, s>>>(p, count);
     return cudaGetLastError();
 }
 

@@ -377,8 +377,12 @@ struct ParamBlob {
 
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_F64_ALL, K_SCORE, K_SELECT, K_F64_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN
 };
+
+// Timing events per ordering step when profiling: before the pair moments,
+// after them, after score + select, after the FP64 passes, after regress-out.
+constexpr int EV_PER_STEP = 5;
 
 struct Launch {
     LaunchKind kind;
@@ -411,6 +415,12 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
 
     ParamBlob blob;
     std::vector<Launch> L;
+    for (int k = 0; k < K; ++k)
+        if (pl.inst[k].hist) {
+            Launch lf{K_FILL_NAN};
+            lf.c = k;
+            L.push_back(lf);
+        }
     {
         std::vector<GramParams> g(K);
         std::vector<IotaParams> io(K);
@@ -478,7 +488,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     }
     if (profile) {
         for (cudaEvent_t e : pl.pev) cudaEventDestroy(e);
-        pl.pev.assign(2 * (size_t)std::max(1, pl.maxd - 1), nullptr);
+        pl.pev.assign(EV_PER_STEP * (size_t)std::max(1, pl.maxd - 1), nullptr);
         for (auto &e : pl.pev) CK(cudaEventCreate(&e));
         pl.punits.assign((size_t)std::max(1, pl.maxd - 1), 0.0);
     }
@@ -589,7 +599,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         const int cnt = (int)sc.size();
         if (profile) {
             Launch ev{K_EVENT};
-            ev.a = 2 * t;
+            ev.a = EV_PER_STEP * t;
             L.push_back(ev);
             pl.punits[t] = units;
         }
@@ -611,7 +621,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         }
         if (profile) {
             Launch ev{K_EVENT};
-            ev.a = 2 * t + 1;
+            ev.a = EV_PER_STEP * t + 1;
             L.push_back(ev);
         }
         Launch ls{K_SCORE};
@@ -624,6 +634,11 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         lse.off = blob.add(se);
         lse.count = cnt;
         L.push_back(lse);
+        if (profile) {
+            Launch ev{K_EVENT};
+            ev.a = EV_PER_STEP * t + 2;
+            L.push_back(ev);
+        }
         for (int pass = 1; pass <= 2; ++pass) {
             Launch lf{K_F64_PASS};
             lf.off = blob.add(pass == 1 ? f1 : f2);
@@ -636,6 +651,11 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             lrs.a = maxp;
             L.push_back(lrs);
         }
+        if (profile) {
+            Launch ev{K_EVENT};
+            ev.a = EV_PER_STEP * t + 3;
+            L.push_back(ev);
+        }
         Launch lr{K_REGRESS};
         lr.off = blob.add(rg);
         lr.count = cnt;
@@ -647,6 +667,11 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         ld.count = cnt;
         ld.a = maxp;
         L.push_back(ld);
+        if (profile) {
+            Launch ev{K_EVENT};
+            ev.a = EV_PER_STEP * t + 4;
+            L.push_back(ev);
+        }
     }
     if (!stop_after_score0) {
         std::vector<FinishParams> fp(K);
@@ -695,6 +720,9 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         case K_EVENT:
             e = cudaEventRecordWithFlags(pl.pev[l.a], s, cudaEventRecordExternal);
             --nodes;
+            break;
+        case K_FILL_NAN:
+            e = launch_fill_nan(pl.inst[l.c].hist, (size_t)pl.inst[l.c].d * pl.inst[l.c].d, s);
             break;
         }
         ++nodes;
@@ -848,19 +876,24 @@ static lingam_status run_plan(lingam_ctx *ctx, int32_t *const *orders_out, doubl
     }
     st.graph_nodes = pl.nodes;
     if (pl.profile && !pl.pev.empty()) {
-        double tot = 0, units = 0;
+        double ph[4] = {0, 0, 0, 0}, units = 0;
         int64_t launches = 0;
         for (size_t t = 0; t < pl.punits.size(); ++t) {
-            float ms = 0;
-            if (pl.punits[t] > 0 &&
-                cudaEventElapsedTime(&ms, pl.pev[2 * t], pl.pev[2 * t + 1]) == cudaSuccess) {
-                tot += ms;
-                units += pl.punits[t];
-                ++launches;
+            if (pl.punits[t] <= 0) continue;
+            for (int k = 0; k < 4; ++k) {
+                float ms = 0;
+                if (cudaEventElapsedTime(&ms, pl.pev[EV_PER_STEP * t + k],
+                                         pl.pev[EV_PER_STEP * t + k + 1]) == cudaSuccess)
+                    ph[k] += ms;
             }
+            units += pl.punits[t];
+            ++launches;
         }
         cudaGetLastError();
-        st.pair_ms = tot;
+        st.pair_ms = ph[0];
+        st.score_ms = ph[1];
+        st.refine_ms = ph[2];
+        st.regress_ms = ph[3];
         st.pair_launches = launches;
         st.pair_units = units;
     }

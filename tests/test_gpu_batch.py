@@ -25,8 +25,9 @@ def _small_batch():
     insts = []
     for r in range(5):
         insts.append((base.X, st.integers(0, base.n - 1, base.n).astype(np.int32)))
-    for k, (n, d) in enumerate([(700, 9), (2100, 33), (1200, 17), (3000, 40), (900, 2), (500, 1)]):
+    for k, (n, d) in enumerate([(700, 9), (2100, 33), (1200, 17), (3000, 40), (900, 2)]):
         insts.append((gen.cfg2(seed=600 + k, n=n, d=d).X, None))
+    insts.append((gen.Stream(610).laplace(1.0, 500).reshape(500, 1).astype(np.float32), None))
     return insts
 
 
