@@ -195,6 +195,37 @@ lingam_status lingam_get_stats(const lingam_ctx *ctx, lingam_stats *out);
 lingam_status lingam_peak_probe(lingam_ctx *ctx, int32_t which, double *ops_per_s,
                                 double *sm_clock_mhz);
 
+/*
+ * First-step scores for callers that must not allocate device memory.
+ *
+ * (The paper has no counterpart: this is a packaging variant of the FP64
+ * pair-moment kernel for constrained callers.)  Every other entry point needs
+ * a context, and lingam_create allocates device workspace.  Some callers
+ * cannot do that while they run: code invoked from inside a device-memory
+ * allocator or pool (cudaMalloc would re-enter it), plugins of applications
+ * that reserve nearly all device memory up front, and services that forbid
+ * cudaMalloc/cudaFree on their serving path because those calls can
+ * synchronise the device.  This call needs no context and allocates nothing:
+ * its scratch is a fixed ~66 KB array built into the library, present on
+ * every GPU that loads the library until the process exits.
+ *
+ *   X      device pointer, FP64, row-major [n][ld], ld >= d (read only).
+ *   M_out  device pointer, double[d]: M(i) = -sum_j min(0, I(i,j))^2 of the
+ *          first ordering step, computed in FP64 (what lingam_step_measures
+ *          returns in M_out).
+ *   stream the call is ordered on it and synchronises it before returning.
+ * Limits: 2 <= d <= 64 (the scratch array's size), 2 <= n <= 2^30; anything
+ * else returns LINGAM_ERR_ARG without touching the GPU.  NaN/Inf input gives
+ * LINGAM_ERR_NONFINITE, a zero variance or |rho| = 1 LINGAM_ERR_DEGENERATE.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * on one GPU share the array (the call clears what must start at zero), so
+ * calls that overlap in time on the same GPU race and must be serialised by
+ * the caller.
+ */
+lingam_status lingam_step_scores_noalloc(const double *X, int64_t n, int64_t d, int64_t ld,
+                                         double *M_out, lingam_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,7 @@ SIGNATURES = {
     "lingam_step_measures": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _P]),
     "lingam_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "lingam_peak_probe": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "lingam_step_scores_noalloc": (_I32, [_P, _I64, _I64, _I64, _P, _P]),
 }
 
 

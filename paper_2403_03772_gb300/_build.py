@@ -22,7 +22,7 @@ LIBNAME = "liblingam_gb300.so"
 LIBPATH = os.path.join(LIBDIR, LIBNAME)
 
 SOURCES = ["kernels_pair.cu", "kernels_prep.cu", "kernels_batch.cu", "kernels_gram_tc.cu",
-           "lingam_abi.cu"]
+           "lingam_abi.cu", "lingam_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
