@@ -342,16 +342,17 @@ __device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUte
 }
 
 // Register budgets: the compensated fast form keeps three FP32 words per
-// accumulator and runs one CTA (9 warps) per SM with up to 224 registers; the
-// accurate form runs two CTAs per SM with up to 112.
-__global__ void __maxnreg__(224)
+// accumulator and runs one CTA (9 warps) per SM with up to 216 registers
+// (216 x 288 threads leaves headroom under the 64K register file); the
+// accurate form runs two CTAs per SM with up to 104.
+__global__ void __maxnreg__(216)
     k_pair_fast_b(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
                   const PairParams *__restrict__ Ps, const int *__restrict__ prefix, int count)
 {
     pair_dispatch<PAIR_FAST>(&tmI, &tmJ, Ps, prefix, count);
 }
 
-__global__ void __maxnreg__(112)
+__global__ void __maxnreg__(104)
     k_pair_accurate_b(const __grid_constant__ CUtensorMap tmI,
                       const __grid_constant__ CUtensorMap tmJ, const PairParams *__restrict__ Ps,
                       const int *__restrict__ prefix, int count)
