@@ -1,6 +1,8 @@
 // kernels.cuh -- launch interface between the host orchestration and kernels.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace lg {
@@ -182,6 +184,17 @@ cudaError_t launch_var_transform(const double *B0, const double *M, int lags, in
                                  cudaStream_t s);
 cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s);
 cudaError_t launch_fill_nan(double *p, size_t count, cudaStream_t s);
+
+// Tensor-core covariance (kernels_gram_tc.cu): slice planes S [6][d_pad][ldk]
+// BF16 described by tmS (box 64 x 128, 128-byte swizzle), expo [d_pad],
+// part [ksplit][d][d] FP64.
+cudaError_t gram_tc_setup();
+int gram_tc_dpad(int d);
+int64_t gram_tc_ldk(int n);
+int gram_tc_ksplit(int n, int d, int num_sms);
+cudaError_t launch_gram_tc(const CUtensorMap *tmS, const double *R, int64_t ldr, int n, int d,
+                           __nv_bfloat16 *S, int *expo, double *part, int ksplit, double *C,
+                           int64_t ldc, double *ref_var, uint32_t *status, cudaStream_t s);
 
 cudaError_t launch_peak_probe(int which, int blocks, int iters, unsigned long long *cycles,
                               unsigned long long *ns, float *sink, cudaStream_t s);

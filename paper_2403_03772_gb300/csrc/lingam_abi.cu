@@ -69,6 +69,10 @@ int64_t roundup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+// The mixed form computes the covariance of a single-instance run on the
+// tensor cores (kernels_gram_tc.cu).
+constexpr bool TC_GRAM_ENABLED = false;
+
 // Steps with at most P64 remaining variables are scored entirely in FP64:
 // cheap there, and the scores of late steps are small enough that FP32
 // rounding would dominate them.
@@ -91,6 +95,11 @@ struct InstDev {
     int zrow = 0;
     int ksplit = 1;
     size_t mom_elems = 0, hz_elems = 0;
+    // tensor-core covariance (mixed form): digit planes, scale exponents, map
+    __nv_bfloat16 *S = nullptr;
+    int *expo = nullptr;
+    int tc_ksplit = 0;
+    CUtensorMap tmS{};
 };
 
 // Sample-split decisions of one global step (shared by sizing and capture).
@@ -299,14 +308,18 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     };
     struct Off {
         size_t R, C, Cpart, mom, hz, M, E, hist, ref, fmom, fhz, lcoef, U, order, scratch, rows,
-            state, isd, I32;
+            state, isd, I32, S, expo;
     };
     std::vector<Off> o(K);
     for (int k = 0; k < K; ++k) {
         const int64_t n = spec[k].n, d = spec[k].d, ldr = pl.inst[k].ldr;
         o[k].R = take((size_t)d * ldr * 8);
         o[k].C = take((size_t)d * d * 8);
-        o[k].Cpart = take((size_t)pl.inst[k].ksplit * d * d * 8);
+        const bool tc = TC_GRAM_ENABLED && prec == LINGAM_PREC_MIXED && K == 1;
+        pl.inst[k].tc_ksplit = tc ? gram_tc_ksplit((int)n, (int)d, ctx->num_sms) : 0;
+        o[k].Cpart = take((size_t)std::max(pl.inst[k].ksplit, pl.inst[k].tc_ksplit) * d * d * 8);
+        o[k].S = tc ? take((size_t)6 * gram_tc_dpad((int)d) * gram_tc_ldk((int)n) * 2) : 0;
+        o[k].expo = tc ? take((size_t)gram_tc_dpad((int)d) * 4) : 0;
         o[k].mom = take(pl.inst[k].mom_elems * 8);
         o[k].hz = take(pl.inst[k].hz_elems * 8);
         o[k].M = take((size_t)d * 8);
@@ -358,6 +371,22 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         I.isd0 = reinterpret_cast<double *>(base + o[k].isd);
         I.isd1 = I.isd0 + d;
         I.I32 = reinterpret_cast<float *>(base + o[k].I32);
+        if (I.tc_ksplit > 0) {
+            I.S = reinterpret_cast<__nv_bfloat16 *>(base + o[k].S);
+            I.expo = reinterpret_cast<int *>(base + o[k].expo);
+            const int64_t ldk = gram_tc_ldk((int)I.n);
+            const int dpad = gram_tc_dpad((int)I.d);
+            cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)6 * dpad};
+            cuuint64_t strides[1] = {(cuuint64_t)(ldk * 2)};
+            cuuint32_t box[2] = {64, 128}, elem[2] = {1, 1};
+            lingam_status st = make_tensor_maps(ctx, pl);   // loads the encoder
+            if (st) return st;
+            CUresult r = g_encode(&I.tmS, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, I.S, dims, strides,
+                                  box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (slices)");
+        }
     }
     return make_tensor_maps(ctx, pl);
 }
@@ -377,7 +406,7 @@ struct ParamBlob {
 
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_F64_ALL, K_SCORE, K_SELECT, K_F64_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC
 };
 
 // Timing events per ordering step when profiling: before the pair moments,
@@ -431,12 +460,18 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             io[k] = IotaParams{I.U0, (int)I.d, I.state};
             maxks = std::max(maxks, I.ksplit);
         }
-        Launch lg_{K_GRAM};
-        lg_.off = blob.add(g);
-        lg_.count = K;
-        lg_.a = pl.maxd;
-        lg_.b = maxks;
-        L.push_back(lg_);
+        if (K == 1 && pl.inst[0].tc_ksplit > 0) {
+            Launch lt{K_GRAM_TC};
+            lt.c = 0;
+            L.push_back(lt);
+        } else {
+            Launch lg_{K_GRAM};
+            lg_.off = blob.add(g);
+            lg_.count = K;
+            lg_.a = pl.maxd;
+            lg_.b = maxks;
+            L.push_back(lg_);
+        }
         Launch li{K_IOTA};
         li.off = blob.add(io);
         li.count = K;
@@ -721,6 +756,13 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             e = cudaEventRecordWithFlags(pl.pev[l.a], s, cudaEventRecordExternal);
             --nodes;
             break;
+        case K_GRAM_TC: {
+            InstDev &I = pl.inst[l.c];
+            e = launch_gram_tc(&I.tmS, I.R, I.ldr, (int)I.n, (int)I.d, I.S, I.expo, I.Cpart,
+                               I.tc_ksplit, I.C, I.d, I.ref_var, &I.state->status, s);
+            nodes += 2;
+            break;
+        }
         case K_FILL_NAN:
             e = launch_fill_nan(pl.inst[l.c].hist, (size_t)pl.inst[l.c].d * pl.inst[l.c].d, s);
             break;
@@ -964,6 +1006,7 @@ lingam_status lingam_create(lingam_ctx **out, int device, const lingam_opts *opt
     for (cudaEvent_t *ev : evs)
         if ((e = cudaEventCreate(ev)) != cudaSuccess) return bad(e);
     if ((e = pair_kernel_setup()) != cudaSuccess) return bad(e);
+    if ((e = gram_tc_setup()) != cudaSuccess) return bad(e);
     *out = ctx;
     return LINGAM_OK;
 }
