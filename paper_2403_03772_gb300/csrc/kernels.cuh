@@ -9,13 +9,13 @@ namespace lg {
 
 // Tile shape of the FP32 pair-moment kernel: a warp owns a WI x WJ block of
 // ordered pairs (i, j) and its 32 lanes split the samples; WGI x WGJ consumer
-// warps form the CTA tile TI x TJ; one extra warp issues the TMA loads.
+// warps form the CTA tile TI x TJ; thread 0 also issues the TMA loads.
 constexpr int PAIR_WI = 4, PAIR_WJ = 4, PAIR_WGI = 2, PAIR_WGJ = 4;
 constexpr int PAIR_TI = PAIR_WI * PAIR_WGI;  // 8 rows  (variables i)
 constexpr int PAIR_TJ = PAIR_WJ * PAIR_WGJ;  // 16 cols (variables j)
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
 constexpr int PAIR_STAGES = 4;
-constexpr int PAIR_THREADS = 32 * (PAIR_WGI * PAIR_WGJ + 1);
+constexpr int PAIR_THREADS = 32 * PAIR_WGI * PAIR_WGJ;
 
 // Scale folded into the fast-form residual: u~ = KSC * u makes
 // 2^(-u~^2) = exp(-u^2/2).

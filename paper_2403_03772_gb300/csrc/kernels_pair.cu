@@ -21,14 +21,14 @@ namespace lg {
 // FP32 pair-moment kernel (TMA-staged, warp-tiled)
 // ------------------------------------------------------------------------
 //
-// CTA tile: TI positions i x TJ positions j.  A producer warp streams chunks
-// of S samples of the TI + TJ standardised columns into shared memory with
-// 2-D bulk tensor copies (one box for the i rows, one for the j rows) into a
-// STAGES-deep ring guarded by full/empty mbarriers.  Each consumer warp owns
-// WI x WJ ordered pairs; lane l handles samples s = 64 it + 2 l, 2 l + 1 of a
-// chunk (VEC = 2 consecutive floats, conflict-free 8-byte loads), so all 32
-// lanes of a warp share the pair coefficients and the moments are reduced
-// across lanes once, after the last chunk.
+// CTA tile: TI positions i x TJ positions j.  Thread 0 streams chunks of S
+// samples of the TI + TJ standardised columns into shared memory with 2-D
+// bulk tensor copies (one box for the i rows, one for the j rows) into a
+// STAGES-deep ring guarded by full/empty mbarriers.  Each warp owns WI x WJ
+// ordered pairs; lane l handles the four consecutive samples 128 it + 4 l ..
+// + 3 of a chunk (conflict-free 16-byte loads), so all 32 lanes of a warp
+// share the pair coefficients and the moments are reduced across lanes once,
+// after the last chunk.
 //
 // Variants:
 //   PAIR_ACCURATE: per sample  log cosh u + ln2 = |u| + log1pf(expf(-2|u|)),
@@ -159,39 +159,30 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     __syncthreads();
     if (nck <= 0 || *abort_flag) return;
 
-    if (warp == NCW) {
-        // ---------------- producer warp: one elected lane issues the TMA ----
-        if (lane == 0) {
-            prefetch_tensormap(tmI);
-            prefetch_tensormap(tmJ);
-            int issued = 0;
-            for (int k = 0; k < nck; ++k) {
-                const int st = k % STAGES;
-                if (k >= STAGES) {
-                    const uint32_t par = ((k / STAGES) - 1) & 1;
-                    if (!mbar_wait_bounded(&empty[st], par)) {
-                        set_status(P.status, ST_TIMEOUT);
-                        *abort_flag = 1;
-                        break;
-                    }
-                }
-                if (*abort_flag) break;
-                float *dst = buf + st * STAGE_FLOATS;
-                const int x = (c0 + k) * S;
-                mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-                tma_load_2d(dst, tmI, x, P.row0 + ti * TI, &full[st]);
-                tma_load_2d(dst + TI * S, tmJ, x, P.row0 + tj * TJ, &full[st]);
-                issued = k + 1;
-            }
-            // never leave with a copy in flight: wait (bounded) for the last
-            // phases issued on every stage
-            for (int k = max(0, issued - STAGES); k < issued; ++k)
-                (void)mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
-        }
-        return;
+    // Thread 0 issues the bulk tensor copies: chunks 0 .. STAGES-2 up front,
+    // then chunk k + STAGES - 1 at iteration k, into the stage that chunk
+    // k - 1 used (free once every warp has finished chunk k - 1).  No warp is
+    // set aside for this: register allocation rounds a CTA up to a multiple
+    // of four warps, so 8 warps keep the full register budget.
+    int issued = 0;
+    auto issue = [&](int k) -> bool {
+        const int st = k % STAGES;
+        if (k >= STAGES && !mbar_wait_bounded(&empty[st], ((k / STAGES) - 1) & 1)) return false;
+        float *dst = buf + st * STAGE_FLOATS;
+        const int x = (c0 + k) * S;
+        mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+        tma_load_2d(dst, tmI, x, P.row0 + ti * TI, &full[st]);
+        tma_load_2d(dst + TI * S, tmJ, x, P.row0 + tj * TJ, &full[st]);
+        issued = k + 1;
+        return true;
+    };
+    if (threadIdx.x == 0) {
+        prefetch_tensormap(tmI);
+        prefetch_tensormap(tmJ);
+        for (int k = 0; k < min(STAGES - 1, nck); ++k) (void)issue(k);
     }
 
-    // ---------------- consumer warps ----------------------------------------
+    // ---------------- every warp computes -----------------------------------
     const int wi = warp / WGJ, wj = warp % WGJ;
     const int ri0 = wi * WI, cj0 = wj * WJ;
     const int pi0 = ti * TI + ri0, pj0 = tj * TJ + cj0;
@@ -242,6 +233,12 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     constexpr int FOLD = 4;
 
     for (int k = 0; k < nck; ++k) {
+        if (threadIdx.x == 0 && k + STAGES - 1 < nck && !*abort_flag) {
+            if (!issue(k + STAGES - 1)) {
+                set_status(P.status, ST_TIMEOUT);
+                *abort_flag = 1;
+            }
+        }
         const int st = k % STAGES;
         const uint32_t par = (k / STAGES) & 1;
         if (!mbar_wait_bounded(&full[st], par)) {
@@ -283,6 +280,12 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
         if (lane == 0) mbar_arrive(&empty[st]);
         if (*abort_flag) break;
     }
+
+    // never leave with a copy in flight: thread 0 waits (bounded) for the
+    // last phase issued on every stage (already consumed ones return at once)
+    if (threadIdx.x == 0)
+        for (int k = max(0, issued - STAGES); k < issued; ++k)
+            (void)mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
 
     // ---------------- cross-lane reduction (fixed xor tree) ------------------
     double *mom = P.mom + (size_t)split * P.p * P.p * 2;
@@ -341,18 +344,17 @@ __device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUte
     pair_block<MODE>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
 }
 
-// Register budgets: the compensated fast form keeps three FP32 words per
-// accumulator and runs one CTA (9 warps) per SM with up to 216 registers
-// (216 x 288 threads leaves headroom under the 64K register file); the
-// accurate form runs two CTAs per SM with up to 104.
-__global__ void __maxnreg__(216)
+// Register budgets (256 threads per CTA): the compensated fast form keeps
+// three FP32 words per accumulator and runs one CTA per SM with up to 248
+// registers; the accurate form runs two CTAs per SM with up to 120.
+__global__ void __maxnreg__(248)
     k_pair_fast_b(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
                   const PairParams *__restrict__ Ps, const int *__restrict__ prefix, int count)
 {
     pair_dispatch<PAIR_FAST>(&tmI, &tmJ, Ps, prefix, count);
 }
 
-__global__ void __maxnreg__(104)
+__global__ void __maxnreg__(120)
     k_pair_accurate_b(const __grid_constant__ CUtensorMap tmI,
                       const __grid_constant__ CUtensorMap tmJ, const PairParams *__restrict__ Ps,
                       const int *__restrict__ prefix, int count)
