@@ -203,6 +203,31 @@ def time_form(ctx, X, steps, warmup, flush_buf, torch, rank, world):
     return ms, stats, order
 
 
+def run_one_order(args):
+    """One order of the headline workload in the first form, bracketed by
+    cudaProfilerStart/Stop so that a profiler started with
+    --profile-from-start off sees exactly one order's launches (after the
+    autotuner and a warm-up order)."""
+    import torch
+    import paper_2403_03772_gb300 as pkg
+    torch.cuda.set_device(0)
+    ds = gen.cfg3()
+    X = torch.from_numpy(ds.X).to("cuda:0")
+    prec = args.forms[0]
+    with pkg.Context(0, prec) as ctx:
+        if prec in ("mixed", "fp32") and not args.no_autotune:
+            ctx.autotune(ds.n, ds.d)
+        ctx.causal_order(X)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        order = ctx.causal_order(X)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"one_order": prec, "graph_nodes": ctx.stats()["graph_nodes"],
+                          "order_head": [int(v) for v in order[:8]]}), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2403_03772_gb300 as pkg
@@ -220,8 +245,12 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev)
     clocks.start()
     t_region0 = time.perf_counter()
+    tunings = {}
     for prec in args.forms:
         with pkg.Context(dev, prec, profile=True) as ctx:
+            # tile shapes and split schedules of the pair kernel (untimed)
+            if prec in ("mixed", "fp32") and not args.no_autotune:
+                tunings[prec] = ctx.autotune(n, d)
             ms, stats, order = time_form(ctx, X, args.steps, args.warmup, flush, torch, rank, world)
             pair_ms = sum(s["pair_ms"] for s in stats)
             pair_units = sum(s["pair_units"] for s in stats)
@@ -230,11 +259,14 @@ def run_ours(args, rank, world):
                                k: sum(s[k] for s in stats) / len(stats)
                                for k in ("pair_ms", "score_ms", "refine_ms", "regress_ms")},
                            "fp64_candidates": stats[-1]["fp64_candidates"],
+                           "df_candidates": stats[-1]["df_candidates"],
                            "pair_launches": sum(s["pair_launches"] for s in stats),
                            "refined_steps": stats[-1]["refined_steps"],
                            "genuine_ties": stats[-1]["genuine_ties"],
                            "graph_nodes": stats[-1]["graph_nodes"],
-                           "order_head": [int(v) for v in order[:8]]}
+                           "order_head": [int(v) for v in order[:8]],
+                           "tuning": ({k: tunings[prec][k] for k in ("p_max", "tile", "ctas_per_sm")}
+                                      if prec in tunings else None)}
     # batched form: the bootstrap workload (128 resamples of d=200, n=4000 plus
     # 64 uneven instances) in one call, against the same instances ordered one
     # call at a time with the plain FP32 form
@@ -246,6 +278,9 @@ def run_ours(args, rank, world):
         Wb = sum(gen.residual_samples(b.X.shape[1], b.X.shape[0] if b.rows is None else len(b.rows))
                  for b in insts)
         with pkg.Context(dev, "mixed") as ctx:
+            if not args.no_autotune:
+                ctx.autotune(max(int(X.shape[0]) if r is None else len(r) for X, r in batch),
+                             max(int(X.shape[1]) for X, _ in batch))
             for _ in range(args.warmup):
                 ctx.causal_order_batch(batch)
             torch.cuda.synchronize()
@@ -279,6 +314,27 @@ def run_ours(args, rank, world):
                       "sequential_plain_fp32_ms": seq_ms,
                       "sequential_plain_fp32_value": (Wb / (seq_ms * 1e-3)) if seq_ms else None}
 
+    # the paper's long-sample case: n = 1e6, d = 100 (Sec. 2.3), head form
+    long_info = None
+    if args.long_n:
+        dl = gen.long_n(seed=rank_seed(gen.SEEDS[6], rank))
+        Xl = torch.from_numpy(dl.X).to(f"cuda:{dev}")
+        Wl = gen.residual_samples(dl.d, dl.n)
+        head0 = args.forms[0]
+        with pkg.Context(dev, head0, profile=True) as ctx:
+            if head0 in ("mixed", "fp32") and not args.no_autotune:
+                ctx.autotune(dl.n, dl.d)
+            lms, lst, lorder = time_form(ctx, Xl, args.steps, args.warmup, flush, torch, rank,
+                                         world)
+        lmax = max_over_ranks(sum(lms), world, f"cuda:{dev}")
+        long_info = {"workload": "long_n_d100_n1e6 (cfg2 generator)", "precision": head0,
+                     "residual_samples": Wl, "ms_per_order": lmax / args.steps,
+                     "value": job_throughput(Wl, world, args.steps, lmax),
+                     "pair_kernel_ms_per_order": sum(s["pair_ms"] for s in lst) / len(lst),
+                     "refined_steps": lst[-1]["refined_steps"],
+                     "order_head": [int(v) for v in lorder[:8]]}
+        del Xl
+
     region_s = time.perf_counter() - t_region0
     clk = clocks.stop()
 
@@ -289,6 +345,8 @@ def run_ours(args, rank, world):
     # e2e: the same call with a pinned host input, copies inside the timed region
     e2e = None
     with pkg.Context(dev, head) as ctx:
+        if head in tunings:
+            ctx.set_tuning(tunings[head])
         Xh = torch.from_numpy(ds.X).pin_memory()
         ctx.causal_order(Xh)
         torch.cuda.synchronize()
@@ -318,21 +376,30 @@ def run_ours(args, rank, world):
     per_clk = {"fp32_ops": fma / 2 / (sms * f_mhz * 1e6), "ex2": ex2 / (sms * e_mhz * 1e6),
                "lg2": lg2 / (sms * l_mhz * 1e6), "fp64_fma": dfma / 2 / (sms * d_mhz * 1e6)}
     run_mhz = clk.get("sm_mhz") or f_mhz
-    # fast form per residual-sample: 2 ex2 + 1 lg2 on MUFU, 8 FP32-pipe ops
-    mufu_rate = 1.0 / (2.0 / (per_clk["ex2"] * sms * run_mhz * 1e6) +
-                       1.0 / (per_clk["lg2"] * sms * run_mhz * 1e6))
-    fp32_rate = per_clk["fp32_ops"] * sms * run_mhz * 1e6 / 8.0
-    peak = min(mufu_rate, fp32_rate)
+    # fast form per residual-sample: 2 MUFU ex2 (exp(-u^2/2), exp(-2|u|)), one
+    # lg2 per four samples (the log of the product of four 1 + y), and 7.25
+    # FP32-pipe ops (u: FMUL + FFMA; u^2; u e accumulate; |u| scale; product
+    # chain 1; |u| sum 0.75; lg2 combine 0.5).  Three ceilings per SM and
+    # clock: MUFU, FP32 pipe, and instruction issue (4 warp-instructions).
+    mix = {"mufu_ex2": 2.0, "mufu_lg2": 0.25, "fp32_pipe": 7.25}
+    hz = sms * run_mhz * 1e6
+    mufu_rate = 1.0 / (mix["mufu_ex2"] / (per_clk["ex2"] * hz) +
+                       mix["mufu_lg2"] / (per_clk["lg2"] * hz))
+    fp32_rate = per_clk["fp32_ops"] * hz / mix["fp32_pipe"]
+    issue_rate = 128.0 * hz / (mix["mufu_ex2"] + mix["mufu_lg2"] + mix["fp32_pipe"])
+    peak = min(mufu_rate, fp32_rate, issue_rate)
     f = forms[head]
     achieved = f["pair_units"] / (f["pair_ms"] * 1e-3) if f["pair_ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": f"k_pair_moments ({head})",
+    roofline = {"bound": "alu", "kernel": f"k_pair_{'fast' if head == 'mixed' else 'accurate'}_b",
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gres/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
                 "peak_from": {"sm_mhz": run_mhz, "sms": sms, "per_clock_per_sm": per_clk,
                               "mufu_bound_gres": mufu_rate / 1e9,
                               "fp32_bound_gres": fp32_rate / 1e9,
-                              "ops_per_residual_sample": {"mufu_ex2": 2, "mufu_lg2": 1,
-                                                          "fp32_pipe": 8}},
+                              "issue_bound_gres": issue_rate / 1e9,
+                              "ops_per_residual_sample": mix,
+                              "note": "of measured unit rates (lingam_peak_probe) at the "
+                                      "median SM clock of the timed region"},
                 "kernel_share": f["pair_ms"] / sum(f["ms"])}
 
     cpu = None
@@ -362,10 +429,12 @@ def run_ours(args, rank, world):
                       "pair_kernel_ms_per_step": forms[p]["pair_ms"] / args.steps,
                       "refined_steps": forms[p]["refined_steps"],
                       "fp64_candidates": forms[p]["fp64_candidates"],
+                      "df_candidates": forms[p]["df_candidates"],
                       "phase_ms_per_step": forms[p]["phase_ms_per_step"],
                       "genuine_ties": forms[p]["genuine_ties"],
                       "order_head": forms[p]["order_head"]} for p in args.forms},
         "batched": batch_info,
+        "long_n": long_info,
         "timed_region_s": region_s,
     }
     print(json.dumps(line), flush=True)
@@ -385,13 +454,20 @@ def main():
     ap.add_argument("--ref-p", type=int, default=240)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-long-n", dest="long_n", action="store_false")
+    ap.add_argument("--one-order", action="store_true",
+                    help="run one profiler-bracketed order of the headline workload and exit")
     ap.add_argument("--batched-sequential", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the untuned pair-kernel tiles (one 8 x 16 configuration)")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.one_order:
+        return run_one_order(args)
     return run_ours(args, rank, world)
 
 

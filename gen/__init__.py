@@ -39,7 +39,7 @@ LN2 = 0.6931471805599453
 SQRT3 = 1.7320508075688772
 SQRT_HALF = 0.7071067811865476
 
-SEEDS = {1: 1001, 2: 1002, 3: 1003, 4: 1004, 5: 1005}
+SEEDS = {1: 1001, 2: 1002, 3: 1003, 4: 1004, 5: 1005, 6: 1006}
 
 
 def series_log(x: np.ndarray) -> np.ndarray:
@@ -214,6 +214,15 @@ def cfg2(seed=SEEDS[2], n: int = 5000, d: int = 100) -> Dataset:
     E = _noise_mix(st, n, d)
     X = sem_sample(B, perm, E)
     return Dataset(X.astype(np.float32), B, perm, f"cfg2_d{d}_n{n}")
+
+
+def long_n(seed=SEEDS[6], n: int = 1_000_000, d: int = 100) -> Dataset:
+    """The paper's long-sample case (Sec. 2.3 and its CPU benchmark figure:
+    1e6 observations of 100 variables, 7 hours for a sequential CPU run),
+    drawn with the cfg2 generator (ER DAG, mean in-degree 2, mixed noise)."""
+    ds = cfg2(seed=seed, n=n, d=d)
+    ds.name = f"long_n_d{d}_n{n}"
+    return ds
 
 
 def cfg3(seed=SEEDS[3], n: int = 10000, d: int = 1000) -> Dataset:

@@ -52,13 +52,25 @@ typedef enum {
 /* Arithmetic of the ordering step.
  *   FP32  -- entropy moments in FP32 with the accurate CUDA expf/log1pf, FP64
  *            covariance (Gram), FP64 residual data, rank-1 downdate and OLS.
- *   MIXED -- Gram on the tensor cores (TF32 hi+lo split products, FP32
- *            accumulation), entropy moments with the hardware ex2/lg2
+ *   MIXED -- covariance on the tensor cores (single-instance calls; exact
+ *            7-bit BF16 digit planes, FP64 recombination, about 1e-10
+ *            relative error), entropy moments with the hardware ex2/lg2
  *            approximations and compensated summation; FP64 downdate and OLS.
  *   FP64  -- every moment in FP64 (small problems; GB300 FP64 is slow).
- * In every mode a step whose top scores lie within the FP32 error bound of
- * each other is re-scored in FP64 before the argmax is taken. */
-typedef enum { LINGAM_PREC_FP32 = 0, LINGAM_PREC_MIXED = 1, LINGAM_PREC_FP64 = 2 } lingam_precision;
+ *   DF    -- every moment in double-float (pairs of FP32 numbers, about
+ *            2^-46 relative error per term) on the FP32 pipe, near-ties
+ *            re-scored in FP64: near-FP64 results at a fraction of its cost.
+ * In the FP32 and MIXED forms a step whose top scores lie within the FP32
+ * error bound of each other re-scores its candidates in double-float, and
+ * the candidates still within that bound of each other in FP64, before the
+ * argmax is taken; steps with at most 32 remaining variables are scored in
+ * double-float throughout. */
+typedef enum {
+    LINGAM_PREC_FP32 = 0,
+    LINGAM_PREC_MIXED = 1,
+    LINGAM_PREC_FP64 = 2,
+    LINGAM_PREC_DF = 3
+} lingam_precision;
 
 typedef enum { LINGAM_ROW_MAJOR = 0, LINGAM_COL_MAJOR = 1 } lingam_layout;
 
@@ -66,8 +78,9 @@ typedef struct {
     int32_t precision;     /* lingam_precision */
     int32_t profile;       /* 1: time every launch of the pair-moment kernel
                               with CUDA events (read back by lingam_get_stats) */
-    double tie_scale;      /* multiplies the FP32 error bound that selects the
-                              candidates re-scored in FP64; 0 means 1.0 */
+    double tie_scale;      /* multiplies the FP32 and double-float error
+                              bounds that select the candidates re-scored in
+                              the next tier; 0 means 1.0 */
     int32_t reserved[8];
 } lingam_opts;
 
@@ -165,21 +178,111 @@ lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, in
                                    int64_t ld, int32_t layout, double *I_out, double *M_out,
                                    lingam_stream_t stream);
 
+/*
+ * Total causal effects (Sec. 4.2 ranks nodes "by measuring the total causal
+ * effects"): for the linear acyclic model x = B x + e, T = (I - B)^-1, so
+ * T[i*d + j] is the effect on x_i of a unit change in e_j: the sum over every
+ * directed path j -> i of the product of the edge weights (T[i][i] = 1).
+ *   B      double[d*d] (host or device), B[i*d + j] = edge j -> i, zero unless
+ *          j precedes i in `order` (else LINGAM_ERR_ARG).
+ *   order  host int32[d], a permutation of 0..d-1 (a causal order of B).
+ *   T_out  double[d*d], host memory, or device memory if T_on_device.
+ * FP64: forward substitution of the unit lower triangular I - B in the order.
+ */
+lingam_status lingam_total_effects(lingam_ctx *ctx, const double *B, int64_t d,
+                                   const int32_t *order, double *T_out, int32_t T_on_device,
+                                   lingam_stream_t stream);
+
+/*
+ * Total effects in the time-unrolled VarLiNGAM graph (Sec. 3.2, 4.2) over the
+ * q = (lags+1) d nodes [x(t-lags), ..., x(t-1), x(t)] (node s*d + i is
+ * variable i in slice s, oldest slice first): B0 acts within every slice,
+ * B_tau from slice s - tau to slice s.  B0 (double[d*d]) and Btau
+ * (double[lags*d*d], as varlingam_fit writes them) may be host or device
+ * memory; order is B0's causal order (host int32[d]).  T_out: double[q*q].
+ */
+lingam_status varlingam_total_effects(lingam_ctx *ctx, const double *B0, const double *Btau,
+                                      int64_t d, int32_t lags, const int32_t *order,
+                                      double *T_out, int32_t T_on_device,
+                                      lingam_stream_t stream);
+
+/*
+ * Influence of every node from total effects T (double[q*q], host or device;
+ * Sec. 4.2 Table 2): exert_out[j] = sum_{i != j} |T[i][j]|, receive_out[i] =
+ * sum_{j != i} |T[i][j]| (host double[q] each, optional); the rank outputs
+ * (host int32[q], optional) list the nodes by descending score, equal scores
+ * to the smaller index, so their first k entries are the top-k nodes.
+ */
+lingam_status lingam_influence(lingam_ctx *ctx, const double *T, int64_t q, double *exert_out,
+                               double *receive_out, int32_t *exert_rank_out,
+                               int32_t *receive_rank_out, lingam_stream_t stream);
+
+/*
+ * Edge statistics over bootstrap resamples (the adjacency matrices of a
+ * batch, host or device double[d*d] each): prob_out[i*d + j] = fraction of the
+ * count matrices with |B[i][j]| > threshold, mean_out[i*d + j] = their mean
+ * (host double[d*d] each).  threshold >= 0.
+ */
+lingam_status lingam_bootstrap_edge_stats(lingam_ctx *ctx, const double *const *B, int32_t count,
+                                          int64_t d, double threshold, double *prob_out,
+                                          double *mean_out, lingam_stream_t stream);
+
+/*
+ * Tile shapes and split schedules of the FP32 pair-moment kernel, by range of
+ * the number p of remaining variables.  Bucket b covers
+ * p_max[b-1] < p <= p_max[b] (p_max ascending; the last bucket also covers
+ * every larger p).  tile[b] indexes the kernel's tile configurations (0..4:
+ * warps x pairs per warp, see the library's design notes); ctas_per_sm[b] is
+ * the number of CTAs per SM the sample splits aim for; ms[b] the kernel time
+ * measured at the probe size p_probe[b] with n_probe samples.  One table per
+ * form that runs the FP32 kernel (precision FP32 or MIXED).
+ */
+typedef struct {
+    int32_t count;            /* buckets in use, 1..8 */
+    int32_t precision;        /* LINGAM_PREC_FP32 or LINGAM_PREC_MIXED */
+    int32_t p_max[8];
+    int32_t tile[8];
+    int32_t ctas_per_sm[8];
+    int32_t p_probe[8];
+    double ms[8];
+    int64_t n_probe;
+} lingam_tuning;
+
+/*
+ * Autotuner: times every tile configuration with three split schedules on
+ * synthetic standardised data of n samples (capped at 131072) at probe sizes
+ * p = 64, 128, ..., up to min(d, 2048), and keeps the fastest per bucket for
+ * the context's current precision form (FP32 or MIXED; other forms return
+ * LINGAM_ERR_ARG).  Later calls of that form use the table.  *out (optional)
+ * receives it.  Allocates and frees its own scratch; invalidates the cached
+ * step graph.
+ */
+lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuning *out);
+
+/* Install a table (for example one saved from an earlier lingam_autotune on
+ * the same GPU model) for the form t->precision; checks its entries. */
+lingam_status lingam_set_tuning(lingam_ctx *ctx, const lingam_tuning *t);
+
+/* Current table of form `precision` (the untuned default is one bucket,
+ * tile 0, 4 CTAs per SM). */
+lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam_tuning *out);
+
 /* Counters of the last lingam_causal_order / batch call on ctx. */
 typedef struct {
     double total_ms;          /* device time of the whole call (events) */
     double pair_ms;           /* summed pair-moment kernel time (profile=1) */
     int64_t pair_launches;    /* pair-moment kernel launches timed */
     double pair_units;        /* residual-samples those launches processed */
-    int32_t refined_steps;    /* steps re-scored in FP64 */
+    int32_t refined_steps;    /* steps whose first scores left candidates */
     int32_t genuine_ties;     /* steps whose FP64 top-2 gap <= 1e-9 max|M| */
     int32_t candidates_max;   /* largest candidate set re-scored */
     int32_t graph_nodes;      /* kernel nodes in the step graph */
     double graph_build_ms;    /* capture + instantiate time (0 if cached) */
     int32_t fp64_candidates;  /* candidates re-scored in FP64 over the run */
-    int32_t reserved[5];
+    int32_t df_candidates;    /* candidates re-scored in double-float */
+    int32_t reserved[4];
     double score_ms;          /* summed score + select time (profile=1) */
-    double refine_ms;         /* summed FP64 re-score passes (profile=1) */
+    double refine_ms;         /* summed re-score passes (profile=1) */
     double regress_ms;        /* summed regress-out + downdate (profile=1) */
 } lingam_stats;
 

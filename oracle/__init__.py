@@ -273,3 +273,55 @@ def varlingam(Xt, lags: int = 1, threads: int | None = None, order=None):
     d = B0.shape[0]
     Btau = np.stack([(np.eye(d) - B0) @ M[tau] for tau in range(lags)])
     return np.asarray(order), B0, Btau, M, E
+
+
+# ------------------------------------------------ downstream of the graph ---
+
+def total_effects(B) -> np.ndarray:
+    """Total causal effects of a linear acyclic model x = B x + e (Sec. 4.2
+    ranks nodes "by measuring the total causal effects"): x = (I - B)^-1 e,
+    so T[i, j] = d x_i / d e_j, the sum over every directed path j -> i of the
+    product of its edge weights (T[i, i] = 1).  ``numpy.linalg.solve``."""
+    B = _f64(B)
+    d = B.shape[0]
+    return np.linalg.solve(np.eye(d) - B, np.eye(d))
+
+
+def var_window_graph(B0, Btau) -> np.ndarray:
+    """Adjacency of the time-unrolled VarLiNGAM graph over the nodes
+    [x(t - lags), ..., x(t - 1), x(t)] (Sec. 3.2): B0 acts within every time
+    slice and B_tau from slice s - tau to slice s.  Block (s, s') of the
+    (lags+1) d square matrix is B_{s - s'} (B0 on the diagonal)."""
+    B0 = _f64(B0)
+    Bt = _f64(Btau)
+    lags, d = Bt.shape[0], B0.shape[0]
+    q = (lags + 1) * d
+    A = np.zeros((q, q))
+    for s in range(lags + 1):
+        A[s * d:(s + 1) * d, s * d:(s + 1) * d] = B0
+        for tau in range(1, s + 1):
+            A[s * d:(s + 1) * d, (s - tau) * d:(s - tau + 1) * d] = Bt[tau - 1]
+    return A
+
+
+def influence(T) -> tuple[np.ndarray, np.ndarray]:
+    """Exerted and received influence of every node from the total effects T
+    (Sec. 4.2, Table 2): exert[j] = sum_{i != j} |T[i, j]|,
+    receive[i] = sum_{j != i} |T[i, j]|."""
+    A = np.abs(_f64(T))
+    np.fill_diagonal(A, 0.0)
+    return A.sum(axis=0), A.sum(axis=1)
+
+
+def top_k(score, k: int) -> np.ndarray:
+    """Indices of the k largest scores, larger first, equal scores to the
+    smaller index (a stable sort of -score)."""
+    score = _f64(score)
+    return np.argsort(-score, kind="stable")[:k].astype(np.int32)
+
+
+def bootstrap_edge_stats(Bs, threshold: float = 0.0) -> tuple[np.ndarray, np.ndarray]:
+    """Edge statistics over bootstrap resamples: the fraction of resamples in
+    which |B[i, j]| > threshold, and the mean of B[i, j]."""
+    Bs = _f64(Bs)
+    return (np.abs(Bs) > threshold).mean(axis=0), Bs.mean(axis=0)

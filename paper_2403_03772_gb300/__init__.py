@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "_lib", "liblingam_gb300.so")
 
 OK, ERR_ARG, ERR_NONFINITE, ERR_DEGENERATE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT = range(7)
-PREC = {"fp32": 0, "mixed": 1, "fp64": 2}
+PREC = {"fp32": 0, "mixed": 1, "fp64": 2, "df": 3}
 ROW_MAJOR, COL_MAJOR = 0, 1
 
 
@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("refined_steps", ctypes.c_int32), ("genuine_ties", ctypes.c_int32),
                 ("candidates_max", ctypes.c_int32), ("graph_nodes", ctypes.c_int32),
                 ("graph_build_ms", ctypes.c_double), ("fp64_candidates", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5), ("score_ms", ctypes.c_double),
+                ("df_candidates", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+                ("score_ms", ctypes.c_double),
                 ("refine_ms", ctypes.c_double), ("regress_ms", ctypes.c_double)]
 
 
@@ -52,6 +53,30 @@ class Instance(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("n_src", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("d", ctypes.c_int64), ("ld", ctypes.c_int64),
                 ("rows", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("p_max", ctypes.c_int32 * 8), ("tile", ctypes.c_int32 * 8),
+                ("ctas_per_sm", ctypes.c_int32 * 8), ("p_probe", ctypes.c_int32 * 8),
+                ("ms", ctypes.c_double * 8), ("n_probe", ctypes.c_int64)]
+
+    def to_dict(self) -> dict:
+        k = self.count
+        return {"count": k, "precision": self.precision, "p_max": list(self.p_max[:k]),
+                "tile": list(self.tile[:k]), "ctas_per_sm": list(self.ctas_per_sm[:k]),
+                "p_probe": list(self.p_probe[:k]), "ms": list(self.ms[:k]),
+                "n_probe": self.n_probe}
+
+    @classmethod
+    def from_dict(cls, t: dict) -> "Tuning":
+        out = cls()
+        out.count, out.precision, out.n_probe = t["count"], t["precision"], t.get("n_probe", 0)
+        for name in ("p_max", "tile", "ctas_per_sm", "p_probe", "ms"):
+            arr = getattr(out, name)
+            for i, v in enumerate(t.get(name, [])[:8]):
+                arr[i] = v
+        return out
 
 
 _lib = None
@@ -71,6 +96,13 @@ SIGNATURES = {
     "lingam_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "lingam_peak_probe": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "lingam_step_scores_noalloc": (_I32, [_P, _I64, _I64, _I64, _P, _P]),
+    "lingam_autotune": (_I32, [_P, _I64, _I64, ctypes.POINTER(Tuning)]),
+    "lingam_total_effects": (_I32, [_P, _P, _I64, _P, _P, _I32, _P]),
+    "varlingam_total_effects": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _I32, _P]),
+    "lingam_influence": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P]),
+    "lingam_bootstrap_edge_stats": (_I32, [_P, _P, _I32, _I64, _D, _P, _P, _P]),
+    "lingam_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
+    "lingam_get_tuning": (_I32, [_P, _I32, ctypes.POINTER(Tuning)]),
 }
 
 
@@ -106,6 +138,20 @@ def _stream_of(arrs):
             if isinstance(a, torch.Tensor) and a.is_cuda:
                 return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
     return ctypes.c_void_p(0)
+
+
+def _square_f64(A):
+    """(pointer, size, keepalive) of a square FP64 matrix (host or CUDA)."""
+    torch = _torch()
+    if torch is not None and isinstance(A, torch.Tensor):
+        if A.dtype != torch.float64 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+            raise TypeError("expected a square float64 tensor")
+        A = A.contiguous()
+        return ctypes.c_void_p(A.data_ptr()), A.shape[0], A
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("expected a square matrix")
+    return ctypes.c_void_p(A.ctypes.data), A.shape[0], A
 
 
 def _matrix(X, dtype):
@@ -235,6 +281,54 @@ class Context:
                                             _ptr(B0), _ptr(Bt), _stream_of([keep])))
         return order, B0, Bt
 
+    # -- read-outs of the estimated graph (Sec. 4.2) -----------------------------
+    def total_effects(self, B, order):
+        """T = (I - B)^-1 (host float64 [d, d]); B must follow ``order``."""
+        p, d, keep = _square_f64(B)
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        T = np.empty((d, d))
+        self._check(self._lib.lingam_total_effects(self._h, p, d, _ptr(order), _ptr(T), 0,
+                                                   _stream_of([keep])))
+        return T
+
+    def varlingam_total_effects(self, B0, Btau, order):
+        """Total effects over the time-unrolled nodes [x(t-lags) .. x(t)]."""
+        p0, d, k0 = _square_f64(B0)
+        Bt = np.ascontiguousarray(Btau, dtype=np.float64)
+        if Bt.ndim != 3 or Bt.shape[1:] != (d, d):
+            raise ValueError("Btau must be [lags, d, d]")
+        lags = Bt.shape[0]
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        q = (lags + 1) * d
+        T = np.empty((q, q))
+        self._check(self._lib.varlingam_total_effects(self._h, p0, _ptr(Bt), d, lags, _ptr(order),
+                                                      _ptr(T), 0, _stream_of([k0])))
+        return T
+
+    def influence(self, T):
+        """(exert, receive, exert_rank, receive_rank) of every node."""
+        p, q, keep = _square_f64(T)
+        ex, rc = np.empty(q), np.empty(q)
+        rex, rrc = np.empty(q, dtype=np.int32), np.empty(q, dtype=np.int32)
+        self._check(self._lib.lingam_influence(self._h, p, q, _ptr(ex), _ptr(rc), _ptr(rex),
+                                               _ptr(rrc), _stream_of([keep])))
+        return ex, rc, rex, rrc
+
+    def bootstrap_edge_stats(self, Bs, threshold: float = 0.0):
+        """(prob, mean) of the edges over a list of [d, d] adjacency matrices."""
+        keep = [_square_f64(B) for B in Bs]
+        if not keep:
+            raise ValueError("need at least one matrix")
+        d = keep[0][1]
+        if any(k[1] != d for k in keep):
+            raise ValueError("all matrices must be d x d")
+        ptrs = (ctypes.c_void_p * len(keep))(*[k[0].value for k in keep])
+        prob, mean = np.empty((d, d)), np.empty((d, d))
+        self._check(self._lib.lingam_bootstrap_edge_stats(
+            self._h, ptrs, len(keep), d, float(threshold), _ptr(prob), _ptr(mean),
+            _stream_of([k[2] for k in keep])))
+        return prob, mean
+
     def causal_order_batch(self, instances, adjacency: bool = False):
         """instances: list of (X [n_src, d] float32, rows int32[n] or None).
         Returns the list of orders (and adjacency matrices when asked)."""
@@ -268,6 +362,50 @@ class Context:
         st = Stats()
         self._check(self._lib.lingam_get_stats(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_ if k != "reserved"}
+
+    def autotune(self, n: int, d: int, cache: str | None = None) -> dict:
+        """Tile shapes and split schedules of the FP32 pair kernel for problems
+        of n samples and up to d variables, in the context's form.  With
+        ``cache`` (a JSON file) a table saved for the same GPU model, form and
+        sizes is installed instead of re-measuring, and a new one is saved."""
+        import json
+        key = None
+        if cache:
+            torch = _torch()
+            dev = torch.cuda.get_device_name(0) if torch and torch.cuda.is_available() else "gpu"
+            key = f"{dev}|{self.precision}|n={int(n)}|d={int(d)}"
+            try:
+                with open(cache) as f:
+                    saved = json.load(f)
+            except (OSError, ValueError):
+                saved = {}
+            if key in saved:
+                t = Tuning.from_dict(saved[key])
+                self._check(self._lib.lingam_set_tuning(self._h, ctypes.byref(t)))
+                return saved[key]
+        t = Tuning()
+        self._check(self._lib.lingam_autotune(self._h, int(n), int(d), ctypes.byref(t)))
+        out = t.to_dict()
+        if cache:
+            try:
+                with open(cache) as f:
+                    saved = json.load(f)
+            except (OSError, ValueError):
+                saved = {}
+            saved[key] = out
+            with open(cache, "w") as f:
+                json.dump(saved, f, indent=1)
+        return out
+
+    def tuning(self, precision: str | None = None) -> dict:
+        t = Tuning()
+        self._check(self._lib.lingam_get_tuning(self._h, PREC[precision or self.precision],
+                                                ctypes.byref(t)))
+        return t.to_dict()
+
+    def set_tuning(self, table: dict):
+        t = Tuning.from_dict(table)
+        self._check(self._lib.lingam_set_tuning(self._h, ctypes.byref(t)))
 
     def peak_probe(self, which: int):
         """(ops per second, SM MHz) of unit `which`: 0 FP32 FMA flop/s,

@@ -16,27 +16,35 @@ enum : uint32_t {
     ST_ARG = 8u,
 };
 
-// Maximum candidates re-scored in FP64 at one step.
-constexpr int MAXC = 64;
-
-// Device-resident state of one ordering run.
+// Device-resident state of one ordering run.  A step whose FP32 scores do
+// not separate the argmax re-scores its candidates in double-float (tier 1),
+// then the still-undecided ones in FP64 (tier 2).  The candidate arrays hold
+// up to d entries (every remaining variable), so no candidate is ever dropped.
 struct DevState {
     uint32_t status;
     int32_t m_pos;          // position (in U) chosen at the current step
-    int32_t ncand;          // candidates for FP64 re-scoring (1 = decided in FP32)
+    int32_t ncand;          // candidates of the current tier (1 = decided in FP32)
     int32_t refined_steps;
     int32_t genuine_ties;
     int32_t cand_max;
-    int32_t cand_overflow;
-    int32_t pass_begin;     // candidate index range of the current FP64 pass
+    int32_t pass_begin;     // candidate index range of the current re-score pass
     int32_t pass_end;
     int32_t resolved;       // 1 once the step's argmax is decided
     int32_t fp64_candidates;  // candidates re-scored in FP64 over the run
-    int32_t pad;
-    int32_t cand[MAXC];     // candidate positions, by upper bound M + E descending
-    double ub[MAXC];        // M + E of each candidate
-    double m64[MAXC];       // FP64 score of each re-scored candidate
+    int32_t tier;           // 1: next re-score in double-float, 2: in FP64
+    int32_t df_candidates;  // candidates re-scored in double-float over the run
+    int32_t *cand;          // [d] candidate positions, by upper bound M + E descending
+    double *ub;             // [d] M + E of each candidate (FP32 scores)
+    double *mhp;            // [d] re-scored M of each candidate
+    double *ehp;            // [d] bound on |mhp - M| (0 in FP64)
 };
+
+// Argmax order of Algorithm 1: larger M first, equal M to the smaller
+// original index.
+__device__ __forceinline__ bool better(double m, int u, double bm, int bu)
+{
+    return (m > bm) || (m == bm && u < bu);
+}
 
 // ------------------------------------------------ entropy approximation ----
 // Maximum-entropy approximation of differential entropy (Hyvarinen 1998), the
@@ -171,6 +179,21 @@ __device__ __forceinline__ double warp_sum_xor(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Block-wide sum in a fixed order (warp xor trees, then warp 0 over the
+// per-warp totals); the result is valid in warp 0.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum_xor(v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) t = warp_sum_xor(t);
+    __syncthreads();
+    return t;
 }
 
 }  // namespace lg

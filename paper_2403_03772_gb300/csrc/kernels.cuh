@@ -3,19 +3,35 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace lg {
 
-// Tile shape of the FP32 pair-moment kernel: a warp owns a WI x WJ block of
-// ordered pairs (i, j) and its 32 lanes split the samples; WGI x WGJ consumer
-// warps form the CTA tile TI x TJ; thread 0 also issues the TMA loads.
-constexpr int PAIR_WI = 4, PAIR_WJ = 4, PAIR_WGI = 2, PAIR_WGJ = 4;
-constexpr int PAIR_TI = PAIR_WI * PAIR_WGI;  // 8 rows  (variables i)
-constexpr int PAIR_TJ = PAIR_WJ * PAIR_WGJ;  // 16 cols (variables j)
+// Tile configurations of the FP32 pair-moment kernel.  A warp owns wi x wj
+// ordered pairs (i, j) and its 32 lanes split the samples; wgi x wgj warps
+// form the CTA tile (wi wgi) x (wj wgj); `stages` chunk buffers of PAIR_S
+// samples sit in shared memory, filled by TMA (thread 0 issues the copies).
+// The register caps set how many CTAs share an SM in each form.  The
+// autotuner picks a configuration and a split schedule per range of p.
+struct PairCfg {
+    int wi, wj, wgi, wgj, stages;
+    int reg_fast, reg_acc;   // register cap per thread (fast / accurate form)
+    constexpr int ti() const { return wi * wgi; }
+    constexpr int tj() const { return wj * wgj; }
+    constexpr int warps() const { return wgi * wgj; }
+    constexpr int threads() const { return 32 * wgi * wgj; }
+};
+constexpr PairCfg PAIR_CFGS[] = {
+    {4, 4, 2, 4, 4, 248, 120},   // 0: 256 threads, 8 x 16 tile
+    {4, 4, 1, 4, 3, 168, 128},   // 1: 128 threads, 4 x 16 tile
+    {4, 2, 2, 4, 4, 128, 80},    // 2: 256 threads, 8 x 8 tile
+    {2, 4, 2, 4, 4, 128, 80},    // 3: 256 threads, 4 x 16 tile
+    {4, 4, 2, 2, 4, 168, 128},   // 4: 128 threads, 8 x 8 tile
+};
+constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
-constexpr int PAIR_STAGES = 4;
-constexpr int PAIR_THREADS = 32 * PAIR_WGI * PAIR_WGJ;
 
 // Scale folded into the fast-form residual: u~ = KSC * u makes
 // 2^(-u~^2) = exp(-u^2/2).
@@ -38,17 +54,25 @@ struct PairParams {
     const double *isd;    // [p] 1 / sqrt(C_ii) by position
 };
 
-struct F64Params {
-    const double *R;      // FP64 residual data [d][ldr] by original index
+// High-precision pair moments (kernels_refine.cu): tier 1 double-float from
+// the split standardised residuals, tier 2 FP64 from the residual data.
+constexpr int HP_THREADS = 256;
+
+struct HpParams {
+    const double *R;      // tier 2: FP64 residual data [d][ldr] by original index
     int64_t ldr;
+    const float *zhi;     // tier 1: standardised residuals z = zhi + zlo, [p][ldz]
+    const float *zlo;     //   by position (same rows as the FP32 pair kernel)
+    int64_t ldz;
+    const double *isd;    // tier 1: [p] 1 / sqrt(C_ii) by position
     const double *C;
     int64_t ldc;
     const int32_t *U;
     int p, n;
-    int mode;             // 0: all pairs + variables; 1: FP64 re-score of candidates
-    int pass;             // mode 1: 1 = first pass (also variable moments), 2 = second
+    int mode;             // 0: all pairs + variables; 1: re-score of candidates
+    int with_vars;        // mode 1: also the variable moments
     const DevState *state;
-    double *mom;          // mode 0: [p][p][2]; mode 1: [MAXC][p][4]
+    double *mom;          // mode 0: [p][p][2]; mode 1: [d][p][4] by candidate slot
     double *hz;           // [p][2] variable moment sums
     uint32_t *status;
     const float *I32;     // mode 1: [p][p] FP32-path I(i, j), or null
@@ -77,22 +101,25 @@ struct SelectParams {
     int p;
     DevState *state;
     int32_t *scratch;     // [p] candidate list workspace
+    int tier;             // tier of the first re-score (1 double-float, 2 FP64)
 };
 
 struct RefineSelectParams {
-    const double *mom;    // [MAXC][p][4]
+    const double *mom;    // [d][p][4] by candidate slot
     const double *hz;     // [p][2]
     int p, n;
     const int32_t *U;
     DevState *state;
     double *hist;         // optional row of the score history
-    int pass;             // 1 or 2
+    int tier;             // 1: double-float passes, 2: FP64 pass
+    double epsI;          // tier 1: bound on the error of each re-scored I(i, j)
 };
 
 struct RegressParams {
     double *R;            // FP64 residual data [d][ldr], updated in place
     int64_t ldr;
     float *z;             // FP32 standardised residuals [d][ldz], compacted by position
+    float *zlo;           // optional: z_exact - z as FP32 (double-float low part)
     int64_t ldz;
     const double *C;
     int64_t ldc;
@@ -159,10 +186,26 @@ cudaError_t launch_downdate_b(const DowndateParams *P, int count, int maxp, cuda
 cudaError_t launch_finish_b(const FinishParams *P, int count, cudaStream_t s);
 
 cudaError_t pair_kernel_setup();
-cudaError_t launch_pair_b(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
+size_t pair_smem_bytes(int cfg);
+// CTAs of configuration cfg resident per SM in the given form (occupancy API).
+int pair_ctas_per_sm(int mode, int cfg);
+cudaError_t launch_pair_b(int mode, int cfg, const CUtensorMap *tmI, const CUtensorMap *tmJ,
                           const PairParams *P, const int *prefix, int count, int total_ctas,
                           cudaStream_t s);
-cudaError_t launch_pairs_f64_b(const F64Params *P, int count, int blocks_per_inst, cudaStream_t s);
+
+// Sample splits of one pair-kernel launch: with `tiles` CTA tiles in total
+// and a target of `target` CTAs, the samples of an instance with nchunks
+// chunks are cut into nsplit ranges of cps chunks.
+inline void pair_split(int64_t tiles, int64_t target, int nchunks, int *cps, int *nsplit)
+{
+    const int ns_pair = tiles > 0 ? (int)std::max<int64_t>(1, (target + tiles - 1) / tiles) : 1;
+    const int ns = std::max(1, std::min(ns_pair, nchunks));
+    *cps = (nchunks + ns - 1) / ns;
+    *nsplit = (nchunks + *cps - 1) / *cps;
+}
+cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks_per_inst,
+                              cudaStream_t s);
+cudaError_t df_tables_setup();
 cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream_t s);
 cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s);
 cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp,
@@ -184,6 +227,7 @@ cudaError_t launch_var_transform(const double *B0, const double *M, int lags, in
                                  cudaStream_t s);
 cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s);
 cudaError_t launch_fill_nan(double *p, size_t count, cudaStream_t s);
+cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStream_t s);
 
 // Tensor-core covariance (kernels_gram_tc.cu): slice planes S [6][d_pad][ldk]
 // BF16 described by tmS (box 64 x 128, 128-byte swizzle), expo [d_pad],
@@ -195,6 +239,17 @@ int gram_tc_ksplit(int n, int d, int num_sms);
 cudaError_t launch_gram_tc(const CUtensorMap *tmS, const double *R, int64_t ldr, int n, int d,
                            __nv_bfloat16 *S, int *expo, double *part, int ksplit, double *C,
                            int64_t ldc, double *ref_var, uint32_t *status, cudaStream_t s);
+
+// Graph read-outs (kernels_effects.cu)
+cudaError_t launch_total_effects_prep(const double *B, const int32_t *order, int d, int32_t *pos,
+                                      double *L, uint32_t *status, cudaStream_t s);
+cudaError_t launch_identity_minus(const double *W, int d, double *T, cudaStream_t s);
+cudaError_t launch_var_window(const double *B0, const double *Bt, int d, int lags,
+                              const int32_t *order0, double *A, int32_t *order, cudaStream_t s);
+cudaError_t launch_influence(const double *T, int d, double *exert, double *receive,
+                             int32_t *rank_exert, int32_t *rank_receive, cudaStream_t s);
+cudaError_t launch_edge_stats(const double *const *Bs, int count, int d, double threshold,
+                              double *prob, double *mean, uint32_t *status, cudaStream_t s);
 
 cudaError_t launch_peak_probe(int which, int blocks, int iters, unsigned long long *cycles,
                               unsigned long long *ns, float *sink, cudaStream_t s);

@@ -85,7 +85,7 @@ __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
             for (int c = 0; c < WJ; ++c) {
                 const float zc[4] = {zj[c].x, zj[c].y, zj[c].z, zj[c].w};
                 if (MODE == PAIR_FAST) {
-                    float q[4], au[4];
+                    float yv[4], au[4];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const float u = fmaf(ca[r][c], zr[v], -(cb[r][c] * zc[v]));
@@ -99,10 +99,15 @@ __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
                             y = 0.0f;
                         }
                         a2[r][c] += g;
-                        q[v] = 1.0f + y;
+                        yv[v] = y;
                         au[v] = a;
                     }
-                    const float prod = (q[0] * q[1]) * (q[2] * q[3]);
+                    // (1 + y0)(1 + y1)(1 + y2)(1 + y3) by q <- q + y q: one
+                    // add and three FMAs instead of four adds and three products
+                    float prod = 1.0f + yv[3];
+                    prod = fmaf(yv[2], prod, prod);
+                    prod = fmaf(yv[1], prod, prod);
+                    prod = fmaf(yv[0], prod, prod);
                     const float asum = (au[0] + au[1]) + (au[2] + au[3]);
                     a1[r][c] += fmaf(asum, FAST_C3, lg2_approx(prod));
                 } else {
@@ -124,14 +129,15 @@ __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
     }
 }
 
-template <int MODE>
+template <int MODE, int CFG>
 __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtensorMap *tmJ,
                                            const PairParams &P, const int ti, const int tj,
                                            const int split)
 {
-    constexpr int WI = PAIR_WI, WJ = PAIR_WJ, WGJ = PAIR_WGJ;
-    constexpr int NCW = PAIR_WGI * PAIR_WGJ;
-    constexpr int TI = PAIR_TI, TJ = PAIR_TJ, S = PAIR_S, STAGES = PAIR_STAGES;
+    constexpr PairCfg G = PAIR_CFGS[CFG];
+    constexpr int WI = G.wi, WJ = G.wj, WGJ = G.wgj;
+    constexpr int NCW = G.warps();
+    constexpr int TI = G.ti(), TJ = G.tj(), S = PAIR_S, STAGES = G.stages;
     constexpr uint32_t STAGE_FLOATS = (TI + TJ) * S;
     constexpr uint32_t STAGE_BYTES = STAGE_FLOATS * 4;
     constexpr bool COMP = (MODE == PAIR_FAST);
@@ -325,7 +331,7 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
 
 // One launch covers the tiles of every instance in the batch: prefix[k] is the
 // first CTA of instance k (tiles_i * tiles_j * nsplit CTAs each).
-template <int MODE>
+template <int MODE, int CFG>
 __device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUtensorMap *tmJ,
                                               const PairParams *__restrict__ Ps,
                                               const int *__restrict__ prefix, int count)
@@ -341,196 +347,79 @@ __device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUte
     const int local = b - prefix[lo];
     const int tiles = P.tiles_i * P.tiles_j;
     const int split = local / tiles, tile = local % tiles;
-    pair_block<MODE>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
+    pair_block<MODE, CFG>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
 }
 
-// Register budgets (256 threads per CTA): the compensated fast form keeps
-// three FP32 words per accumulator and runs one CTA per SM with up to 248
-// registers; the accurate form runs two CTAs per SM with up to 120.
-__global__ void __maxnreg__(248)
+// One kernel per form and tile configuration; the register cap of each
+// fixes how many CTAs share an SM (see PAIR_CFGS).
+template <int CFG>
+__global__ void __maxnreg__(PAIR_CFGS[CFG].reg_fast)
     k_pair_fast_b(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmJ,
                   const PairParams *__restrict__ Ps, const int *__restrict__ prefix, int count)
 {
-    pair_dispatch<PAIR_FAST>(&tmI, &tmJ, Ps, prefix, count);
+    pair_dispatch<PAIR_FAST, CFG>(&tmI, &tmJ, Ps, prefix, count);
 }
 
-__global__ void __maxnreg__(120)
+template <int CFG>
+__global__ void __maxnreg__(PAIR_CFGS[CFG].reg_acc)
     k_pair_accurate_b(const __grid_constant__ CUtensorMap tmI,
                       const __grid_constant__ CUtensorMap tmJ, const PairParams *__restrict__ Ps,
                       const int *__restrict__ prefix, int count)
 {
-    pair_dispatch<PAIR_ACCURATE>(&tmI, &tmJ, Ps, prefix, count);
+    pair_dispatch<PAIR_ACCURATE, CFG>(&tmI, &tmJ, Ps, prefix, count);
 }
 
-static size_t pair_smem_bytes()
+using PairKernel = void (*)(const CUtensorMap, const CUtensorMap, const PairParams *, const int *,
+                            int);
+
+template <int... C>
+struct PairTable {
+    static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
+    static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
+};
+using PairKernels = PairTable<0, 1, 2, 3, 4>;
+static_assert(PAIR_NCFG == 5, "PairKernels lists every configuration");
+
+static PairKernel pair_kernel(int mode, int cfg)
 {
-    return 1024 + (size_t)PAIR_STAGES * (PAIR_TI + PAIR_TJ) * PAIR_S * 4;
+    return mode == PAIR_FAST ? PairKernels::fast[cfg] : PairKernels::acc[cfg];
 }
+
+size_t pair_smem_bytes(int cfg)
+{
+    const PairCfg &G = PAIR_CFGS[cfg];
+    return 1024 + (size_t)G.stages * (G.ti() + G.tj()) * PAIR_S * 4;
+}
+
+static int g_pair_occ[2][PAIR_NCFG];
 
 cudaError_t pair_kernel_setup()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_accurate_b,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pair_smem_bytes());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pair_fast_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pair_smem_bytes());
+    for (int mode = 0; mode < 2; ++mode)
+        for (int c = 0; c < PAIR_NCFG; ++c) {
+            const void *fn = reinterpret_cast<const void *>(pair_kernel(mode, c));
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)pair_smem_bytes(c));
+            if (e != cudaSuccess) return e;
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, PAIR_CFGS[c].threads(),
+                                                              pair_smem_bytes(c));
+            if (e != cudaSuccess) return e;
+            g_pair_occ[mode][c] = std::max(1, occ);
+        }
+    return cudaSuccess;
 }
 
-cudaError_t launch_pair_b(int mode, const CUtensorMap *tmI, const CUtensorMap *tmJ,
+int pair_ctas_per_sm(int mode, int cfg) { return g_pair_occ[mode == PAIR_FAST][cfg]; }
+
+cudaError_t launch_pair_b(int mode, int cfg, const CUtensorMap *tmI, const CUtensorMap *tmJ,
                           const PairParams *P, const int *prefix, int count, int total_ctas,
                           cudaStream_t s)
 {
     if (total_ctas <= 0 || count <= 0) return cudaSuccess;
-    if (mode == PAIR_FAST)
-        k_pair_fast_b<<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(*tmI, *tmJ, P, prefix,
-                                                                         count);
-    else
-        k_pair_accurate_b<<<total_ctas, PAIR_THREADS, pair_smem_bytes(), s>>>(*tmI, *tmJ, P,
-                                                                             prefix, count);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------------
-// FP64 pair moments (whole step in FP64 mode, or re-scoring of candidates)
-// ------------------------------------------------------------------------
-//
-// One warp per work item, lanes stride the samples, FP64 throughout with the
-// CUDA double exp/log1p.  An item is either an unordered pair {a, b} (both
-// residual directions) or a single variable (moments of z itself).
-__device__ __forceinline__ void f64_terms(double u, double &t1, double &t2)
-{
-    const double au = fabs(u);
-    t1 = au + log1p(exp(-2.0 * au));      // log cosh u + ln 2
-    t2 = u * exp(-0.5 * u * u);
-}
-
-__device__ __forceinline__ void pairs_f64_body(const F64Params &P)
-{
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    int cbeg = 0;
-    int64_t npair_items;
-    bool with_vars = true;
-    if (P.mode == 1) {
-        if (P.state->resolved) return;
-        cbeg = P.state->pass_begin;
-        const int cend = P.state->pass_end;
-        if (cend <= cbeg) return;
-        npair_items = (int64_t)(cend - cbeg) * P.p;
-        with_vars = (P.pass == 1);
-    } else {
-        npair_items = (int64_t)P.p * (P.p - 1) / 2;
-    }
-    const int64_t nitems = npair_items + (with_vars ? P.p : 0);
-
-    for (int64_t q = gw; q < nitems; q += nw) {
-        if (q >= npair_items) {
-            const int a = (int)(q - npair_items);
-            const int oa = P.U[a];
-            const double inv = 1.0 / sqrt(P.C[(int64_t)oa * P.ldc + oa]);
-            const double *ra = P.R + (int64_t)oa * P.ldr;
-            double s1 = 0.0, s2 = 0.0;
-            for (int s = lane; s < P.n; s += 32) {
-                double t1, t2;
-                f64_terms(ra[s] * inv, t1, t2);
-                s1 += t1;
-                s2 += t2;
-            }
-            s1 = warp_sum_xor(s1);
-            s2 = warp_sum_xor(s2);
-            if (lane == 0) {
-                P.hz[(size_t)a * 2 + 0] = s1;
-                P.hz[(size_t)a * 2 + 1] = s2;
-            }
-            continue;
-        }
-        int a, b, cidx = 0;
-        if (P.mode == 1) {
-            cidx = cbeg + (int)(q / P.p);
-            a = P.state->cand[cidx];
-            b = (int)(q % P.p);
-            // I32(a, b) >= epsI proves I(a, b) >= 0: min(0, I)^2 = 0 exactly,
-            // so the entry needs no FP64 moments (marked by a negative sum)
-            if (a == b || (P.I32 && P.I32[(size_t)a * P.p + b] >= P.epsI)) {
-                if (lane == 0) {
-                    double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
-                    o[0] = -1.0;
-                    o[1] = o[2] = o[3] = 0.0;
-                }
-                continue;
-            }
-        } else {
-            // unordered pair index q -> (a, b), a < b
-            const double pp = (double)P.p;
-            int64_t aa = (int64_t)floor(((2.0 * pp - 1.0) -
-                                         sqrt((2.0 * pp - 1.0) * (2.0 * pp - 1.0) - 8.0 * (double)q)) /
-                                        2.0);
-            auto first = [&](int64_t x) { return x * (2 * (int64_t)P.p - x - 1) / 2; };
-            if (aa < 0) aa = 0;
-            while (aa > 0 && first(aa) > q) --aa;
-            while (first(aa + 1) <= q) ++aa;
-            a = (int)aa;
-            b = (int)(a + 1 + (q - first(aa)));
-        }
-        const int oa = P.U[a], ob = P.U[b];
-        const int lo = min(oa, ob), hi = max(oa, ob);
-        const double caa = P.C[(int64_t)oa * P.ldc + oa], cbb = P.C[(int64_t)ob * P.ldc + ob];
-        const double rho = P.C[(int64_t)lo * P.ldc + hi] / (sqrt(caa) * sqrt(cbb));
-        double s2v = 1.0 - rho * rho;
-        if (!(s2v > 1e-12)) {
-            if (lane == 0) set_status(P.status, ST_DEGENERATE);
-            s2v = 1.0;
-        }
-        const double isd = 1.0 / sqrt(s2v);
-        const double ia = 1.0 / sqrt(caa), ib = 1.0 / sqrt(cbb);
-        const double *ra = P.R + (int64_t)oa * P.ldr, *rb = P.R + (int64_t)ob * P.ldr;
-        double ab1 = 0.0, ab2 = 0.0, ba1 = 0.0, ba2 = 0.0;
-        for (int s = lane; s < P.n; s += 32) {
-            const double za = ra[s] * ia, zb = rb[s] * ib;
-            double t1, t2;
-            f64_terms((za - rho * zb) * isd, t1, t2);    // residual of a given b
-            ab1 += t1;
-            ab2 += t2;
-            f64_terms((zb - rho * za) * isd, t1, t2);    // residual of b given a
-            ba1 += t1;
-            ba2 += t2;
-        }
-        ab1 = warp_sum_xor(ab1);
-        ab2 = warp_sum_xor(ab2);
-        ba1 = warp_sum_xor(ba1);
-        ba2 = warp_sum_xor(ba2);
-        if (lane == 0) {
-            if (P.mode == 1) {
-                double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
-                o[0] = ab1;
-                o[1] = ab2;
-                o[2] = ba1;
-                o[3] = ba2;
-            } else {
-                double *o = P.mom + ((size_t)a * P.p + b) * 2;
-                o[0] = ab1;
-                o[1] = ab2;
-                o = P.mom + ((size_t)b * P.p + a) * 2;
-                o[0] = ba1;
-                o[1] = ba2;
-            }
-        }
-    }
-}
-
-// blockIdx.y selects the instance; the x blocks stride its work items.
-__global__ void __launch_bounds__(256) k_pairs_f64_b(const F64Params *__restrict__ Ps)
-{
-    const F64Params P = Ps[blockIdx.y];
-    pairs_f64_body(P);
-}
-
-cudaError_t launch_pairs_f64_b(const F64Params *P, int count, int blocks_per_inst, cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    k_pairs_f64_b<<<dim3(blocks_per_inst, count), 256, 0, s>>>(P);
+    if (cfg < 0 || cfg >= PAIR_NCFG) return cudaErrorInvalidValue;
+    pair_kernel(mode, cfg)<<<total_ctas, PAIR_CFGS[cfg].threads(), pair_smem_bytes(cfg), s>>>(
+        *tmI, *tmJ, P, prefix, count);
     return cudaGetLastError();
 }
 
@@ -606,10 +495,6 @@ cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream
 // Select: argmax of M (ties to the smallest original index) and the set of
 // candidates whose score intervals [M - E, M + E] reach the leader's.
 // ------------------------------------------------------------------------
-__device__ __forceinline__ bool better(double m, int u, double bm, int bu)
-{
-    return (m > bm) || (m == bm && u < bu);
-}
 
 __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restrict__ Ps)
 {
@@ -670,8 +555,7 @@ __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restric
         }
         return;
     }
-    // rank by upper bound M + E descending, ties to the smaller original index;
-    // keep the first MAXC
+    // rank by upper bound M + E descending, ties to the smaller original index
     for (int k = tid; k < cnt; k += blockDim.x) {
         const int q = P.scratch[k];
         const double ub = P.M[q] + P.E[q];
@@ -682,21 +566,18 @@ __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restric
             const double ub2 = P.M[q2] + P.E[q2];
             rank += (ub2 > ub) || (ub2 == ub && P.U[q2] < u);
         }
-        if (rank < MAXC) {
-            st->cand[rank] = q;
-            st->ub[rank] = ub;
-        }
+        st->cand[rank] = q;
+        st->ub[rank] = ub;
     }
     if (tid == 0) {
-        const int nc = min(cnt, MAXC);
         st->m_pos = top;
-        st->ncand = nc;
+        st->ncand = cnt;
         st->resolved = 0;
+        st->tier = P.tier;
         st->pass_begin = 0;
-        st->pass_end = min(2, nc);
+        st->pass_end = P.tier == 1 ? min(2, cnt) : cnt;
         st->refined_steps += 1;
         if (cnt > st->cand_max) st->cand_max = cnt;
-        if (cnt > MAXC) st->cand_overflow += 1;
     }
 }
 
@@ -704,68 +585,6 @@ cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     k_select_b<<<count, 1024, 0, s>>>(P);
-    return cudaGetLastError();
-}
-
-// FP64 re-score of a pass of candidates.  Pass 1 scores the two candidates
-// with the highest upper bounds; if the better of them beats every remaining
-// upper bound the step is decided, otherwise pass 2 scores the rest and the
-// argmax is taken over all FP64 scores (ties to the smallest original index).
-__global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParams *__restrict__ Ps)
-{
-    extern __shared__ double h64[];
-    const RefineSelectParams P = Ps[blockIdx.x];
-    DevState *st = P.state;
-    if (st->resolved) return;
-    const int cb = st->pass_begin, ce = st->pass_end, nc = st->ncand;
-    const double invn = 1.0 / (double)P.n;
-    for (int j = threadIdx.x; j < P.p; j += blockDim.x)
-        h64[j] = neg_entropy_part(P.hz[(size_t)j * 2] * invn - LN2_D, P.hz[(size_t)j * 2 + 1] * invn);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = cb + w; c < ce; c += nw) {
-        const int pc = st->cand[c];
-        double acc = 0.0;
-        for (int j = lane; j < P.p; j += 32) {
-            if (j == pc) continue;
-            const double *o = P.mom + ((size_t)c * P.p + j) * 4;
-            if (o[0] < 0.0) continue;
-            const double hcj = neg_entropy_part(o[0] * invn - LN2_D, o[1] * invn);
-            const double hjc = neg_entropy_part(o[2] * invn - LN2_D, o[3] * invn);
-            const double I = (h64[j] + hcj) - (h64[pc] + hjc);
-            const double v = fmin(0.0, I);
-            acc += v * v;
-        }
-        acc = warp_sum_xor(acc);
-        if (lane == 0) st->m64[c] = -acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int best = 0;
-        for (int c = 1; c < ce; ++c)
-            if (better(st->m64[c], P.U[st->cand[c]], st->m64[best], P.U[st->cand[best]])) best = c;
-        st->fp64_candidates += ce - cb;
-        if (P.hist)
-            for (int c = cb; c < ce; ++c) P.hist[P.U[st->cand[c]]] = st->m64[c];
-        if (ce < nc && !(st->m64[best] > st->ub[ce])) {
-            st->pass_begin = ce;       // undecided: score the rest in pass 2
-            st->pass_end = nc;
-            return;
-        }
-        double mx = 0.0, gap = INFINITY;
-        for (int c = 0; c < ce; ++c) mx = fmax(mx, fabs(st->m64[c]));
-        for (int c = 0; c < ce; ++c)
-            if (c != best) gap = fmin(gap, st->m64[best] - st->m64[c]);
-        if (gap <= 1e-9 * mx) st->genuine_ties += 1;
-        st->m_pos = st->cand[best];
-        st->resolved = 1;
-    }
-}
-
-cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp, cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    k_refine_select_b<<<count, 256, sizeof(double) * maxp, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -107,20 +107,6 @@ cudaError_t launch_pack_gather(const float *X, int64_t ld, const int32_t *rows, 
     return cudaGetLastError();
 }
 
-// Block-wide FP64 sum with a fixed reduction tree (deterministic).
-__device__ double block_sum(double v, double *sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    v = warp_sum_xor(v);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-    if (w == 0) t = warp_sum_xor(t);
-    __syncthreads();
-    return t;   // valid in warp 0
-}
-
 // Subtract each column's mean (one block per variable).
 __global__ void __launch_bounds__(256) k_center(double *R, int64_t ldr, int n)
 {
@@ -296,10 +282,11 @@ __global__ void k_iota_b(const IotaParams *__restrict__ Ps)
         st->refined_steps = 0;
         st->genuine_ties = 0;
         st->cand_max = 0;
-        st->cand_overflow = 0;
         st->resolved = 1;
+        st->tier = 0;
         st->pass_begin = st->pass_end = 0;
         st->fp64_candidates = 0;
+        st->df_candidates = 0;
     }
 }
 
@@ -350,6 +337,7 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
     double *ri = P.R + (int64_t)i * P.ldr;
     const double *rm = INIT ? nullptr : P.R + (int64_t)m * P.ldr;
     float *zo = P.z + (int64_t)col * P.ldz;
+    float *zl = P.zlo ? P.zlo + (int64_t)col * P.ldz : nullptr;
     const int s0 = blockIdx.y * P.sps, s1 = min(P.n, s0 + P.sps);
     float a1 = 0.0f, a2 = 0.0f;
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
@@ -358,8 +346,10 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
             r = r - coef * rm[s];
             ri[s] = r;
         }
-        const float z = (float)(r * isd);
+        const double zx = r * isd;
+        const float z = (float)zx;
         zo[s] = z;
+        if (zl) zl[s] = (float)(zx - (double)z);
         const float az = fabsf(z);
         a1 += az + log1pf(expf(-2.0f * az));
         a2 += z * expf(-0.5f * z * z);
@@ -389,6 +379,28 @@ cudaError_t launch_regress_b(const RegressParams *P, int count, bool init, int m
         k_regress_b<true><<<grid, 256, 0, s>>>(P);
     else
         k_regress_b<false><<<grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+// Synthetic standardised columns for the autotuner: z[r][s] in (-2.5, 2.5)
+// from an integer hash of (r, s) for s < n, 0 in the padding up to ldz.
+__global__ void k_fill_test_z(float *z, int64_t ldz, int rows, int n)
+{
+    const int64_t total = (int64_t)rows * ldz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = q % ldz;
+        uint32_t h = (uint32_t)q * 0x9E3779B1u + 0x85EBCA6Bu;
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        z[q] = s < n ? ((float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f) * 5.0f : 0.0f;
+    }
+}
+
+cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStream_t s)
+{
+    k_fill_test_z<<<1024, 256, 0, s>>>(z, ldz, rows, n);
     return cudaGetLastError();
 }
 

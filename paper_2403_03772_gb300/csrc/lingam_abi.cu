@@ -71,12 +71,19 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 // The mixed form computes the covariance of a single-instance run on the
 // tensor cores (kernels_gram_tc.cu).
-constexpr bool TC_GRAM_ENABLED = false;
+constexpr bool TC_GRAM_ENABLED = true;
 
-// Steps with at most P64 remaining variables are scored entirely in FP64:
-// cheap there, and the scores of late steps are small enough that FP32
-// rounding would dominate them.
-constexpr int P64 = 32;
+// Steps with at most P_HP remaining variables are scored entirely in
+// double-float (FP64 in the FP64 form): cheap there, and the scores of late
+// steps are small enough that FP32 rounding would dominate them.
+constexpr int P_HP = 32;
+
+// Bound on the error of one double-float I(i, j) (kernels_refine.cu).  The
+// terms carry at most about 3e-14 absolute error and the sums fold into FP64
+// every 64 samples.  Measured against FP64 on GB300 over all 1e6 first-step
+// entries of the d=1000, n=10000 workload: max 7.5e-15; the bound keeps a
+// factor of about 130 above that.
+constexpr double DF_EPS_I = 1.0e-12;
 
 struct InstSpec {
     int64_t n, d;
@@ -105,6 +112,7 @@ struct InstDev {
 // Sample-split decisions of one global step (shared by sizing and capture).
 struct StepSplit {
     std::vector<int> pair_nsplit, pair_cps, reg_nsplit, reg_sps;
+    int cfg = 0;           // pair-kernel tile configuration of the step
 };
 
 struct Plan {
@@ -113,11 +121,11 @@ struct Plan {
     bool partial = false;   // graph holds only the first step's scores
     cudaGraphExec_t exec = nullptr;
     int nodes = 0;
-    Buf arena, zarena, params;
+    Buf arena, zarena, zloarena, params;
     std::vector<InstDev> inst;
     int64_t ldz = 0, zrows = 0;
     int maxd = 0;
-    CUtensorMap tmI{}, tmJ{};
+    CUtensorMap tmI[PAIR_NCFG]{}, tmJ[PAIR_NCFG]{};   // per tile configuration
     std::vector<cudaEvent_t> pev;
     std::vector<double> punits;
 };
@@ -134,7 +142,10 @@ struct lingam_ctx {
     Plan plan;
     // host-input staging and the buffers of the adjacency / VAR paths
     Buf xstage, aR, aC, aCpart, aL, aW, aPiv, aM, aBt, aRef, aStatus;
+    // buffers of the graph read-outs (total effects, influence, edge stats)
+    Buf eIn, eIn2, eL, eW, eT, ePos, eOrd, ePtr, eOut, eStatus;
     lingam_stats stats{};
+    lingam_tuning tune[2]{};   // pair-kernel choices: [0] accurate (FP32), [1] fast (MIXED)
 };
 
 static std::string g_create_error;
@@ -174,17 +185,53 @@ static lingam_status status_to_code(lingam_ctx *ctx, uint32_t st)
 
 // ------------------------------------------------------------ planning -----
 
-static bool step_in_fp64(int prec, int p) { return prec == LINGAM_PREC_FP64 || p <= P64; }
+// Whole step scored by the high-precision kernel (every pair): always in the
+// FP64 and DF forms, and at the small late steps of the others.
+static bool step_hp(int prec, int p)
+{
+    return prec == LINGAM_PREC_FP64 || prec == LINGAM_PREC_DF || p <= P_HP;
+}
+
+// Tier of such a step: 2 (FP64) in the FP64 form, else 1 (double-float).
+static int step_hp_tier(int prec) { return prec == LINGAM_PREC_FP64 ? 2 : 1; }
 
 static int pair_nchunks(int64_t n) { return (int)((n + PAIR_S - 1) / PAIR_S); }
 
-static int pair_tiles(int p)
+static int pair_tiles(int p, int cfg)
 {
-    return ((p + PAIR_TI - 1) / PAIR_TI) * ((p + PAIR_TJ - 1) / PAIR_TJ);
+    const PairCfg &G = PAIR_CFGS[cfg];
+    return ((p + G.ti() - 1) / G.ti()) * ((p + G.tj() - 1) / G.tj());
+}
+
+// Tuning table of the FP32 pair kernel of a precision form.
+static const lingam_tuning &tuning_of(const lingam_ctx *ctx, int prec)
+{
+    return ctx->tune[prec == LINGAM_PREC_MIXED ? 1 : 0];
+}
+
+// Bucket of the table that covers p.
+static int tune_bucket(const lingam_tuning &tb, int p)
+{
+    for (int b = 0; b < tb.count; ++b)
+        if (p <= tb.p_max[b]) return b;
+    return tb.count - 1;
+}
+
+// Untuned defaults: the 8 x 16 tile, splits aiming at 4 CTAs per SM.
+static void default_tuning(lingam_tuning &tb, int prec)
+{
+    tb = lingam_tuning{};
+    tb.count = 1;
+    tb.precision = prec;
+    tb.p_max[0] = INT32_MAX;
+    tb.tile[0] = 0;
+    tb.ctas_per_sm[0] = 4;
 }
 
 // Sample splits of the pair and regress kernels at global step t: enough CTAs
-// in total to fill the GPU, never more splits than chunks.
+// in total to fill the GPU, never more splits than chunks.  The pair kernel's
+// tile configuration and split target come from the tuning table at the
+// largest p of the step.
 static StepSplit step_splits(const lingam_ctx *ctx, const std::vector<InstSpec> &spec, int prec,
                              int t)
 {
@@ -194,23 +241,24 @@ static StepSplit step_splits(const lingam_ctx *ctx, const std::vector<InstSpec> 
     ss.pair_cps.assign(K, 1);
     ss.reg_nsplit.assign(K, 1);
     ss.reg_sps.assign(K, 1);
+    int pmax = 0;
+    for (int k = 0; k < K; ++k) pmax = std::max(pmax, (int)spec[k].d - t);
+    const lingam_tuning &tb = tuning_of(ctx, prec);
+    const int b = tune_bucket(tb, pmax);
+    ss.cfg = tb.tile[b];
     int64_t tiles = 0, cols = 0;
     for (int k = 0; k < K; ++k) {
         const int p = (int)spec[k].d - t;
         if (p < 2 && !(t == 0 && p == 1)) continue;
-        if (p >= 2 && !step_in_fp64(prec, p)) tiles += pair_tiles(p);
+        if (p >= 2 && !step_hp(prec, p)) tiles += pair_tiles(p, ss.cfg);
         cols += std::max(1, p - 1);
     }
+    const int64_t target_pair = (int64_t)ctx->num_sms * std::max(1, tb.ctas_per_sm[b]);
     const int64_t target = (int64_t)ctx->num_sms * 4;
-    const int ns_pair = tiles > 0 ? (int)std::max<int64_t>(1, (target + tiles - 1) / tiles) : 1;
     const int ns_reg = cols > 0 ? (int)std::max<int64_t>(1, (target + cols - 1) / cols) : 1;
     for (int k = 0; k < K; ++k) {
         const int64_t n = spec[k].n;
-        const int nch = pair_nchunks(n);
-        const int ns = std::max(1, std::min(ns_pair, nch));
-        const int cps = (nch + ns - 1) / ns;
-        ss.pair_cps[k] = cps;
-        ss.pair_nsplit[k] = (nch + cps - 1) / cps;
+        pair_split(tiles, target_pair, pair_nchunks(n), &ss.pair_cps[k], &ss.pair_nsplit[k]);
         const int nr = std::max(1, std::min<int>(ns_reg, (int)std::max<int64_t>(1, n / 1024)));
         const int sps = (int)((n + nr - 1) / nr);
         ss.reg_sps[k] = sps;
@@ -233,16 +281,19 @@ static lingam_status make_tensor_maps(lingam_ctx *ctx, Plan &pl)
     cuuint64_t dims[2] = {(cuuint64_t)pl.ldz, (cuuint64_t)pl.zrows};
     cuuint64_t strides[1] = {(cuuint64_t)(pl.ldz * sizeof(float))};
     cuuint32_t elem[2] = {1, 1};
-    cuuint32_t boxI[2] = {(cuuint32_t)PAIR_S, (cuuint32_t)PAIR_TI};
-    cuuint32_t boxJ[2] = {(cuuint32_t)PAIR_S, (cuuint32_t)PAIR_TJ};
-    CUresult r = g_encode(&pl.tmI, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl.zarena.p, dims, strides,
-                          boxI, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (rows)");
-    r = g_encode(&pl.tmJ, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl.zarena.p, dims, strides, boxJ, elem,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (cols)");
+    for (int c = 0; c < PAIR_NCFG; ++c) {
+        cuuint32_t boxI[2] = {(cuuint32_t)PAIR_S, (cuuint32_t)PAIR_CFGS[c].ti()};
+        cuuint32_t boxJ[2] = {(cuuint32_t)PAIR_S, (cuuint32_t)PAIR_CFGS[c].tj()};
+        CUresult r = g_encode(&pl.tmI[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl.zarena.p, dims,
+                              strides, boxI, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (rows)");
+        r = g_encode(&pl.tmJ[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl.zarena.p, dims, strides,
+                     boxJ, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(ctx, LINGAM_ERR_CUDA, "tensor map encode failed (cols)");
+    }
     return LINGAM_OK;
 }
 
@@ -254,6 +305,7 @@ static void destroy_plan(Plan &pl)
     pl.pev.clear();
     release(pl.arena);
     release(pl.zarena);
+    release(pl.zloarena);
     release(pl.params);
     pl.inst.clear();
     pl.spec.clear();
@@ -293,7 +345,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
                 pl.inst[k].hz_elems = std::max(
                     pl.inst[k].hz_elems, (size_t)ss.reg_nsplit[k] * (size_t)spec[k].d * 2);
             if (p < 2) continue;
-            if (!step_in_fp64(prec, (int)p))
+            if (!step_hp(prec, (int)p))
                 pl.inst[k].mom_elems =
                     std::max(pl.inst[k].mom_elems, (size_t)ss.pair_nsplit[k] * p * p * 2);
             pl.inst[k].hz_elems =
@@ -308,7 +360,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     };
     struct Off {
         size_t R, C, Cpart, mom, hz, M, E, hist, ref, fmom, fhz, lcoef, U, order, scratch, rows,
-            state, isd, I32, S, expo;
+            state, isd, I32, S, expo, cand, cdbl;
     };
     std::vector<Off> o(K);
     for (int k = 0; k < K; ++k) {
@@ -326,7 +378,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].E = take((size_t)d * 8);
         o[k].hist = scores ? take((size_t)d * d * 8) : 0;
         o[k].ref = take((size_t)d * 8);
-        o[k].fmom = take((size_t)MAXC * d * 4 * 8);
+        o[k].fmom = take((size_t)d * d * 4 * 8);
         o[k].fhz = take((size_t)d * 2 * 8);
         o[k].lcoef = lcoef ? take((size_t)d * d * 8) : 0;
         o[k].U = take((size_t)2 * d * 4);
@@ -336,6 +388,8 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].state = take(sizeof(DevState));
         o[k].isd = take((size_t)2 * d * 8);
         o[k].I32 = take((size_t)d * d * 4);
+        o[k].cand = take((size_t)d * 4);
+        o[k].cdbl = take((size_t)3 * d * 8);
     }
     CK(ensure(pl.arena, off));
     CK(cudaMemset(pl.arena.p, 0, off));
@@ -346,6 +400,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         pl.zrows += spec[k].d;
     }
     CK(ensure(pl.zarena, (size_t)pl.zrows * pl.ldz * 4, true));
+    if (prec != LINGAM_PREC_FP64) CK(ensure(pl.zloarena, (size_t)pl.zrows * pl.ldz * 4, true));
     char *base = reinterpret_cast<char *>(pl.arena.p);
     for (int k = 0; k < K; ++k) {
         InstDev &I = pl.inst[k];
@@ -371,6 +426,14 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         I.isd0 = reinterpret_cast<double *>(base + o[k].isd);
         I.isd1 = I.isd0 + d;
         I.I32 = reinterpret_cast<float *>(base + o[k].I32);
+        {   // candidate arrays of the device state
+            DevState h{};
+            h.cand = reinterpret_cast<int32_t *>(base + o[k].cand);
+            h.ub = reinterpret_cast<double *>(base + o[k].cdbl);
+            h.mhp = h.ub + d;
+            h.ehp = h.mhp + d;
+            CK(cudaMemcpy(I.state, &h, sizeof(DevState), cudaMemcpyHostToDevice));
+        }
         if (I.tc_ksplit > 0) {
             I.S = reinterpret_cast<__nv_bfloat16 *>(base + o[k].S);
             I.expo = reinterpret_cast<int *>(base + o[k].expo);
@@ -405,7 +468,7 @@ struct ParamBlob {
 };
 
 enum LaunchKind {
-    K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_F64_ALL, K_SCORE, K_SELECT, K_F64_PASS, K_REFINE,
+    K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
     K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC
 };
 
@@ -431,16 +494,18 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     cudaStream_t s = ctx->s;
     const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
     // Bound on |I_fp32 - I_exact| per entry, used to pick the candidates that
-    // are re-scored in FP64.  Measured against the FP64 oracle on GB300 over
-    // all 1e6 first-step entries of the d=1000, n=10000 workload: max 1.2e-6
-    // (accurate FP32, plain sums) and 1.5e-7 (fast, compensated sums); the
-    // bounds keep a factor of 3-4 above those.
-    const double epsI = prec == LINGAM_PREC_MIXED ? 6.0e-7 * tie : 4.0e-6 * tie;
+    // are re-scored.  Measured against FP64 on GB300 over all 1e6 first-step
+    // entries of the d=1000, n=10000 workload: max 1.25e-6 (accurate FP32,
+    // plain sums) and 3.5e-7 (fast form: the MUFU ex2/lg2 relative error is
+    // systematic, so it does not average out over the samples); the bounds
+    // keep a factor of 4 above those.
+    const double epsI = prec == LINGAM_PREC_MIXED ? 1.5e-6 * tie : 5.0e-6 * tie;
     const int pmode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
     const double a1 = pmode == PAIR_FAST ? LN2_D : 1.0;
     const double a2 = pmode == PAIR_FAST ? 1.0 / KSC : 1.0;
     const int last_t = stop_after_score0 ? 0 : pl.maxd - 2;
     float *zbase = ptr<float>(pl.zarena);
+    float *zlobase = prec == LINGAM_PREC_FP64 ? nullptr : ptr<float>(pl.zloarena);
 
     ParamBlob blob;
     std::vector<Launch> L;
@@ -486,6 +551,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         P.R = I.R;
         P.ldr = I.ldr;
         P.z = zbase + (int64_t)I.zrow * pl.ldz;
+        P.zlo = zlobase ? zlobase + (int64_t)I.zrow * pl.ldz : nullptr;
         P.ldz = pl.ldz;
         P.C = I.C;
         P.ldc = I.d;
@@ -531,10 +597,10 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         StepSplit ss = step_splits(ctx, pl.spec, prec, t);
         std::vector<PairParams> pp;
         std::vector<int> prefix(1, 0);
-        std::vector<F64Params> fa, f1, f2;
+        std::vector<HpParams> fa, fd1, fd2, f64;
         std::vector<ScoreParams> sc;
         std::vector<SelectParams> se;
-        std::vector<RefineSelectParams> r1, r2;
+        std::vector<RefineSelectParams> rd1, rd2, r64;
         std::vector<RegressParams> rg;
         std::vector<DowndateParams> dd;
         int maxp = 0, maxcols = 0, maxsplit = 1;
@@ -548,21 +614,28 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             units += (double)p * (p - 1) * n;
             int32_t *Uc = (t & 1) ? I.U1 : I.U0;
             int32_t *Un = (t & 1) ? I.U0 : I.U1;
+            double *isd = (t & 1) ? I.isd1 : I.isd0;
             double *hist_row = I.hist ? I.hist + (size_t)t * I.d : nullptr;
-            const bool s64 = step_in_fp64(prec, p);
-            auto f64p = [&](int mode, int pass, double *mom) {
-                F64Params F{};
-                F.I32 = (mode == 1 && !s64) ? I.I32 : nullptr;
+            const bool hp = step_hp(prec, p);
+            const int hp_tier = step_hp_tier(prec);
+            auto hpp = [&](int mode, int with_vars, double *mom) {
+                HpParams F{};
+                // entries whose FP32 I clears the FP32 bound need no re-score
+                F.I32 = (mode == 1 && !hp) ? I.I32 : nullptr;
                 F.epsI = epsI;
                 F.R = I.R;
                 F.ldr = I.ldr;
+                F.zhi = zbase + (int64_t)I.zrow * pl.ldz;
+                F.zlo = zlobase ? zlobase + (int64_t)I.zrow * pl.ldz : nullptr;
+                F.ldz = pl.ldz;
+                F.isd = isd;
                 F.C = I.C;
                 F.ldc = I.d;
                 F.U = Uc;
                 F.p = p;
                 F.n = n;
                 F.mode = mode;
-                F.pass = pass;
+                F.with_vars = with_vars;
                 F.state = I.state;
                 F.mom = mom;
                 F.hz = I.fhz;
@@ -570,8 +643,8 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 return F;
             };
             ScoreParams S{};
-            if (step_in_fp64(prec, p)) {
-                fa.push_back(f64p(0, 0, I.mom));
+            if (hp) {
+                fa.push_back(hpp(0, 1, I.mom));
                 S.mom = I.mom;
                 S.nsplit = 1;
                 S.hz = I.fhz;
@@ -579,7 +652,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 S.a1 = 1.0;
                 S.b1 = -LN2_D;
                 S.a2 = 1.0;
-                S.epsI = 0.0;
+                S.epsI = hp_tier == 1 ? DF_EPS_I * tie : 0.0;
             } else {
                 PairParams P{};
                 P.C = I.C;
@@ -587,15 +660,15 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 P.U = Uc;
                 P.p = p;
                 P.n = n;
-                P.tiles_i = (p + PAIR_TI - 1) / PAIR_TI;
-                P.tiles_j = (p + PAIR_TJ - 1) / PAIR_TJ;
+                P.tiles_i = (p + PAIR_CFGS[ss.cfg].ti() - 1) / PAIR_CFGS[ss.cfg].ti();
+                P.tiles_j = (p + PAIR_CFGS[ss.cfg].tj() - 1) / PAIR_CFGS[ss.cfg].tj();
                 P.nchunks = pair_nchunks(n);
                 P.cps = ss.pair_cps[k];
                 P.nsplit = ss.pair_nsplit[k];
                 P.mom = I.mom;
                 P.status = &I.state->status;
                 P.row0 = I.zrow;
-                P.isd = (t & 1) ? I.isd1 : I.isd0;
+                P.isd = isd;
                 pp.push_back(P);
                 prefix.push_back(prefix.back() + P.tiles_i * P.tiles_j * P.nsplit);
                 S.mom = I.mom;
@@ -617,13 +690,18 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             S.E = I.E;
             S.hist = hist_row;
             S.Iout = stop_after_score0 ? Iout : nullptr;
-            S.I32 = s64 ? nullptr : I.I32;
+            S.I32 = hp ? nullptr : I.I32;
             sc.push_back(S);
-            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch});
-            f1.push_back(f64p(1, 1, I.fmom));
-            f2.push_back(f64p(1, 2, I.fmom));
-            r1.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 1});
-            r2.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 2});
+            // candidates of an FP32-scored step go to double-float first; a
+            // step scored in double-float sends its near-ties to FP64
+            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 1});
+            fd1.push_back(hpp(1, 1, I.fmom));
+            fd2.push_back(hpp(1, 0, I.fmom));
+            f64.push_back(hpp(1, 1, I.fmom));
+            const double e2 = DF_EPS_I * tie;
+            rd1.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 1, e2});
+            rd2.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 1, e2});
+            r64.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 2, 0.0});
             rg.push_back(regress_params(I, t, p, Uc, Un, ss.reg_sps[k], false));
             nsplit_hz[k] = ss.reg_nsplit[k];
             maxcols = std::max(maxcols, p - 1);
@@ -632,6 +710,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         }
         if (sc.empty()) break;
         const int cnt = (int)sc.size();
+        const int hp_blocks = std::max(1, ctx->num_sms * 4 / cnt);
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t;
@@ -644,14 +723,16 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             l.off2 = blob.add(prefix);
             l.count = (int)pp.size();
             l.a = prefix.back();
+            l.b = ss.cfg;
             l.c = pmode;
             L.push_back(l);
         }
         if (!fa.empty()) {
-            Launch l{K_F64_ALL};
+            Launch l{K_HP_ALL};
             l.off = blob.add(fa);
             l.count = (int)fa.size();
-            l.a = std::max(1, ctx->num_sms * 8 / (int)fa.size());
+            l.a = std::max(1, ctx->num_sms * 4 / (int)fa.size());
+            l.c = step_hp_tier(prec);
             L.push_back(l);
         }
         if (profile) {
@@ -674,14 +755,20 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             ev.a = EV_PER_STEP * t + 2;
             L.push_back(ev);
         }
-        for (int pass = 1; pass <= 2; ++pass) {
-            Launch lf{K_F64_PASS};
-            lf.off = blob.add(pass == 1 ? f1 : f2);
+        // re-score passes: double-float pass 1 and 2, then FP64; each is a
+        // no-op unless the step's state routes candidates to it
+        const std::vector<HpParams> *passes[3] = {&fd1, &fd2, &f64};
+        const std::vector<RefineSelectParams> *decides[3] = {&rd1, &rd2, &r64};
+        for (int q = 0; q < 3; ++q) {
+            if (q < 2 && prec == LINGAM_PREC_FP64) continue;   // no double-float tier there
+            Launch lf{K_HP_PASS};
+            lf.off = blob.add(*passes[q]);
             lf.count = cnt;
-            lf.a = std::max(1, ctx->num_sms * 4 / cnt);
+            lf.a = hp_blocks;
+            lf.c = q < 2 ? 1 : 2;
             L.push_back(lf);
             Launch lrs{K_REFINE};
-            lrs.off = blob.add(pass == 1 ? r1 : r2);
+            lrs.off = blob.add(*decides[q]);
             lrs.count = cnt;
             lrs.a = maxp;
             L.push_back(lrs);
@@ -737,13 +824,13 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             e = launch_regress_b((const RegressParams *)P, l.count, true, l.a, l.b, s);
             break;
         case K_PAIR:
-            e = launch_pair_b(l.c, &pl.tmI, &pl.tmJ, (const PairParams *)P,
+            e = launch_pair_b(l.c, l.b, &pl.tmI[l.b], &pl.tmJ[l.b], (const PairParams *)P,
                               (const int *)(pb + l.off2), l.count, l.a, s);
             break;
-        case K_F64_ALL: e = launch_pairs_f64_b((const F64Params *)P, l.count, l.a, s); break;
+        case K_HP_ALL: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
         case K_SCORE: e = launch_score_b((const ScoreParams *)P, l.count, l.a, s); break;
         case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
-        case K_F64_PASS: e = launch_pairs_f64_b((const F64Params *)P, l.count, l.a, s); break;
+        case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
         case K_REFINE:
             e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
             break;
@@ -915,6 +1002,7 @@ static lingam_status run_plan(lingam_ctx *ctx, int32_t *const *orders_out, doubl
         st.genuine_ties += h.genuine_ties;
         st.candidates_max = std::max(st.candidates_max, h.cand_max);
         st.fp64_candidates += h.fp64_candidates;
+        st.df_candidates += h.df_candidates;
     }
     st.graph_nodes = pl.nodes;
     if (pl.profile && !pl.pev.empty()) {
@@ -978,14 +1066,16 @@ lingam_status lingam_create(lingam_ctx **out, int device, const lingam_opts *opt
         g_create_error = "device index out of range";
         return LINGAM_ERR_ARG;
     }
-    if (opts && (opts->precision < 0 || opts->precision > 2)) {
-        g_create_error = "precision must be 0, 1 or 2";
+    if (opts && (opts->precision < 0 || opts->precision > LINGAM_PREC_DF)) {
+        g_create_error = "precision must be 0, 1, 2 or 3";
         return LINGAM_ERR_ARG;
     }
     lingam_ctx *ctx = new (std::nothrow) lingam_ctx();
     if (!ctx) return LINGAM_ERR_OOM;
     ctx->device = device;
     if (opts) ctx->opts = *opts;
+    default_tuning(ctx->tune[0], LINGAM_PREC_FP32);
+    default_tuning(ctx->tune[1], LINGAM_PREC_MIXED);
     auto bad = [&](cudaError_t err) {
         g_create_error = std::string("CUDA error during create: ") + cudaGetErrorString(err);
         cudaGetLastError();
@@ -1007,6 +1097,7 @@ lingam_status lingam_create(lingam_ctx **out, int device, const lingam_opts *opt
         if ((e = cudaEventCreate(ev)) != cudaSuccess) return bad(e);
     if ((e = pair_kernel_setup()) != cudaSuccess) return bad(e);
     if ((e = gram_tc_setup()) != cudaSuccess) return bad(e);
+    if ((e = df_tables_setup()) != cudaSuccess) return bad(e);
     *out = ctx;
     return LINGAM_OK;
 }
@@ -1017,8 +1108,11 @@ lingam_status lingam_destroy(lingam_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->s) cudaStreamSynchronize(ctx->s);
     destroy_plan(ctx->plan);
-    Buf *aux[] = {&ctx->xstage, &ctx->aR, &ctx->aC, &ctx->aCpart, &ctx->aL, &ctx->aW,
-                  &ctx->aPiv, &ctx->aM, &ctx->aBt, &ctx->aRef, &ctx->aStatus};
+    Buf *aux[] = {&ctx->xstage, &ctx->aR,   &ctx->aC,   &ctx->aCpart,  &ctx->aL,
+                  &ctx->aW,     &ctx->aPiv, &ctx->aM,   &ctx->aBt,     &ctx->aRef,
+                  &ctx->aStatus, &ctx->eIn, &ctx->eIn2, &ctx->eL,      &ctx->eW,
+                  &ctx->eT,     &ctx->ePos, &ctx->eOrd, &ctx->ePtr,    &ctx->eOut,
+                  &ctx->eStatus};
     for (Buf *b : aux) release(*b);
     cudaEvent_t evs[] = {ctx->e0, ctx->e1, ctx->g0, ctx->g1};
     for (cudaEvent_t ev : evs)
@@ -1037,7 +1131,7 @@ const char *lingam_last_error(const lingam_ctx *ctx)
 lingam_status lingam_set_precision(lingam_ctx *ctx, int32_t precision)
 {
     if (!ctx) return LINGAM_ERR_ARG;
-    if (precision < 0 || precision > 2) return fail(ctx, LINGAM_ERR_ARG, "bad precision");
+    if (precision < 0 || precision > LINGAM_PREC_DF) return fail(ctx, LINGAM_ERR_ARG, "bad precision");
     ctx->opts.precision = precision;
     return LINGAM_OK;
 }
@@ -1159,7 +1253,7 @@ lingam_status varlingam_fit(lingam_ctx *ctx, const void *Xt, int64_t T, int64_t 
     if (n <= q) return fail(ctx, LINGAM_ERR_DEGENERATE, "T - lags must exceed lags*d + d");
     if (q > 6000) return fail(ctx, LINGAM_ERR_ARG, "(lags+1)*d > 6000 is not supported");
     if (ctx->opts.precision == LINGAM_PREC_FP64)
-        return fail(ctx, LINGAM_ERR_ARG, "varlingam_fit takes FP32 data; use FP32 or MIXED");
+        return fail(ctx, LINGAM_ERR_ARG, "varlingam_fit takes FP32 data; use FP32, MIXED or DF");
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     lingam_status st;
     if ((st = begin_call(ctx, user))) return st;
@@ -1239,7 +1333,7 @@ lingam_status lingam_causal_order_batch(lingam_ctx *ctx, const lingam_instance *
     if (!inst || count < 1 || !orders_out)
         return fail(ctx, LINGAM_ERR_ARG, "need instances, count >= 1 and orders_out");
     if (ctx->opts.precision == LINGAM_PREC_FP64)
-        return fail(ctx, LINGAM_ERR_ARG, "batched ordering takes FP32 data; use FP32 or MIXED");
+        return fail(ctx, LINGAM_ERR_ARG, "batched ordering takes FP32 data; use FP32, MIXED or DF");
     bool any_rows = false;
     std::vector<InstSpec> spec(count);
     for (int k = 0; k < count; ++k) {
@@ -1331,6 +1425,382 @@ lingam_status lingam_get_stats(const lingam_ctx *ctx, lingam_stats *out)
 {
     if (!ctx || !out) return LINGAM_ERR_ARG;
     *out = ctx->stats;
+    return LINGAM_OK;
+}
+
+// ------------------------------------------------ graph read-outs (Sec. 4.2)
+
+// Device copy of a caller matrix of `bytes` (used in place when it already
+// lives on the device).
+static lingam_status device_view(lingam_ctx *ctx, const void *src, size_t bytes, Buf &stage,
+                                 const void **out)
+{
+    if (is_device_ptr(src)) {
+        *out = src;
+        return LINGAM_OK;
+    }
+    CK(ensure(stage, bytes));
+    CK(cudaMemcpyAsync(stage.p, src, bytes, cudaMemcpyHostToDevice, ctx->s));
+    *out = stage.p;
+    return LINGAM_OK;
+}
+
+static lingam_status check_perm(lingam_ctx *ctx, const int32_t *order, int64_t d)
+{
+    std::vector<char> seen((size_t)d, 0);
+    for (int64_t k = 0; k < d; ++k) {
+        if (order[k] < 0 || order[k] >= d || seen[order[k]])
+            return fail(ctx, LINGAM_ERR_ARG, "order is not a permutation of 0..d-1");
+        seen[order[k]] = 1;
+    }
+    return LINGAM_OK;
+}
+
+// T = (I - B)^-1 for B strictly lower triangular in the device order dOrd.
+static lingam_status effects_core(lingam_ctx *ctx, const double *dB, const int32_t *dOrd, int q,
+                                  double *T_out, int on_device, uint32_t *status)
+{
+    CK(ensure(ctx->eL, (size_t)q * q * 8));
+    CK(ensure(ctx->eW, (size_t)q * q * 8));
+    CK(ensure(ctx->eT, (size_t)q * q * 8));
+    CK(ensure(ctx->ePos, (size_t)q * 4));
+    CK(launch_total_effects_prep(dB, dOrd, q, ptr<int32_t>(ctx->ePos), ptr<double>(ctx->eL), status,
+                                 ctx->s));
+    CK(launch_unit_lower_inverse(ptr<double>(ctx->eL), q, dOrd, q, ptr<double>(ctx->eW), q, ctx->s));
+    CK(launch_identity_minus(ptr<double>(ctx->eW), q, ptr<double>(ctx->eT), ctx->s));
+    if (T_out)
+        CK(cudaMemcpyAsync(T_out, ctx->eT.p, (size_t)q * q * 8,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
+    return LINGAM_OK;
+}
+
+lingam_status lingam_total_effects(lingam_ctx *ctx, const double *B, int64_t d,
+                                   const int32_t *order, double *T_out, int32_t T_on_device,
+                                   lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!B || !order || !T_out) return fail(ctx, LINGAM_ERR_ARG, "B, order or T_out is NULL");
+    if (d < 1 || d > 12000) return fail(ctx, LINGAM_ERR_ARG, "need 1 <= d <= 12000");
+    lingam_status st = check_perm(ctx, order, d);
+    if (st) return st;
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = begin_call(ctx, user))) return st;
+    CK(ensure(ctx->eStatus, 256));
+    CK(ensure(ctx->eOrd, (size_t)d * 4));
+    uint32_t *status = ptr<uint32_t>(ctx->eStatus);
+    CK(cudaMemsetAsync(status, 0, 4, ctx->s));
+    CK(cudaMemcpyAsync(ctx->eOrd.p, order, (size_t)d * 4, cudaMemcpyHostToDevice, ctx->s));
+    const void *dB = nullptr;
+    if ((st = device_view(ctx, B, (size_t)d * d * 8, ctx->eIn, &dB))) return st;
+    if ((st = effects_core(ctx, (const double *)dB, ptr<int32_t>(ctx->eOrd), (int)d, T_out,
+                           T_on_device, status)))
+        return st;
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    if (hst & ST_ARG) return fail(ctx, LINGAM_ERR_ARG, "B has an edge that does not follow order");
+    return status_to_code(ctx, hst);
+}
+
+lingam_status varlingam_total_effects(lingam_ctx *ctx, const double *B0, const double *Btau,
+                                      int64_t d, int32_t lags, const int32_t *order, double *T_out,
+                                      int32_t T_on_device, lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!B0 || !Btau || !order || !T_out)
+        return fail(ctx, LINGAM_ERR_ARG, "B0, Btau, order or T_out is NULL");
+    if (d < 1 || lags < 1 || (lags + 1) * d > 12000)
+        return fail(ctx, LINGAM_ERR_ARG, "need d >= 1, lags >= 1, (lags+1)*d <= 12000");
+    lingam_status st = check_perm(ctx, order, d);
+    if (st) return st;
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = begin_call(ctx, user))) return st;
+    const int q = (int)((lags + 1) * d);
+    CK(ensure(ctx->eStatus, 256));
+    CK(ensure(ctx->ePtr, (size_t)d * 4));
+    CK(ensure(ctx->eOrd, (size_t)q * 4));
+    CK(ensure(ctx->eOut, (size_t)q * q * 8));
+    uint32_t *status = ptr<uint32_t>(ctx->eStatus);
+    CK(cudaMemsetAsync(status, 0, 4, ctx->s));
+    CK(cudaMemcpyAsync(ctx->ePtr.p, order, (size_t)d * 4, cudaMemcpyHostToDevice, ctx->s));
+    const void *d0 = nullptr, *dt = nullptr;
+    if ((st = device_view(ctx, B0, (size_t)d * d * 8, ctx->eIn, &d0))) return st;
+    if ((st = device_view(ctx, Btau, (size_t)lags * d * d * 8, ctx->eIn2, &dt))) return st;
+    CK(launch_var_window((const double *)d0, (const double *)dt, (int)d, lags,
+                         ptr<int32_t>(ctx->ePtr), ptr<double>(ctx->eOut), ptr<int32_t>(ctx->eOrd),
+                         ctx->s));
+    if ((st = effects_core(ctx, ptr<double>(ctx->eOut), ptr<int32_t>(ctx->eOrd), q, T_out,
+                           T_on_device, status)))
+        return st;
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    if (hst & ST_ARG) return fail(ctx, LINGAM_ERR_ARG, "B0 has an edge that does not follow order");
+    return status_to_code(ctx, hst);
+}
+
+lingam_status lingam_influence(lingam_ctx *ctx, const double *T, int64_t q, double *exert_out,
+                               double *receive_out, int32_t *exert_rank_out,
+                               int32_t *receive_rank_out, lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!T) return fail(ctx, LINGAM_ERR_ARG, "T is NULL");
+    if (q < 1 || q > 12000) return fail(ctx, LINGAM_ERR_ARG, "need 1 <= q <= 12000");
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    lingam_status st;
+    if ((st = begin_call(ctx, user))) return st;
+    CK(ensure(ctx->eOut, (size_t)q * 16 + 64));
+    CK(ensure(ctx->ePos, (size_t)q * 8 + 64));
+    const void *dT = nullptr;
+    if ((st = device_view(ctx, T, (size_t)q * q * 8, ctx->eIn, &dT))) return st;
+    double *ex = ptr<double>(ctx->eOut), *rc = ex + q;
+    int32_t *rex = ptr<int32_t>(ctx->ePos), *rrc = rex + q;
+    CK(launch_influence((const double *)dT, (int)q, ex, rc, rex, rrc, ctx->s));
+    if (exert_out) CK(cudaMemcpyAsync(exert_out, ex, q * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if (receive_out) CK(cudaMemcpyAsync(receive_out, rc, q * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if (exert_rank_out)
+        CK(cudaMemcpyAsync(exert_rank_out, rex, q * 4, cudaMemcpyDeviceToHost, ctx->s));
+    if (receive_rank_out)
+        CK(cudaMemcpyAsync(receive_rank_out, rrc, q * 4, cudaMemcpyDeviceToHost, ctx->s));
+    return end_call(ctx, user);
+}
+
+lingam_status lingam_bootstrap_edge_stats(lingam_ctx *ctx, const double *const *B, int32_t count,
+                                          int64_t d, double threshold, double *prob_out,
+                                          double *mean_out, lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!B || count < 1 || !prob_out || !mean_out)
+        return fail(ctx, LINGAM_ERR_ARG, "need B, count >= 1, prob_out and mean_out");
+    if (d < 1 || d > 12000) return fail(ctx, LINGAM_ERR_ARG, "need 1 <= d <= 12000");
+    if (!(threshold >= 0.0)) return fail(ctx, LINGAM_ERR_ARG, "threshold must be >= 0");
+    for (int k = 0; k < count; ++k)
+        if (!B[k]) return fail(ctx, LINGAM_ERR_ARG, "a B pointer is NULL");
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    lingam_status st;
+    if ((st = begin_call(ctx, user))) return st;
+    const size_t mat = (size_t)d * d * 8;
+    std::vector<const double *> dptr(count);
+    size_t host_mats = 0;
+    for (int k = 0; k < count; ++k) host_mats += is_device_ptr(B[k]) ? 0 : 1;
+    CK(ensure(ctx->eIn, std::max<size_t>(host_mats * mat, 256)));
+    size_t h = 0;
+    for (int k = 0; k < count; ++k) {
+        if (is_device_ptr(B[k])) {
+            dptr[k] = B[k];
+        } else {
+            char *dst = reinterpret_cast<char *>(ctx->eIn.p) + h * mat;
+            CK(cudaMemcpyAsync(dst, B[k], mat, cudaMemcpyHostToDevice, ctx->s));
+            dptr[k] = reinterpret_cast<const double *>(dst);
+            ++h;
+        }
+    }
+    CK(ensure(ctx->ePtr, (size_t)count * sizeof(void *)));
+    CK(ensure(ctx->eOut, 2 * mat));
+    CK(ensure(ctx->eStatus, 256));
+    uint32_t *status = ptr<uint32_t>(ctx->eStatus);
+    CK(cudaMemsetAsync(status, 0, 4, ctx->s));
+    CK(cudaMemcpyAsync(ctx->ePtr.p, dptr.data(), (size_t)count * sizeof(void *),
+                       cudaMemcpyHostToDevice, ctx->s));
+    double *prob = ptr<double>(ctx->eOut), *mean = prob + (size_t)d * d;
+    CK(launch_edge_stats(reinterpret_cast<const double *const *>(ctx->ePtr.p), count, (int)d,
+                         threshold, prob, mean, status, ctx->s));
+    CK(cudaMemcpyAsync(prob_out, prob, mat, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(mean_out, mean, mat, cudaMemcpyDeviceToHost, ctx->s));
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    return status_to_code(ctx, hst);
+}
+
+static lingam_status check_tuning(lingam_ctx *ctx, const lingam_tuning &t)
+{
+    if (t.precision != LINGAM_PREC_FP32 && t.precision != LINGAM_PREC_MIXED)
+        return fail(ctx, LINGAM_ERR_ARG, "tuning tables exist for the FP32 and MIXED forms only");
+    if (t.count < 1 || t.count > 8) return fail(ctx, LINGAM_ERR_ARG, "tuning count must be 1..8");
+    for (int b = 0; b < t.count; ++b) {
+        if (t.tile[b] < 0 || t.tile[b] >= PAIR_NCFG)
+            return fail(ctx, LINGAM_ERR_ARG, "tuning tile index out of range");
+        if (t.ctas_per_sm[b] < 1 || t.ctas_per_sm[b] > 64)
+            return fail(ctx, LINGAM_ERR_ARG, "tuning ctas_per_sm must be 1..64");
+        if (b > 0 && t.p_max[b] <= t.p_max[b - 1])
+            return fail(ctx, LINGAM_ERR_ARG, "tuning p_max must ascend");
+    }
+    return LINGAM_OK;
+}
+
+lingam_status lingam_set_tuning(lingam_ctx *ctx, const lingam_tuning *t)
+{
+    if (!ctx || !t) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    lingam_status st = check_tuning(ctx, *t);
+    if (st) return st;
+    CK(cudaSetDevice(ctx->device));
+    ctx->tune[t->precision == LINGAM_PREC_MIXED ? 1 : 0] = *t;
+    destroy_plan(ctx->plan);
+    return LINGAM_OK;
+}
+
+lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam_tuning *out)
+{
+    if (!ctx || !out) return LINGAM_ERR_ARG;
+    if (precision != LINGAM_PREC_FP32 && precision != LINGAM_PREC_MIXED) return LINGAM_ERR_ARG;
+    *out = ctx->tune[precision == LINGAM_PREC_MIXED ? 1 : 0];
+    return LINGAM_OK;
+}
+
+// Times one pair-kernel launch of configuration cfg on the synthetic columns
+// (minimum of three runs after a warm-up).
+static lingam_status time_pair(lingam_ctx *ctx, int mode, int cfg, const CUtensorMap *tI,
+                               const CUtensorMap *tJ, PairParams P, PairParams *dP, int *dprefix,
+                               int ctas_target, cudaEvent_t a, cudaEvent_t b, double *ms_out)
+{
+    const int tiles = pair_tiles(P.p, cfg);
+    P.tiles_i = (P.p + PAIR_CFGS[cfg].ti() - 1) / PAIR_CFGS[cfg].ti();
+    P.tiles_j = (P.p + PAIR_CFGS[cfg].tj() - 1) / PAIR_CFGS[cfg].tj();
+    pair_split(tiles, (int64_t)ctx->num_sms * ctas_target, P.nchunks, &P.cps, &P.nsplit);
+    const int total = tiles * P.nsplit;
+    const int prefix[2] = {0, total};
+    CK(cudaMemcpyAsync(dP, &P, sizeof(PairParams), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(dprefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice, ctx->s));
+    CK(launch_pair_b(mode, cfg, tI, tJ, dP, dprefix, 1, total, ctx->s));
+    double best = 1e30;
+    for (int r = 0; r < 3; ++r) {
+        CK(cudaEventRecord(a, ctx->s));
+        CK(launch_pair_b(mode, cfg, tI, tJ, dP, dprefix, 1, total, ctx->s));
+        CK(cudaEventRecord(b, ctx->s));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        best = std::min(best, (double)ms);
+    }
+    *ms_out = best;
+    return LINGAM_OK;
+}
+
+lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuning *out)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    const int prec = ctx->opts.precision;
+    if (prec != LINGAM_PREC_FP32 && prec != LINGAM_PREC_MIXED)
+        return fail(ctx, LINGAM_ERR_ARG, "autotune needs the FP32 or MIXED form");
+    if (n < 2 || d < 2 || d > 6000) return fail(ctx, LINGAM_ERR_ARG, "need n >= 2, 2 <= d <= 6000");
+    CK(cudaSetDevice(ctx->device));
+    destroy_plan(ctx->plan);
+    const int mode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
+    const int nprobe = (int)std::min<int64_t>(n, 131072);
+    lingam_tuning tb{};
+    tb.precision = prec;
+    tb.n_probe = nprobe;
+    // buckets (32, 64], (64, 128], ... up to the one holding d; probes capped at 2048
+    for (int edge = 64; tb.count < 8; edge *= 2) {
+        const bool last = edge >= d || tb.count == 7;
+        tb.p_max[tb.count] = last ? INT32_MAX : edge;
+        tb.p_probe[tb.count] = (int)std::min<int64_t>(std::min<int64_t>(edge, d), 2048);
+        ++tb.count;
+        if (last) break;
+    }
+    int pmax = 0;
+    for (int b = 0; b < tb.count; ++b) pmax = std::max(pmax, tb.p_probe[b]);
+    pmax = std::max(pmax, 2);
+    const int64_t ldz = roundup(std::max<int64_t>(nprobe, PAIR_S), 64);
+    const int nch = pair_nchunks(nprobe);
+    int64_t mom_elems = 0;
+    for (int b = 0; b < tb.count; ++b)
+        for (int c = 0; c < PAIR_NCFG; ++c)
+            for (int m = 1; m <= 4; m *= 2) {
+                int cps = 1, ns = 1;
+                pair_split(pair_tiles(tb.p_probe[b], c),
+                           (int64_t)ctx->num_sms * pair_ctas_per_sm(mode, c) * m, nch, &cps, &ns);
+                mom_elems = std::max<int64_t>(mom_elems,
+                                              (int64_t)ns * tb.p_probe[b] * tb.p_probe[b] * 2);
+            }
+    Buf z, C, U, isd, mom, status, dP, dpre;
+    auto cleanup = [&]() {
+        release(z);
+        release(C);
+        release(U);
+        release(isd);
+        release(mom);
+        release(status);
+        release(dP);
+        release(dpre);
+    };
+    cudaEvent_t a = nullptr, b = nullptr;
+    lingam_status st = [&]() -> lingam_status {
+        CK(ensure(z, (size_t)pmax * ldz * 4));
+        CK(ensure(C, (size_t)pmax * pmax * 8, true));      // rho = 0 for every pair
+        CK(ensure(U, (size_t)pmax * 4));
+        CK(ensure(isd, (size_t)pmax * 8));
+        CK(ensure(mom, (size_t)mom_elems * 8));
+        CK(ensure(status, 256, true));
+        CK(ensure(dP, sizeof(PairParams)));
+        CK(ensure(dpre, 64));
+        CK(launch_fill_test_z(ptr<float>(z), ldz, pmax, nprobe, ctx->s));
+        CK(launch_iota_plain(ptr<int32_t>(U), pmax, ctx->s));
+        std::vector<double> ones(pmax, 1.0);
+        CK(cudaMemcpyAsync(isd.p, ones.data(), pmax * 8, cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        CUtensorMap tI[PAIR_NCFG], tJ[PAIR_NCFG];
+        {
+            Plan tmp;
+            tmp.ldz = ldz;
+            tmp.zrows = pmax;
+            tmp.zarena = z;
+            lingam_status s2 = make_tensor_maps(ctx, tmp);
+            for (int c = 0; c < PAIR_NCFG; ++c) {
+                tI[c] = tmp.tmI[c];
+                tJ[c] = tmp.tmJ[c];
+            }
+            tmp.zarena = Buf{};
+            if (s2) return s2;
+        }
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        for (int bk = 0; bk < tb.count; ++bk) {
+            PairParams P{};
+            P.C = ptr<double>(C);
+            P.ldc = pmax;
+            P.U = ptr<int32_t>(U);
+            P.p = tb.p_probe[bk];
+            P.n = nprobe;
+            P.nchunks = nch;
+            P.mom = ptr<double>(mom);
+            P.status = ptr<uint32_t>(status);
+            P.row0 = 0;
+            P.isd = ptr<double>(isd);
+            double best = 1e30;
+            for (int c = 0; c < PAIR_NCFG; ++c)
+                for (int m = 1; m <= 4; m *= 2) {
+                    const int target = pair_ctas_per_sm(mode, c) * m;
+                    double ms = 0;
+                    lingam_status s2 = time_pair(ctx, mode, c, &tI[c], &tJ[c], P, ptr<PairParams>(dP),
+                                                 ptr<int>(dpre), target, a, b, &ms);
+                    if (s2) return s2;
+                    if (ms < best) {
+                        best = ms;
+                        tb.tile[bk] = c;
+                        tb.ctas_per_sm[bk] = target;
+                        tb.ms[bk] = ms;
+                    }
+                }
+        }
+        uint32_t hst = 0;
+        CK(cudaMemcpy(&hst, status.p, 4, cudaMemcpyDeviceToHost));
+        if (hst) return status_to_code(ctx, hst);
+        return LINGAM_OK;
+    }();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cleanup();
+    if (st) return st;
+    ctx->tune[mode == PAIR_FAST ? 1 : 0] = tb;
+    if (out) *out = tb;
     return LINGAM_OK;
 }
 

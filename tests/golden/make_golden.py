@@ -5,7 +5,7 @@ inputs of ``gen/``; nothing comes from the CUDA path.  Each file records the
 workload, its seed and the SHA-256 prefix of the generated float32 data, so a
 test can refuse to compare against data that drifted.
 
-    python tests/golden/make_golden.py cfg1 cfg2 cfg4 cfg5 cfg3 [--threads N]
+    python tests/golden/make_golden.py cfg1 cfg2 cfg4 cfg5 cfg3 long_n [--threads N]
 
 cfg3 (d=1000, n=10000) is ~1e5 core-seconds of FP64 libm work.
 """
@@ -54,6 +54,15 @@ def run_cfg(k, threads):
     order = oracle.causal_order(ds.X, threads=threads)
     write_order(f"cfg{k}", order,
                 header(f"cfg{k} d={ds.d} n={ds.n} seed={gen.SEEDS[k]}", ds.digest(),
+                       time.time() - t, threads))
+
+
+def run_long_n(threads):
+    ds = gen.long_n()
+    t = time.time()
+    order = oracle.causal_order(ds.X, threads=threads)
+    write_order("long_n", order,
+                header(f"long_n d={ds.d} n={ds.n} seed={gen.SEEDS[6]}", ds.digest(),
                        time.time() - t, threads))
 
 
@@ -108,6 +117,8 @@ def main():
             run_cfg4(a.threads)
         elif w == "cfg5":
             run_cfg5(a.threads)
+        elif w == "long_n":
+            run_long_n(a.threads)
         else:
             raise SystemExit(f"unknown workload {w}")
 

@@ -46,11 +46,32 @@ def test_binding_signatures_cover_the_header():
     assert set(pkg.SIGNATURES) == set(_declared())
 
 
-def test_struct_layouts_match_the_header():
+STRUCTS = {"Opts": "lingam_opts", "Stats": "lingam_stats", "Instance": "lingam_instance",
+           "Tuning": "lingam_tuning"}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Size and every field offset of the ctypes mirrors equal the C compiler's
+    for the structs of include/lingam.h."""
     import paper_2403_03772_gb300 as pkg
-    assert ctypes.sizeof(pkg.Opts) == 48
-    assert ctypes.sizeof(pkg.Stats) == 104
-    assert ctypes.sizeof(pkg.Instance) == 48
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lingam.h"',
+             'int main(void) {']
+    for py, c in STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in getattr(pkg, py)._fields_:
+            lines.append(f'printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        py, field, value = line.split()
+        cls = getattr(pkg, py)
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (py, field, got, value)
 
 
 def test_missing_library_fails_loudly(tmp_path):

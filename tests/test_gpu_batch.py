@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctx():
     import paper_2403_03772_gb300 as pkg
-    c = {p: pkg.Context(0, p) for p in ["fp32", "mixed"]}
+    c = {p: pkg.Context(0, p) for p in ["fp32", "mixed", "df"]}
     yield c
     for v in c.values():
         v.close()

@@ -3,7 +3,8 @@ oracle (element by element on the same seeded inputs).
 
 Orders must be identical integer permutations; per-step scores M(i) within
 1e-4 of the step's max |M| (+1e-12); first-step I(i, j) within a bound
-derived from FP32 moment errors; adjacency within 1e-5 absolute.
+derived from FP32 moment errors (1e-11 for the double-float form, 1e-10 for
+FP64); adjacency within 1e-5 absolute.
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ from gpu_util import B_ABS, read_golden_order, scores_close
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32", "mixed", "fp64"]
+PRECS = ["fp32", "mixed", "fp64", "df"]
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +57,9 @@ def test_first_step_measures_match_oracle(ctx, torch_cuda, prec, shape):
     ref = oracle.search_step(X.astype(np.float64))
     # I: FP32 moments carry ~1e-7 relative error; h = -K1 (m1-g)^2 - K2 m2^2
     # amplifies it by 2 K1 |m1 - g| <= ~20 -> a few e-6 absolute on I.
-    tolI = 1e-10 if prec == "fp64" else 5e-5
+    # double-float: terms carry <= ~3e-14 absolute error, so I stays far
+    # below the 1e-10 bound the re-score tier assumes for it
+    tolI = {"fp64": 1e-10, "df": 1e-11}.get(prec, 5e-5)
     assert np.max(np.abs(I - ref["I"])) < tolI
     scale = np.max(np.abs(ref["k_list"]))
     assert np.max(np.abs(M - ref["k_list"])) <= 1e-4 * scale + 1e-12
@@ -76,7 +79,7 @@ def test_cfg1_order_and_scores(ctx, torch_cuda, datasets, prec):
     assert scores_close(scores, ref_scores) <= 0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "df"])
 def test_cfg2_order_and_scores(ctx, torch_cuda, datasets, prec):
     ds = datasets("cfg2")
     gold, dig = read_golden_order("cfg2")
@@ -172,3 +175,22 @@ def test_stats_report_the_run(ctx, torch_cuda, datasets):
     c.causal_order(_dev(torch_cuda, ds.X, "fp32"))
     st = c.stats()
     assert st["total_ms"] > 0 and st["graph_nodes"] >= 7 * (ds.d - 1)
+
+
+@pytest.mark.parametrize("tie", [300.0, 1e7])
+def test_rescore_tiers_keep_the_order(torch_cuda, datasets, tie):
+    """Widened error bounds push many steps through the double-float tier
+    (and, at 1e7, the double-float near-ties on to FP64); the order and the
+    scores must still be the oracle's."""
+    import paper_2403_03772_gb300 as pkg
+    ds = datasets("cfg2")
+    gold, _ = read_golden_order("cfg2")
+    with pkg.Context(0, "mixed", tie_scale=tie) as c:
+        order, scores = c.causal_order(_dev(torch_cuda, ds.X, "mixed"), scores=True)
+        st = c.stats()
+    assert list(order) == list(gold)
+    assert st["df_candidates"] > 0
+    if tie > 1e4:
+        assert st["fp64_candidates"] > 0
+    _, ref_scores = oracle.causal_order(ds.X, scores=True)
+    assert scores_close(scores, ref_scores) <= 0
