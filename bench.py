@@ -331,6 +331,10 @@ def run_ours(args, rank, world):
                      "residual_samples": Wl, "ms_per_order": lmax / args.steps,
                      "value": job_throughput(Wl, world, args.steps, lmax),
                      "pair_kernel_ms_per_order": sum(s["pair_ms"] for s in lst) / len(lst),
+                     "phase_ms_per_order": {
+                         k: sum(s[k] for s in lst) / len(lst)
+                         for k in ("pair_ms", "score_ms", "refine_ms", "regress_ms")},
+                     "df_candidates": lst[-1]["df_candidates"],
                      "refined_steps": lst[-1]["refined_steps"],
                      "order_head": [int(v) for v in lorder[:8]]}
         del Xl
@@ -432,6 +436,7 @@ def run_ours(args, rank, world):
                       "df_candidates": forms[p]["df_candidates"],
                       "phase_ms_per_step": forms[p]["phase_ms_per_step"],
                       "genuine_ties": forms[p]["genuine_ties"],
+                      "tuning": forms[p]["tuning"],
                       "order_head": forms[p]["order_head"]} for p in args.forms},
         "batched": batch_info,
         "long_n": long_info,
