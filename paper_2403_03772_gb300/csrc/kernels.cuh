@@ -72,11 +72,14 @@ struct HpParams {
     int mode;             // 0: all pairs + variables; 1: re-score of candidates
     int with_vars;        // mode 1: also the variable moments
     const DevState *state;
-    double *mom;          // mode 0: [p][p][2]; mode 1: [d][p][4] by candidate slot
-    double *hz;           // [p][2] variable moment sums
+    double *mom;          // mode 0: [nsplit][p][p][2]; mode 1: [nsplit][d][p][4] by candidate slot
+    double *hz;           // [nsplit][p][2] variable moment sums
     uint32_t *status;
     const float *I32;     // mode 1: [p][p] FP32-path I(i, j), or null
     double epsI;          // bound on |I32 - I| (entries with I32 >= epsI are skipped)
+    int nsplit;           // sample ranges per work item (partial sums per range)
+    int sps;              // samples per range
+    int64_t mom_sstride;  // elements between the ranges' moment records
 };
 
 struct ScoreParams {
@@ -105,9 +108,11 @@ struct SelectParams {
 };
 
 struct RefineSelectParams {
-    const double *mom;    // [d][p][4] by candidate slot
-    const double *hz;     // [p][2]
+    const double *mom;    // [nsplit][d][p][4] by candidate slot
+    const double *hz;     // [nsplit][p][2]
     int p, n;
+    int nsplit;           // partial records per value, summed in range order
+    int64_t mom_sstride;
     const int32_t *U;
     DevState *state;
     double *hist;         // optional row of the score history

@@ -244,14 +244,22 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
         npair = (int64_t)P.p * (P.p - 1) / 2;
     }
     const int64_t nitems = npair + (with_vars ? P.p : 0);
-    if ((int64_t)blockIdx.x >= nitems) return;
+    const int64_t nunits = nitems * P.nsplit;
+    if ((int64_t)blockIdx.x >= nunits) return;
     if (TIER == 1) {
         for (int k = threadIdx.x; k < EXP_TAB; k += blockDim.x) s_exp[k] = g_exp_tab[k];
         for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) s_log[k] = g_log_tab[k];
         __syncthreads();
     }
-    const int n = P.n;
-    for (int64_t q = blockIdx.x; q < nitems; q += gridDim.x) {
+    for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        // work unit = (item q, sample range sp); each range writes its own
+        // partial record, summed in range order by the consumer
+        const int64_t q = unit / P.nsplit;
+        const int sp = (int)(unit % P.nsplit);
+        const int s0 = (int)((int64_t)sp * P.sps);
+        const int n = (int)std::min<int64_t>(P.n, (int64_t)s0 + P.sps);
+        double *momp = P.mom + (size_t)sp * P.mom_sstride;
+        double *hzp = P.hz + (size_t)sp * P.p * 2;
         if (q >= npair) {
             // moments of the standardised variable at position a
             const int a = (int)(q - npair);
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
                 const float *zh = P.zhi + (int64_t)a * P.ldz, *zl = P.zlo + (int64_t)a * P.ldz;
                 DfAcc A1, A2;
                 int cnt = 0;
-                for (int s = threadIdx.x; s < n; s += blockDim.x) {
+                for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
                     dfl t1, t2;
                     df_terms(dfl{zh[s], zl[s]}, t1, t2, s_exp, s_log);
                     A1.add(t1);
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
                 const double inv = 1.0 / sqrt(P.C[(int64_t)oa * P.ldc + oa]);
                 const double *ra = P.R + (int64_t)oa * P.ldr;
                 double s1 = 0.0, s2 = 0.0;
-                for (int s = threadIdx.x; s < n; s += blockDim.x) {
+                for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
                     double t1, t2;
                     f64_terms(ra[s] * inv, t1, t2);
                     s1 += t1;
@@ -291,8 +299,8 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             }
             block_sum_fixed<2>(v, s_red);
             if (threadIdx.x == 0) {
-                P.hz[(size_t)a * 2 + 0] = v[0];
-                P.hz[(size_t)a * 2 + 1] = v[1];
+                hzp[(size_t)a * 2 + 0] = v[0];
+                hzp[(size_t)a * 2 + 1] = v[1];
             }
             continue;
         }
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             // I32(a, b) >= epsI proves I(a, b) >= 0: min(0, I)^2 = 0 exactly,
             // so the entry needs no moments (marked by a negative sum)
             if (a == b || (P.I32 && P.I32[(size_t)a * P.p + b] >= P.epsI)) {
-                if (threadIdx.x == 0) {
+                if (threadIdx.x == 0 && sp == 0) {   // the marker lives in range 0
                     double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
                     o[0] = -1.0;
                     o[1] = o[2] = o[3] = 0.0;
@@ -345,7 +353,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             const float *zbh = P.zhi + (int64_t)b * P.ldz, *zbl = P.zlo + (int64_t)b * P.ldz;
             DfAcc A1, A2, B1, B2;
             int cnt = 0;
-            for (int s = threadIdx.x; s < n; s += blockDim.x) {
+            for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
                 const dfl za{zah[s], zal[s]}, zb{zbh[s], zbl[s]};
                 dfl t1, t2;
                 df_terms(df_resid(al, be, za, zb), t1, t2, s_exp, s_log);
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             const double ib = 1.0 / sqrt(P.C[(int64_t)ob * P.ldc + ob]);
             const double *ra = P.R + (int64_t)oa * P.ldr, *rb = P.R + (int64_t)ob * P.ldr;
             double ab1 = 0.0, ab2 = 0.0, ba1 = 0.0, ba2 = 0.0;
-            for (int s = threadIdx.x; s < n; s += blockDim.x) {
+            for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
                 const double za = ra[s] * ia, zb = rb[s] * ib;
                 double t1, t2;
                 f64_terms((za - rho * zb) * alpha, t1, t2);
@@ -393,16 +401,16 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
         block_sum_fixed<4>(v, s_red);
         if (threadIdx.x == 0) {
             if (P.mode == 1) {
-                double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
+                double *o = momp + ((size_t)cidx * P.p + b) * 4;
                 o[0] = v[0];
                 o[1] = v[1];
                 o[2] = v[2];
                 o[3] = v[3];
             } else {
-                double *o = P.mom + ((size_t)a * P.p + b) * 2;
+                double *o = momp + ((size_t)a * P.p + b) * 2;
                 o[0] = v[0];
                 o[1] = v[1];
-                o = P.mom + ((size_t)b * P.p + a) * 2;
+                o = momp + ((size_t)b * P.p + a) * 2;
                 o[0] = v[2];
                 o[1] = v[3];
             }
@@ -465,8 +473,14 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
     const int cb = st->pass_begin, ce = st->pass_end, nc = st->ncand;
     const double invn = 1.0 / (double)P.n;
     const double eps = P.tier == 1 ? P.epsI : 0.0;
-    for (int j = threadIdx.x; j < P.p; j += blockDim.x)
-        h64[j] = neg_entropy_part(P.hz[(size_t)j * 2] * invn - LN2_D, P.hz[(size_t)j * 2 + 1] * invn);
+    for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int sp = 0; sp < P.nsplit; ++sp) {
+            s1 += P.hz[((size_t)sp * P.p + j) * 2];
+            s2 += P.hz[((size_t)sp * P.p + j) * 2 + 1];
+        }
+        h64[j] = neg_entropy_part(s1 * invn - LN2_D, s2 * invn);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = cb + w; c < ce; c += nw) {
@@ -474,8 +488,12 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
         double acc = 0.0, err = 0.0;
         for (int j = lane; j < P.p; j += 32) {
             if (j == pc) continue;
-            const double *o = P.mom + ((size_t)c * P.p + j) * 4;
-            if (o[0] < 0.0) continue;
+            const size_t rec = ((size_t)c * P.p + j) * 4;
+            if (P.mom[rec] < 0.0) continue;     // skipped entry (marker in range 0)
+            double o[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int sp = 0; sp < P.nsplit; ++sp)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] += P.mom[(size_t)sp * P.mom_sstride + rec + k];
             const double hcj = neg_entropy_part(o[0] * invn - LN2_D, o[1] * invn);
             const double hjc = neg_entropy_part(o[2] * invn - LN2_D, o[3] * invn);
             const double I = (h64[j] + hcj) - (h64[pc] + hjc);

@@ -101,7 +101,7 @@ struct InstDev {
     DevState *state = nullptr;
     int zrow = 0;
     int ksplit = 1;
-    size_t mom_elems = 0, hz_elems = 0;
+    size_t mom_elems = 0, hz_elems = 0, fmom_elems = 0, fhz_elems = 0;
     // tensor-core covariance (mixed form): digit planes, scale exponents, map
     __nv_bfloat16 *S = nullptr;
     int *expo = nullptr;
@@ -112,6 +112,7 @@ struct InstDev {
 // Sample-split decisions of one global step (shared by sizing and capture).
 struct StepSplit {
     std::vector<int> pair_nsplit, pair_cps, reg_nsplit, reg_sps;
+    std::vector<int> hp0_nsplit, hp1_nsplit;   // sample ranges of the high-precision kernel
     int cfg = 0;           // pair-kernel tile configuration of the step
 };
 
@@ -232,11 +233,23 @@ static void default_tuning(lingam_tuning &tb, int prec)
 // in total to fill the GPU, never more splits than chunks.  The pair kernel's
 // tile configuration and split target come from the tuning table at the
 // largest p of the step.
+// Sample ranges per work item of the high-precision kernel: enough work units
+// for about eight 256-thread blocks per SM, each range at least 4096 samples.
+static int hp_splits(const lingam_ctx *ctx, int64_t items, int64_t n, int count)
+{
+    const int64_t target = std::max<int64_t>(1, (int64_t)ctx->num_sms * 8 / std::max(1, count));
+    int64_t s = (target + std::max<int64_t>(items, 1) - 1) / std::max<int64_t>(items, 1);
+    s = std::min<int64_t>(s, std::max<int64_t>(1, n / 4096));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
+}
+
 static StepSplit step_splits(const lingam_ctx *ctx, const std::vector<InstSpec> &spec, int prec,
                              int t)
 {
     const int K = (int)spec.size();
     StepSplit ss;
+    ss.hp0_nsplit.assign(K, 1);
+    ss.hp1_nsplit.assign(K, 1);
     ss.pair_nsplit.assign(K, 1);
     ss.pair_cps.assign(K, 1);
     ss.reg_nsplit.assign(K, 1);
@@ -263,9 +276,16 @@ static StepSplit step_splits(const lingam_ctx *ctx, const std::vector<InstSpec> 
         const int sps = (int)((n + nr - 1) / nr);
         ss.reg_sps[k] = sps;
         ss.reg_nsplit[k] = (int)((n + sps - 1) / sps);
+        const int64_t p = std::max<int64_t>(2, spec[k].d - t);
+        // mode 0 items: every pair and variable; mode 1: about two candidates'
+        // rows plus the variables
+        ss.hp0_nsplit[k] = hp_splits(ctx, p * (p - 1) / 2 + p, n, K);
+        ss.hp1_nsplit[k] = hp_splits(ctx, 3 * p, n, K);
     }
     return ss;
 }
+
+static int hp_sps(int64_t n, int nsplit) { return (int)((n + nsplit - 1) / nsplit); }
 
 static lingam_status make_tensor_maps(lingam_ctx *ctx, Plan &pl)
 {
@@ -336,6 +356,8 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         pl.inst[k].ldr = roundup(spec[k].n, 32);
         pl.inst[k].ksplit = gram_ksplit((int)spec[k].n, (int)spec[k].d, ctx->num_sms);
         pl.inst[k].mom_elems = (size_t)spec[k].d * spec[k].d * 2;
+        pl.inst[k].fmom_elems = (size_t)spec[k].d * spec[k].d * 4;
+        pl.inst[k].fhz_elems = (size_t)spec[k].d * 2;
     }
     for (int t = 0; t + 1 < std::max(2, pl.maxd); ++t) {
         StepSplit ss = step_splits(ctx, spec, prec, t);
@@ -348,6 +370,13 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
             if (!step_hp(prec, (int)p))
                 pl.inst[k].mom_elems =
                     std::max(pl.inst[k].mom_elems, (size_t)ss.pair_nsplit[k] * p * p * 2);
+            else
+                pl.inst[k].mom_elems =
+                    std::max(pl.inst[k].mom_elems, (size_t)ss.hp0_nsplit[k] * p * p * 2);
+            const size_t hs = (size_t)std::max(ss.hp0_nsplit[k], ss.hp1_nsplit[k]);
+            pl.inst[k].fhz_elems = std::max(pl.inst[k].fhz_elems, hs * p * 2);
+            pl.inst[k].fmom_elems = std::max(pl.inst[k].fmom_elems,
+                                             (size_t)ss.hp1_nsplit[k] * spec[k].d * p * 4);
             pl.inst[k].hz_elems =
                 std::max(pl.inst[k].hz_elems, (size_t)ss.reg_nsplit[k] * (size_t)p * 2);
         }
@@ -378,8 +407,8 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].E = take((size_t)d * 8);
         o[k].hist = scores ? take((size_t)d * d * 8) : 0;
         o[k].ref = take((size_t)d * 8);
-        o[k].fmom = take((size_t)d * d * 4 * 8);
-        o[k].fhz = take((size_t)d * 2 * 8);
+        o[k].fmom = take(pl.inst[k].fmom_elems * 8);
+        o[k].fhz = take(pl.inst[k].fhz_elems * 8);
         o[k].lcoef = lcoef ? take((size_t)d * d * 8) : 0;
         o[k].U = take((size_t)2 * d * 4);
         o[k].order = take((size_t)d * 4);
@@ -640,15 +669,18 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 F.mom = mom;
                 F.hz = I.fhz;
                 F.status = &I.state->status;
+                F.nsplit = mode == 0 ? ss.hp0_nsplit[k] : ss.hp1_nsplit[k];
+                F.sps = hp_sps(n, F.nsplit);
+                F.mom_sstride = mode == 0 ? (int64_t)p * p * 2 : (int64_t)I.d * p * 4;
                 return F;
             };
             ScoreParams S{};
             if (hp) {
                 fa.push_back(hpp(0, 1, I.mom));
                 S.mom = I.mom;
-                S.nsplit = 1;
+                S.nsplit = ss.hp0_nsplit[k];
                 S.hz = I.fhz;
-                S.nsplit_hz = 1;
+                S.nsplit_hz = ss.hp0_nsplit[k];
                 S.a1 = 1.0;
                 S.b1 = -LN2_D;
                 S.a2 = 1.0;
@@ -699,9 +731,14 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             fd2.push_back(hpp(1, 0, I.fmom));
             f64.push_back(hpp(1, 1, I.fmom));
             const double e2 = DF_EPS_I * tie;
-            rd1.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 1, e2});
-            rd2.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 1, e2});
-            r64.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, Uc, I.state, hist_row, 2, 0.0});
+            const int ns1 = ss.hp1_nsplit[k];
+            const int64_t fst = (int64_t)I.d * p * 4;
+            rd1.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, ns1, fst, Uc, I.state, hist_row,
+                                             1, e2});
+            rd2.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, ns1, fst, Uc, I.state, hist_row,
+                                             1, e2});
+            r64.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, ns1, fst, Uc, I.state, hist_row,
+                                             2, 0.0});
             rg.push_back(regress_params(I, t, p, Uc, Un, ss.reg_sps[k], false));
             nsplit_hz[k] = ss.reg_nsplit[k];
             maxcols = std::max(maxcols, p - 1);
@@ -710,7 +747,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         }
         if (sc.empty()) break;
         const int cnt = (int)sc.size();
-        const int hp_blocks = std::max(1, ctx->num_sms * 4 / cnt);
+        const int hp_blocks = std::max(1, ctx->num_sms * 8 / cnt);
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t;
@@ -731,7 +768,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             Launch l{K_HP_ALL};
             l.off = blob.add(fa);
             l.count = (int)fa.size();
-            l.a = std::max(1, ctx->num_sms * 4 / (int)fa.size());
+            l.a = std::max(1, ctx->num_sms * 8 / (int)fa.size());
             l.c = step_hp_tier(prec);
             L.push_back(l);
         }

@@ -194,3 +194,20 @@ def test_rescore_tiers_keep_the_order(torch_cuda, datasets, tie):
         assert st["fp64_candidates"] > 0
     _, ref_scores = oracle.causal_order(ds.X, scores=True)
     assert scores_close(scores, ref_scores) <= 0
+
+
+@pytest.mark.parametrize("prec,tie", [("mixed", 300.0), ("fp32", 100.0), ("df", 1.0)])
+def test_split_sample_ranges_keep_the_order(torch_cuda, prec, tie):
+    """n = 40000 cuts every high-precision work item into several sample
+    ranges (partial sums added in range order); widened bounds send many
+    candidates through those passes.  Order and scores stay the oracle's."""
+    import paper_2403_03772_gb300 as pkg
+    X, _ = _random_sem(21, 40000, 60)
+    with pkg.Context(0, prec, tie_scale=tie) as c:
+        order, scores = c.causal_order(_dev(torch_cuda, X, prec), scores=True)
+        st = c.stats()
+    ref, ref_scores = oracle.causal_order(X, scores=True)
+    assert list(order) == list(ref)
+    assert scores_close(scores, ref_scores) <= 0
+    if prec != "df":
+        assert st["df_candidates"] > 0
