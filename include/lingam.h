@@ -171,12 +171,36 @@ lingam_status lingam_causal_order_batch(lingam_ctx *ctx, const lingam_instance *
 /*
  * Scores of the first ordering step only, for parity checks: I_out optional
  * host double[d*d] with I(i, j) of Algorithm 1 at original indices (diagonal
- * 0); M_out optional host double[d] with M(i).  Same data rules as
+ * 0); M_out optional host double[d] with M(i); eps_out optional host
+ * double[d*d] with the bound on |I_out - I_exact| that the library uses to
+ * pick the candidates it re-scores (from its moment-error model in the FP32
+ * and MIXED forms, a fixed 1e-12 in DF, 0 in FP64).  Same data rules as
  * lingam_causal_order.
  */
 lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
                                    int64_t ld, int32_t layout, double *I_out, double *M_out,
-                                   lingam_stream_t stream);
+                                   double *eps_out, lingam_stream_t stream);
+
+/*
+ * Sparse weighted adjacency on a causal order.  The paper only says the
+ * adjacency comes from "regressing" each variable on the ones before it
+ * (Sec. 1); this is the pruned reading: for every variable k with
+ * predecessors P, the adaptive lasso of Zou (2006) in covariance form,
+ *     min_b 1/2 b'C_PP b - b'C_Pk + lam sum_j w_j |b_j|,  w_j = |b_ols_j|^-gamma,
+ * on the centred FP64 covariance C = Xc'Xc/n, by cyclic coordinate descent
+ * over P in order, warm-started along lam_i = lam_max eps^(i/(n_lambda-1)),
+ * i = 0..n_lambda-1 (lam_max = max_j |C_jk| / w_j), each lam's sweeps ending
+ * once the largest change |db_j| sqrt(C_jj) <= 1e-10 sqrt(C_kk); the lam with
+ * the smallest BIC = n log(RSS/n) + df log n (first minimum) gives row k.
+ *   X, n, d, ld, layout, order: as lingam_fit_adjacency.
+ *   gamma > 0 (1 is usual), 2 <= n_lambda <= 1000, 0 < eps < 1 (60, 1e-6
+ *   are the library's test settings).
+ *   B_out: double[d*d], host memory, or device memory if B_on_device.
+ */
+lingam_status lingam_prune_adjacency(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
+                                     int64_t ld, int32_t layout, const int32_t *order,
+                                     double gamma, int32_t n_lambda, double eps, double *B_out,
+                                     int32_t B_on_device, lingam_stream_t stream);
 
 /*
  * Total causal effects (Sec. 4.2 ranks nodes "by measuring the total causal
@@ -231,7 +255,7 @@ lingam_status lingam_bootstrap_edge_stats(lingam_ctx *ctx, const double *const *
  * Tile shapes and split schedules of the FP32 pair-moment kernel, by range of
  * the number p of remaining variables.  Bucket b covers
  * p_max[b-1] < p <= p_max[b] (p_max ascending; the last bucket also covers
- * every larger p).  tile[b] indexes the kernel's tile configurations (0..4:
+ * every larger p).  tile[b] indexes the kernel's tile configurations (0..6:
  * warps x pairs per warp, see the library's design notes); ctas_per_sm[b] is
  * the number of CTAs per SM the sample splits aim for; ms[b] the kernel time
  * measured at the probe size p_probe[b] with n_probe samples.  One table per

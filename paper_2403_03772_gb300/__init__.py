@@ -92,12 +92,14 @@ SIGNATURES = {
     "lingam_fit_adjacency": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _I32, _P]),
     "varlingam_fit": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _I32, _P, _P, _P, _P]),
     "lingam_causal_order_batch": (_I32, [_P, ctypes.POINTER(Instance), _I32, _P, _P, _P, _P]),
-    "lingam_step_measures": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _P]),
+    "lingam_step_measures": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _P, _P, _P]),
     "lingam_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "lingam_peak_probe": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "lingam_step_scores_noalloc": (_I32, [_P, _I64, _I64, _I64, _P, _P]),
     "lingam_autotune": (_I32, [_P, _I64, _I64, ctypes.POINTER(Tuning)]),
     "lingam_total_effects": (_I32, [_P, _P, _I64, _P, _P, _I32, _P]),
+    "lingam_prune_adjacency": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _D, _I32, _D, _P, _I32,
+                                      _P]),
     "varlingam_total_effects": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _I32, _P]),
     "lingam_influence": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P]),
     "lingam_bootstrap_edge_stats": (_I32, [_P, _P, _I32, _I64, _D, _P, _P, _P]),
@@ -248,14 +250,17 @@ class Context:
         self._check(code)
         return (order, sc) if scores else order
 
-    def step_measures(self, X):
-        """(I [d, d], M [d]) of the first ordering step."""
+    def step_measures(self, X, bounds: bool = False):
+        """(I [d, d], M [d]) of the first ordering step; with ``bounds`` also
+        the per-entry bound on |I - I_exact| the library works with."""
         p, n, d, ld, lay, keep = _matrix(X, self._dtype())
         I = np.empty((d, d))
         M = np.empty(d)
+        eps = np.empty((d, d)) if bounds else None
         self._check(self._lib.lingam_step_measures(self._h, p, n, d, ld, lay, _ptr(I), _ptr(M),
+                                                   _ptr(eps) if bounds else None,
                                                    _stream_of([keep])))
-        return I, M
+        return (I, M, eps) if bounds else (I, M)
 
     def fit_adjacency(self, X, order, out=None):
         p, n, d, ld, lay, keep = _matrix(X, np.float32)
@@ -269,6 +274,18 @@ class Context:
         B = np.empty((d, d))
         self._check(self._lib.lingam_fit_adjacency(self._h, p, n, d, ld, lay, _ptr(order),
                                                    _ptr(B), 0, _stream_of([keep])))
+        return B
+
+    def prune_adjacency(self, X, order, gamma: float = 1.0, n_lambda: int = 60,
+                        eps: float = 1e-6):
+        """Sparse adjacency: adaptive lasso + BIC of each variable on its
+        predecessors in ``order`` (host float64 [d, d])."""
+        p, n, d, ld, lay, keep = _matrix(X, np.float32)
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        B = np.empty((d, d))
+        self._check(self._lib.lingam_prune_adjacency(self._h, p, n, d, ld, lay, _ptr(order),
+                                                     float(gamma), int(n_lambda), float(eps),
+                                                     _ptr(B), 0, _stream_of([keep])))
         return B
 
     def varlingam_fit(self, Xt, lags: int = 1):

@@ -181,6 +181,20 @@ __device__ __forceinline__ double warp_sum_xor(double v)
     return v;
 }
 
+// Neumaier's compensated running sum in FP32 (the rounding error of every
+// addition is carried in c; value() adds the two in FP64).
+struct CompSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x)
+                                              : __fadd_rn(__fsub_rn(x, t), s));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Block-wide sum in a fixed order (warp xor trees, then warp 0 over the
 // per-warp totals); the result is valid in warp 0.
 __device__ __forceinline__ double block_sum(double v, double *sh)

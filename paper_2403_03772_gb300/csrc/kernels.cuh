@@ -18,17 +18,20 @@ namespace lg {
 struct PairCfg {
     int wi, wj, wgi, wgj, stages;
     int reg_fast, reg_acc;   // register cap per thread (fast / accurate form)
+    int groups;              // groups of 4 samples per lane and iteration (1 or 2)
     constexpr int ti() const { return wi * wgi; }
     constexpr int tj() const { return wj * wgj; }
     constexpr int warps() const { return wgi * wgj; }
     constexpr int threads() const { return 32 * wgi * wgj; }
 };
 constexpr PairCfg PAIR_CFGS[] = {
-    {4, 4, 2, 4, 4, 248, 120},   // 0: 256 threads, 8 x 16 tile
-    {4, 4, 1, 4, 3, 168, 128},   // 1: 128 threads, 4 x 16 tile
-    {4, 2, 2, 4, 4, 128, 80},    // 2: 256 threads, 8 x 8 tile
-    {2, 4, 2, 4, 4, 128, 80},    // 3: 256 threads, 4 x 16 tile
-    {4, 4, 2, 2, 4, 168, 128},   // 4: 128 threads, 8 x 8 tile
+    {4, 4, 2, 4, 4, 248, 128, 1},   // 0: 256 threads, 8 x 16 tile
+    {4, 4, 1, 4, 3, 168, 128, 1},   // 1: 128 threads, 4 x 16 tile
+    {4, 2, 2, 4, 4, 128, 96, 1},    // 2: 256 threads, 8 x 8 tile
+    {2, 4, 2, 4, 4, 128, 96, 1},    // 3: 256 threads, 4 x 16 tile
+    {4, 4, 2, 2, 4, 168, 128, 1},   // 4: 128 threads, 8 x 8 tile
+    {4, 4, 1, 4, 3, 168, 168, 2},   // 5: as 1, 8 samples per lane and iteration
+    {4, 2, 1, 4, 3, 128, 96, 2},    // 6: 128 threads, 4 x 8 tile, 8 samples per lane
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
@@ -75,11 +78,23 @@ struct HpParams {
     double *mom;          // mode 0: [nsplit][p][p][2]; mode 1: [nsplit][d][p][4] by candidate slot
     double *hz;           // [nsplit][p][2] variable moment sums
     uint32_t *status;
-    const float *I32;     // mode 1: [p][p] FP32-path I(i, j), or null
-    double epsI;          // bound on |I32 - I| (entries with I32 >= epsI are skipped)
+    const float *I32;     // mode 1: [p][p] lower bound of I(i, j) from the FP32 scores,
+                          // or null; entries with I32 >= 0 contribute 0 and are skipped
     int nsplit;           // sample ranges per work item (partial sums per range)
     int sps;              // samples per range
     int64_t mom_sstride;  // elements between the ranges' moment records
+};
+
+// Per-entry bound on |I_fp32(i, j) - I(i, j)| (FP32-scored steps).  Each of
+// the four entropies of I is h(m1, m2) = -K1 (m1 - GAMMA)^2 - K2 m2^2, so a
+// moment error (dm1, dm2) moves it by at most
+//     2 K1 |m1 - GAMMA| dm1 + 2 K2 |m2| dm2 + K1 dm1^2 + K2 dm2^2.
+// Residual moments: dm1 <= d1 + da a, dm2 <= d2 + da a with
+// a = 1 / sqrt(1 - rho^2) (the FP32 residual a z_i - b z_j loses absolute
+// accuracy in proportion to a); variable moments: dv1, dv2.
+struct ErrModel {
+    double d1, d2, da;    // residual-moment error terms of the pair kernel
+    double dv1, dv2;      // variable-moment error terms (regress kernel)
 };
 
 struct ScoreParams {
@@ -89,13 +104,20 @@ struct ScoreParams {
     int nsplit_hz;
     double a1, b1, a2;    // entry moments: m1 = a1 S1/n + b1, m2 = a2 S2/n
     double ha1, hb1, ha2; // variable moments, same form
-    double epsI;          // bound on |I_fp32 - I_exact| (0 when exact)
+    double epsI;          // fixed bound on |I - I_exact| unless use_model (0 when exact)
+    int use_model;        // 1: per-entry bounds from `model` (FP32-scored steps)
+    ErrModel model;
+    const double *C;      // model: covariance by original index, and
+    int64_t ldc;          //   1 / sqrt(C_ii) by position, for rho_ij
+    const double *isd;
     const int32_t *U;
     double *M;            // out [p]
     double *E;            // out [p] error bound of M
     double *hist;         // optional [d][d] score history (row already offset)
     double *Iout;         // optional [p][p] I(i, j) by position (step-measure calls)
-    float *I32;           // optional [p][p] I(i, j) as FP32, read by the FP64 passes
+    float *I32;           // optional [p][p] lower bound of I(i, j) (rounded down), read by
+                          // the re-score passes: entries with I32 >= 0 are skipped
+    double *epsOut;       // optional [p][p] the entry bounds (step-measure calls)
 };
 
 struct SelectParams {
@@ -118,6 +140,7 @@ struct RefineSelectParams {
     double *hist;         // optional row of the score history
     int tier;             // 1: double-float passes, 2: FP64 pass
     double epsI;          // tier 1: bound on the error of each re-scored I(i, j)
+    int last;             // tier 1: the last double-float pass of the step
 };
 
 struct RegressParams {
@@ -235,11 +258,12 @@ cudaError_t launch_fill_nan(double *p, size_t count, cudaStream_t s);
 cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStream_t s);
 
 // Tensor-core covariance (kernels_gram_tc.cu): slice planes S [6][d_pad][ldk]
-// BF16 described by tmS (box 64 x 128, 128-byte swizzle), expo [d_pad],
-// part [ksplit][d][d] FP64.
+// BF16 described by tmS (box 64 x 128, 128-byte swizzle), expo
+// [periods][d_pad] per 128-sample period, part [ksplit][d][d] FP64.
 cudaError_t gram_tc_setup();
 int gram_tc_dpad(int d);
 int64_t gram_tc_ldk(int n);
+int64_t gram_tc_expo_count(int n, int d);   // [drain periods][d_pad] exponents
 int gram_tc_ksplit(int n, int d, int num_sms);
 cudaError_t launch_gram_tc(const CUtensorMap *tmS, const double *R, int64_t ldr, int n, int d,
                            __nv_bfloat16 *S, int *expo, double *part, int ksplit, double *C,
@@ -253,6 +277,9 @@ cudaError_t launch_var_window(const double *B0, const double *Bt, int d, int lag
                               const int32_t *order0, double *A, int32_t *order, cudaStream_t s);
 cudaError_t launch_influence(const double *T, int d, double *exert, double *receive,
                              int32_t *rank_exert, int32_t *rank_receive, cudaStream_t s);
+cudaError_t launch_prune(const double *C, const double *Bols, const int32_t *order, int d, int n,
+                         double gamma, int L, double eps, double tol, double *Cp, double *ws,
+                         double *B, cudaStream_t s);
 cudaError_t launch_edge_stats(const double *const *Bs, int count, int d, double threshold,
                               double *prob, double *mean, uint32_t *status, cudaStream_t s);
 

@@ -123,35 +123,44 @@ __host__ __device__ constexpr uint32_t tc_instr_desc(int M, int N)
 }
 
 // ------------------------------------------------------------- slicing ----
-// One block per padded variable row: scale exponent e (max |x| < 2^e) and the
-// six digit planes, zero beyond n and for rows beyond d.
+// One block per padded variable row, one warp per drain period of 128
+// samples: the period's scale exponent e (max |x| < 2^e over the period, so
+// a large value elsewhere in the column costs no digits here) and the six
+// digit planes of its samples, zero beyond n and for rows beyond d.
 __global__ void __launch_bounds__(256) k_gram_slices(const double *__restrict__ R, int64_t ldr,
                                                      int n, int d, int d_pad, int64_t ldk,
                                                      __nv_bfloat16 *__restrict__ S,
                                                      int *__restrict__ expo)
 {
-    __shared__ double smax[8];
     const int i = blockIdx.x;
-    double m = 0.0;
-    if (i < d)
-        for (int s = threadIdx.x; s < n; s += blockDim.x) m = fmax(m, fabs(R[(int64_t)i * ldr + s]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
-    __syncthreads();
-    m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, smax[w]);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);                      // m = f 2^e, f in [0.5, 1)
-    if (threadIdx.x == 0) expo[i] = e;
-    const double inv = ldexp(1.0, -e);
-    for (int64_t s = threadIdx.x; s < ldk; s += blockDim.x) {
-        double r = (i < d && s < n) ? R[(int64_t)i * ldr + s] * inv : 0.0;   // |r| < 1
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int periods = (int)((ldk + TC_DRAIN - 1) / TC_DRAIN);
+    for (int p = warp; p < periods; p += blockDim.x >> 5) {
+        double x[TC_DRAIN / 32];
+        double m = 0.0;
 #pragma unroll
-        for (int k = 0; k < TC_SLICES; ++k) {
-            const double sr = r * 128.0;
-            const double sg = trunc(sr);             // |sg| <= 127
-            r = sr - sg;                             // exact
-            S[((int64_t)k * d_pad + i) * ldk + s] = __float2bfloat16_rn(ldexpf((float)sg, -7 * k));
+        for (int v = 0; v < TC_DRAIN / 32; ++v) {
+            const int64_t s = (int64_t)p * TC_DRAIN + v * 32 + lane;
+            x[v] = (i < d && s < n) ? R[(int64_t)i * ldr + s] : 0.0;
+            m = fmax(m, fabs(x[v]));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        int e = 0;
+        if (m > 0.0) frexp(m, &e);                  // m = f 2^e, f in [0.5, 1)
+        if (lane == 0) expo[(int64_t)p * d_pad + i] = e;
+        const double inv = ldexp(1.0, -e);
+#pragma unroll
+        for (int v = 0; v < TC_DRAIN / 32; ++v) {
+            const int64_t s = (int64_t)p * TC_DRAIN + v * 32 + lane;
+            if (s >= ldk) continue;
+            double r = x[v] * inv;                   // |r| < 1
+#pragma unroll
+            for (int k = 0; k < TC_SLICES; ++k) {
+                const double sr = r * 128.0;
+                const double sg = trunc(sr);         // |sg| <= 127
+                r = sr - sg;                         // exact
+                S[((int64_t)k * d_pad + i) * ldk + s] = __float2bfloat16_rn(ldexpf((float)sg, -7 * k));
+            }
         }
     }
 }
@@ -161,7 +170,8 @@ struct TcGramParams {
     int d, d_pad, n;
     int64_t ldk;
     int ksplit, chunks_per_split;   // in TC_KC chunks
-    double *part;                   // [ksplit][d][d] partial sums (scaled units)
+    double *part;                   // [ksplit][d][d] partial sums (units of 2^-14)
+    const int *expo;                // [periods][d_pad] scale exponents per drain period
     uint32_t *status;
 };
 
@@ -177,6 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ uint64_t full_bar, mma_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    __shared__ int s_ecol[TC_TILE];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nt = P.d_pad / TC_TILE;
@@ -258,6 +269,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ++period_chunk;
         const bool drain = period_chunk * TC_KC >= TC_DRAIN || c == c1 - 1;
         if (drain) {
+            // the period's scales: entry (row, col) of this period's products
+            // is worth 2^(e_row + e_col) in the partial's units
+            const int64_t pe = (int64_t)(c / (TC_DRAIN / TC_KC)) * P.d_pad;
+            s_ecol[threadIdx.x] = P.expo[pe + bj * TC_TILE + threadIdx.x];
+            __syncthreads();
+            const int erow = P.expo[pe + bi * TC_TILE + warp * 32 + lane];
             double *out = P.part + (size_t)blockIdx.y * P.d * P.d;
             const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
@@ -273,8 +290,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int q = 0; q < 32; ++q) {
                         const int col = bj * TC_TILE + cb * 32 + q;
                         if (col < P.d) {
-                            const double v = (((double)a0[q] + (double)a1[q]) + (double)a2[q]) +
-                                             (double)a3[q];
+                            const double v = ldexp((((double)a0[q] + (double)a1[q]) +
+                                                    (double)a2[q]) + (double)a3[q],
+                                                   erow + s_ecol[cb * 32 + q]);
                             o[q] = first_drain ? v : o[q] + v;
                         }
                     }
@@ -291,11 +309,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
 }
 
-// C[i][j] = 2^(e_i + e_j - 14) / n * sum over splits (upper-tile entry, so C is
-// exactly symmetric).
+// C[i][j] = 2^-14 / n * sum over splits (upper-tile entry, so C is exactly
+// symmetric).
 __global__ void k_gram_tc_reduce(const double *__restrict__ part, int ksplit, int n, int d,
-                                 const int *__restrict__ expo, double *__restrict__ C,
-                                 int64_t ldc, double *ref_var)
+                                 double *__restrict__ C, int64_t ldc, double *ref_var)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
     if (j >= d) return;
@@ -306,7 +323,7 @@ __global__ void k_gram_tc_reduce(const double *__restrict__ part, int ksplit, in
     }
     double s = 0.0;
     for (int z = 0; z < ksplit; ++z) s += part[(size_t)z * d * d + (size_t)a * d + b];
-    const double v = ldexp(s, expo[a] + expo[b] - 14) / (double)n;
+    const double v = ldexp(s, -14) / (double)n;
     C[(int64_t)i * ldc + j] = v;
     if (i == j && ref_var) ref_var[i] = v;
 }
@@ -321,6 +338,10 @@ cudaError_t gram_tc_setup()
 
 int gram_tc_dpad(int d) { return (d + TC_TILE - 1) / TC_TILE * TC_TILE; }
 int64_t gram_tc_ldk(int n) { return ((int64_t)n + TC_KC - 1) / TC_KC * TC_KC; }
+int64_t gram_tc_expo_count(int n, int d)
+{
+    return (gram_tc_ldk(n) + TC_DRAIN - 1) / TC_DRAIN * gram_tc_dpad(d);
+}
 
 int gram_tc_ksplit(int n, int d, int num_sms)
 {
@@ -354,14 +375,15 @@ cudaError_t launch_gram_tc(const CUtensorMap *tmS, const double *R, int64_t ldr,
     P.ksplit = ksplit;
     P.chunks_per_split = std::max(1, per_split_periods * (TC_DRAIN / TC_KC));
     P.part = part;
+    P.expo = expo;
     P.status = status;
     const int used_splits = (nchunks + P.chunks_per_split - 1) / P.chunks_per_split;
     k_gram_tc<<<dim3(nt * (nt + 1) / 2, used_splits), TC_THREADS, gram_tc_smem_bytes(), s>>>(*tmS,
                                                                                             P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_gram_tc_reduce<<<dim3((d + 127) / 128, d), 128, 0, s>>>(part, used_splits, n, d, expo, C,
-                                                              ldc, ref_var);
+    k_gram_tc_reduce<<<dim3((d + 127) / 128, d), 128, 0, s>>>(part, used_splits, n, d, C, ldc,
+                                                              ref_var);
     return cudaGetLastError();
 }
 

@@ -52,43 +52,56 @@ __device__ __forceinline__ void accurate_terms(float u, float &t1, float &t2)
 constexpr float FAST_C2 = (float)(-2.0 * LOG2E_D / KSC);
 constexpr float FAST_C3 = (float)(LOG2E_D / KSC);
 
-// One chunk of S samples for the WI x WJ pairs of a warp: lane l takes the
-// four consecutive samples 128 it + 4 l .. + 3 (one 16-byte shared load per
-// column).  Fast form: sum_s log2(2 cosh u_s) = log2(e)/k sum |u~_s| +
+// One chunk of S samples for the WI x WJ pairs of a warp.  An iteration
+// covers G x 128 samples: lane l takes the G groups of four consecutive
+// samples g 128 + 4 l .. + 3 (one 16-byte shared load per column and group,
+// conflict-free).  Fast form: sum_s log2(2 cosh u_s) = log2(e)/k sum |u~_s| +
 // sum_s log2(1 + y_s); the second sum is taken as log2 of the product of
-// the four (1 + y_s) in (1, 16], one MUFU lg2 per four samples instead of
-// four (the logarithm of a product is the sum of the logarithms).
-template <int MODE, bool TAIL, int WI, int WJ, int S>
+// the 4 G factors (1 + y_s) in (1, 2^(4G)], one MUFU lg2 per 4 G samples (the
+// logarithm of a product is the sum of the logarithms).
+template <int MODE, bool TAIL, int WI, int WJ, int S, int G>
 __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
                                            const float *__restrict__ cols,
                                            const float (&ca)[WI][WJ], const float (&cb)[WI][WJ],
                                            float (&a1)[WI][WJ], float (&a2)[WI][WJ], int lane,
                                            int valid)
 {
+    constexpr int V = 4 * G;   // samples per lane and iteration
 #pragma unroll 1
-    for (int it = 0; it < S / 128; ++it) {
-        const int s = it * 128 + lane * 4;
-        float4 zi[WI], zj[WJ];
+    for (int it = 0; it < S / (128 * G); ++it) {
+        const int s0 = it * 128 * G + lane * 4;
+        float zi[WI][V], zj[WJ][V];
 #pragma unroll
-        for (int r = 0; r < WI; ++r) zi[r] = *reinterpret_cast<const float4 *>(rows + r * S + s);
+        for (int g = 0; g < G; ++g) {
 #pragma unroll
-        for (int c = 0; c < WJ; ++c) zj[c] = *reinterpret_cast<const float4 *>(cols + c * S + s);
-        bool ok[4] = {true, true, true, true};
-        if (TAIL) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) ok[v] = (s + v) < valid;
-        }
-#pragma unroll
-        for (int r = 0; r < WI; ++r) {
-            const float zr[4] = {zi[r].x, zi[r].y, zi[r].z, zi[r].w};
+            for (int r = 0; r < WI; ++r) {
+                const float4 t = *reinterpret_cast<const float4 *>(rows + r * S + s0 + g * 128);
+                zi[r][4 * g] = t.x;
+                zi[r][4 * g + 1] = t.y;
+                zi[r][4 * g + 2] = t.z;
+                zi[r][4 * g + 3] = t.w;
+            }
 #pragma unroll
             for (int c = 0; c < WJ; ++c) {
-                const float zc[4] = {zj[c].x, zj[c].y, zj[c].z, zj[c].w};
-                if (MODE == PAIR_FAST) {
-                    float yv[4], au[4];
+                const float4 t = *reinterpret_cast<const float4 *>(cols + c * S + s0 + g * 128);
+                zj[c][4 * g] = t.x;
+                zj[c][4 * g + 1] = t.y;
+                zj[c][4 * g + 2] = t.z;
+                zj[c][4 * g + 3] = t.w;
+            }
+        }
+        bool ok[V];
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const float u = fmaf(ca[r][c], zr[v], -(cb[r][c] * zc[v]));
+        for (int v = 0; v < V; ++v) ok[v] = !TAIL || (s0 + (v / 4) * 128 + (v % 4)) < valid;
+#pragma unroll
+        for (int r = 0; r < WI; ++r) {
+#pragma unroll
+            for (int c = 0; c < WJ; ++c) {
+                if (MODE == PAIR_FAST) {
+                    float yv[V], au[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float u = fmaf(ca[r][c], zi[r][v], -(cb[r][c] * zj[c][v]));
                         const float e = ex2_approx(-(u * u));        // exp(-u^2/2)
                         float g = u * e;
                         float a = fabsf(u);
@@ -102,18 +115,18 @@ __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
                         yv[v] = y;
                         au[v] = a;
                     }
-                    // (1 + y0)(1 + y1)(1 + y2)(1 + y3) by q <- q + y q: one
-                    // add and three FMAs instead of four adds and three products
-                    float prod = 1.0f + yv[3];
-                    prod = fmaf(yv[2], prod, prod);
-                    prod = fmaf(yv[1], prod, prod);
-                    prod = fmaf(yv[0], prod, prod);
-                    const float asum = (au[0] + au[1]) + (au[2] + au[3]);
+                    // prod (1 + y_v) by q <- q + y q: one add and V - 1 FMAs
+                    float prod = 1.0f + yv[V - 1];
+#pragma unroll
+                    for (int v = V - 2; v >= 0; --v) prod = fmaf(yv[v], prod, prod);
+                    float asum = au[0];
+#pragma unroll
+                    for (int v = 1; v < V; ++v) asum += au[v];
                     a1[r][c] += fmaf(asum, FAST_C3, lg2_approx(prod));
                 } else {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const float u = fmaf(ca[r][c], zr[v], -(cb[r][c] * zc[v]));
+                    for (int v = 0; v < V; ++v) {
+                        const float u = fmaf(ca[r][c], zi[r][v], -(cb[r][c] * zj[c][v]));
                         float t1, t2;
                         accurate_terms(u, t1, t2);
                         if (TAIL && !ok[v]) {
@@ -140,7 +153,7 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     constexpr int TI = G.ti(), TJ = G.tj(), S = PAIR_S, STAGES = G.stages;
     constexpr uint32_t STAGE_FLOATS = (TI + TJ) * S;
     constexpr uint32_t STAGE_BYTES = STAGE_FLOATS * 4;
-    constexpr bool COMP = (MODE == PAIR_FAST);
+    constexpr bool COMP = true;   // compensated (hi, lo) folds in both forms
 
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -257,9 +270,9 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
         const int valid = min(S, P.n - (c0 + k) * S);
         if (COMP) {
             if (valid == S)
-                pair_chunk<MODE, false, WI, WJ, S>(rows, cols, ca, cb, a1, a2, lane, valid);
+                pair_chunk<MODE, false, WI, WJ, S, G.groups>(rows, cols, ca, cb, a1, a2, lane, valid);
             else
-                pair_chunk<MODE, true, WI, WJ, S>(rows, cols, ca, cb, a1, a2, lane, valid);
+                pair_chunk<MODE, true, WI, WJ, S, G.groups>(rows, cols, ca, cb, a1, a2, lane, valid);
             // fold the partial sums of FOLD chunks into (hi, lo) pairs
             if ((k % FOLD) == FOLD - 1 || k == nck - 1) {
 #pragma unroll
@@ -278,9 +291,9 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
             }
         } else {
             if (valid == S)
-                pair_chunk<MODE, false, WI, WJ, S>(rows, cols, ca, cb, s1, s2, lane, valid);
+                pair_chunk<MODE, false, WI, WJ, S, G.groups>(rows, cols, ca, cb, s1, s2, lane, valid);
             else
-                pair_chunk<MODE, true, WI, WJ, S>(rows, cols, ca, cb, s1, s2, lane, valid);
+                pair_chunk<MODE, true, WI, WJ, S, G.groups>(rows, cols, ca, cb, s1, s2, lane, valid);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -377,8 +390,8 @@ struct PairTable {
     static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
-using PairKernels = PairTable<0, 1, 2, 3, 4>;
-static_assert(PAIR_NCFG == 5, "PairKernels lists every configuration");
+using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6>;
+static_assert(PAIR_NCFG == 7, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {
@@ -430,20 +443,35 @@ cudaError_t launch_pair_b(int mode, int cfg, const CUtensorMap *tmI, const CUten
 // I(i, j) = (h(z_j) + h(r_i^j)) - (h(z_i) + h(r_j^i)) with h = H - H(nu);
 // M(i) = -sum_{j != i} min(0, I(i, j))^2, summed by each lane over j in
 // ascending order and across lanes by a fixed xor tree.  E(i) bounds |M(i) -
-// M_exact(i)| given |I - I_exact| <= epsI.
-__global__ void __launch_bounds__(256) k_score_b(const ScoreParams *__restrict__ Ps)
+// M_exact(i)| given |I - I_exact| <= eps per entry: a fixed epsI for steps
+// scored in double-float, else the moment-error model of ErrModel.
+// Bound on the change of h(m1, m2) for moment errors (e1, e2), in FP32 (a
+// bound needs no more precision; the 1 % factor covers its own rounding).
+__device__ __forceinline__ float h_err(float m1, float m2, float e1, float e2)
 {
-    extern __shared__ double hsh[];   // h(z_j), j < p
+    return 1.01f * (2.0f * (float)K1 * fabsf(m1 - (float)GAMMA) * e1 +
+                    2.0f * (float)K2 * fabsf(m2) * e2 + (float)K1 * e1 * e1 +
+                    (float)K2 * e2 * e2);
+}
+
+__global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restrict__ Ps)
+{
+    extern __shared__ double hsh[];   // h(z_j), j < p; then their error bounds (float)
     const ScoreParams P = Ps[blockIdx.y];
     if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= P.p) return;
+    float *wsh = reinterpret_cast<float *>(hsh + P.p);
     const double invn = 1.0 / (double)P.n;
+    const bool model = P.use_model != 0;
+    const ErrModel em = P.model;
     for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
         double S1 = 0.0, S2 = 0.0;
         for (int s = 0; s < P.nsplit_hz; ++s) {
             S1 += P.hz[((size_t)s * P.p + j) * 2 + 0];
             S2 += P.hz[((size_t)s * P.p + j) * 2 + 1];
         }
-        hsh[j] = neg_entropy_part(P.ha1 * S1 * invn + P.hb1, P.ha2 * S2 * invn);
+        const double m1 = P.ha1 * S1 * invn + P.hb1, m2 = P.ha2 * S2 * invn;
+        hsh[j] = neg_entropy_part(m1, m2);
+        if (model) wsh[j] = h_err((float)m1, (float)m2, (float)em.dv1, (float)em.dv2);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -452,7 +480,7 @@ __global__ void __launch_bounds__(256) k_score_b(const ScoreParams *__restrict__
     const size_t plane = (size_t)P.p * P.p * 2;
     const double hi = hsh[i];
     double acc = 0.0, err = 0.0;
-    const double eps = P.epsI;
+    const int oi = P.U[i];
     for (int j = lane; j < P.p; j += 32) {
         if (j == i) continue;
         double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
@@ -464,14 +492,27 @@ __global__ void __launch_bounds__(256) k_score_b(const ScoreParams *__restrict__
             b1 += pji[s * plane];
             b2 += pji[s * plane + 1];
         }
-        const double hij = neg_entropy_part(P.a1 * a1 * invn + P.b1, P.a2 * a2 * invn);
-        const double hji = neg_entropy_part(P.a1 * b1 * invn + P.b1, P.a2 * b2 * invn);
+        const double mi1 = P.a1 * a1 * invn + P.b1, mi2 = P.a2 * a2 * invn;
+        const double mj1 = P.a1 * b1 * invn + P.b1, mj2 = P.a2 * b2 * invn;
+        const double hij = neg_entropy_part(mi1, mi2);
+        const double hji = neg_entropy_part(mj1, mj2);
         const double I = (hsh[j] + hij) - (hi + hji);
+        double eps = P.epsI;
+        if (model) {
+            const int oj = P.U[j];
+            const double rho = P.C[(int64_t)min(oi, oj) * P.ldc + max(oi, oj)] * P.isd[i] * P.isd[j];
+            const float ra = rsqrtf(fmaxf((float)fma(-rho, rho, 1.0), 1e-12f)) * 1.01f;
+            const float e1 = (float)em.d1 + (float)em.da * ra;
+            const float e2 = (float)em.d2 + (float)em.da * ra;
+            eps = (double)(h_err((float)mi1, (float)mi2, e1, e2) +
+                           h_err((float)mj1, (float)mj2, e1, e2) + wsh[i] + wsh[j]);
+        }
         const double v = fmin(0.0, I);
         acc += v * v;
         if (I < eps) err += 2.0 * fabs(v) * eps + eps * eps;
         if (P.Iout) P.Iout[(size_t)i * P.p + j] = I;
-        if (P.I32) P.I32[(size_t)i * P.p + j] = (float)I;
+        if (P.epsOut) P.epsOut[(size_t)i * P.p + j] = eps;
+        if (P.I32) P.I32[(size_t)i * P.p + j] = __double2float_rd(I - eps);
     }
     acc = warp_sum_xor(acc);
     err = warp_sum_xor(err);
@@ -487,7 +528,7 @@ cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream
     if (count <= 0) return cudaSuccess;
     const int rows_per_block = 8;
     dim3 grid((maxp + rows_per_block - 1) / rows_per_block, count);
-    k_score_b<<<grid, 256, sizeof(double) * maxp, s>>>(P);
+    k_score_b<<<grid, 256, (sizeof(double) + sizeof(float)) * maxp + 16, s>>>(P);
     return cudaGetLastError();
 }
 

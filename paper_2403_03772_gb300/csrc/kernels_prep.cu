@@ -303,7 +303,8 @@ cudaError_t launch_iota_b(const IotaParams *P, int count, int maxd, cudaStream_t
 // the same pass: the new column is standardised with its downdated variance
 // C_ii - C_im^2 / C_mm, written as FP32 to its compacted position for the
 // next pair-moment kernel, and its own entropy moments are accumulated
-// (accurate FP32 functions, FP64 block sums).  INIT=true only standardises
+// (accurate FP32 functions, compensated FP32 sums per thread, FP64 block
+// sums).  INIT=true only standardises
 // (first step, no regression).
 template <bool INIT>
 __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restrict__ Ps)
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
     float *zo = P.z + (int64_t)col * P.ldz;
     float *zl = P.zlo ? P.zlo + (int64_t)col * P.ldz : nullptr;
     const int s0 = blockIdx.y * P.sps, s1 = min(P.n, s0 + P.sps);
-    float a1 = 0.0f, a2 = 0.0f;
+    CompSum a1, a2;
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         double r = ri[s];
         if (!INIT) {
@@ -351,11 +352,11 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
         zo[s] = z;
         if (zl) zl[s] = (float)(zx - (double)z);
         const float az = fabsf(z);
-        a1 += az + log1pf(expf(-2.0f * az));
-        a2 += z * expf(-0.5f * z * z);
+        a1.add(az + log1pf(expf(-2.0f * az)));
+        a2.add(z * expf(-0.5f * z * z));
     }
-    const double t1 = block_sum((double)a1, sh);
-    const double t2 = block_sum((double)a2, sh);
+    const double t1 = block_sum(a1.value(), sh);
+    const double t2 = block_sum(a2.value(), sh);
     if (threadIdx.x == 0) {
         const int np = INIT ? P.p : P.p - 1;
         double *o = P.hzpart + ((size_t)blockIdx.y * np + col) * 2;

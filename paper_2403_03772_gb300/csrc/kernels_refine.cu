@@ -309,9 +309,9 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             cidx = cbeg + (int)(q / P.p);
             a = P.state->cand[cidx];
             b = (int)(q % P.p);
-            // I32(a, b) >= epsI proves I(a, b) >= 0: min(0, I)^2 = 0 exactly,
-            // so the entry needs no moments (marked by a negative sum)
-            if (a == b || (P.I32 && P.I32[(size_t)a * P.p + b] >= P.epsI)) {
+            // a lower bound I32(a, b) >= 0 proves I(a, b) >= 0: min(0, I)^2 = 0
+            // exactly, so the entry needs no moments (marked by a negative sum)
+            if (a == b || (P.I32 && P.I32[(size_t)a * P.p + b] >= 0.0f)) {
                 if (threadIdx.x == 0 && sp == 0) {   // the marker lives in range 0
                     double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
                     o[0] = -1.0;
@@ -457,10 +457,11 @@ cudaError_t df_tables_setup()
 // advances the step's decision:
 //   tier 1 (df): each M carries the bound e = sum_j (2 |min(0, I)| epsI2 +
 //     epsI2^2) over its computed entries.  Pass 1 covers the two candidates
-//     with the highest FP32 upper bounds; if the best lower bound M - e does
-//     not beat the next upper bound, pass 2 covers the rest.  Candidates
-//     whose intervals overlap the best one's go to tier 2; if none do, the
-//     step is decided.
+//     with the highest FP32 upper bounds; pass 2 the others whose upper
+//     bound still reaches the best lower bound M - e.  Candidates whose
+//     intervals overlap the best one's go to tier 2; if none do, the step is
+//     decided.  The last pass always decides or escalates, so every step
+//     ends decided.
 //   tier 2 (FP64): the argmax of the FP64 scores (ties to the smallest
 //     original index), and a tie count when the top two are within
 //     1e-9 max|M|.
@@ -521,14 +522,19 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
         for (int c = cb; c < ce; ++c) P.hist[P.U[st->cand[c]]] = st->mhp[c];
     const double lb = st->mhp[best] - st->ehp[best];
     if (P.tier == 1) {
-        if (ce < nc && !(lb > st->ub[ce])) {
-            st->pass_begin = ce;       // undecided: score the rest in pass 2
-            st->pass_end = nc;
+        // candidates never re-scored whose FP32 upper bound still reaches lb
+        // (a prefix of the rest: they are sorted by upper bound)
+        int cend = ce;
+        while (cend < nc && !(lb > st->ub[cend])) ++cend;
+        if (cend > ce && !P.last) {
+            st->pass_begin = ce;       // undecided: pass 2 re-scores those
+            st->pass_end = cend;
             return;
         }
-        // candidates still not separated from the best one go to FP64; the
-        // ones never re-scored have upper bounds below lb
-        int nk = 0;
+        // candidates still not separated from the best one go to FP64: the
+        // re-scored ones whose interval reaches lb and, after the last
+        // double-float pass, any left whose upper bound reaches it
+        int nk = cend - ce;
         for (int c = 0; c < ce; ++c)
             nk += (c == best || !(st->mhp[c] + st->ehp[c] < lb));
         if (nk == 1) {
@@ -537,8 +543,9 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
             return;
         }
         nk = 0;   // compact in place (the write index never passes the read index)
-        for (int c = 0; c < ce; ++c)
-            if (c == best || !(st->mhp[c] + st->ehp[c] < lb)) st->cand[nk++] = st->cand[c];
+        for (int c = 0; c < cend; ++c)
+            if (c >= ce || c == best || !(st->mhp[c] + st->ehp[c] < lb))
+                st->cand[nk++] = st->cand[c];
         st->ncand = nk;
         st->pass_begin = 0;
         st->pass_end = nk;

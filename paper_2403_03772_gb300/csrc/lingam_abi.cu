@@ -85,6 +85,12 @@ constexpr int P_HP = 32;
 // factor of about 130 above that.
 constexpr double DF_EPS_I = 1.0e-12;
 
+// With the tensor-core covariance (single-instance MIXED runs; about 2e-10
+// relative error on heavy-tailed data) the standardised columns and rho
+// themselves carry that error, which moves I by up to 7.4e-11 on the test
+// workloads: the double-float bound there is 1e-9.
+constexpr double DF_EPS_I_TC = 1.0e-9;
+
 struct InstSpec {
     int64_t n, d;
     bool operator==(const InstSpec &o) const { return n == o.n && d == o.d; }
@@ -400,7 +406,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         pl.inst[k].tc_ksplit = tc ? gram_tc_ksplit((int)n, (int)d, ctx->num_sms) : 0;
         o[k].Cpart = take((size_t)std::max(pl.inst[k].ksplit, pl.inst[k].tc_ksplit) * d * d * 8);
         o[k].S = tc ? take((size_t)6 * gram_tc_dpad((int)d) * gram_tc_ldk((int)n) * 2) : 0;
-        o[k].expo = tc ? take((size_t)gram_tc_dpad((int)d) * 4) : 0;
+        o[k].expo = tc ? take((size_t)gram_tc_expo_count((int)n, (int)d) * 4) : 0;
         o[k].mom = take(pl.inst[k].mom_elems * 8);
         o[k].hz = take(pl.inst[k].hz_elems * 8);
         o[k].M = take((size_t)d * 8);
@@ -513,8 +519,9 @@ struct Launch {
 
 // Capture the covariance + ordering loop of the current plan into one graph.
 // stop_after_score0 captures only the first step up to its scores (and writes
-// I(i, j) of the single instance to Iout).
-static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, double *Iout)
+// I(i, j) of the single instance to Iout and the per-entry bounds to epsOut).
+static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, double *Iout,
+                                  double *epsOut)
 {
     Plan &pl = ctx->plan;
     const int K = (int)pl.inst.size();
@@ -522,13 +529,22 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     const bool profile = ctx->opts.profile != 0 && !stop_after_score0;
     cudaStream_t s = ctx->s;
     const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
-    // Bound on |I_fp32 - I_exact| per entry, used to pick the candidates that
-    // are re-scored.  Measured against FP64 on GB300 over all 1e6 first-step
-    // entries of the d=1000, n=10000 workload: max 1.25e-6 (accurate FP32,
-    // plain sums) and 3.5e-7 (fast form: the MUFU ex2/lg2 relative error is
-    // systematic, so it does not average out over the samples); the bounds
-    // keep a factor of 4 above those.
-    const double epsI = prec == LINGAM_PREC_MIXED ? 1.5e-6 * tie : 5.0e-6 * tie;
+    // Moment-error model of the FP32 pair kernels and the regress kernel
+    // (ErrModel): per-sample worst cases of the MUFU ex2/lg2 approximations
+    // (relative 2^-22.5 / absolute 2^-22.6), the FP32 product of four 1 + y
+    // and the accurate expf/log1pf (a few ulp), with compensated sums; the
+    // residual a z_i - b z_j carries about 3 * 2^-24 a (|z_i| + |z_j|).
+    // Those worst cases assume every per-sample error has the same sign; on
+    // the calibration workloads (heavy and light tails, skewed noise, VAR
+    // innovations, n = 1e6, a near-collinear chain) the largest error was
+    // 0.18 of the resulting bound, so the terms are scaled by 0.6: the bound
+    // stays 3x above every error seen, and a GPU test keeps it above 2x.
+    const double s6 = 0.6 * tie;
+    ErrModel em{};
+    if (prec == LINGAM_PREC_MIXED)
+        em = ErrModel{2.0e-7 * s6, 1.2e-7 * s6, 3.0e-7 * s6, 1.5e-7 * s6, 1.0e-7 * s6};
+    else
+        em = ErrModel{1.5e-7 * s6, 1.0e-7 * s6, 3.0e-7 * s6, 1.5e-7 * s6, 1.0e-7 * s6};
     const int pmode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
     const double a1 = pmode == PAIR_FAST ? LN2_D : 1.0;
     const double a2 = pmode == PAIR_FAST ? 1.0 / KSC : 1.0;
@@ -646,12 +662,12 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             double *isd = (t & 1) ? I.isd1 : I.isd0;
             double *hist_row = I.hist ? I.hist + (size_t)t * I.d : nullptr;
             const bool hp = step_hp(prec, p);
+            const double eps2 = (I.tc_ksplit > 0 ? DF_EPS_I_TC : DF_EPS_I) * tie;
             const int hp_tier = step_hp_tier(prec);
             auto hpp = [&](int mode, int with_vars, double *mom) {
                 HpParams F{};
                 // entries whose FP32 I clears the FP32 bound need no re-score
                 F.I32 = (mode == 1 && !hp) ? I.I32 : nullptr;
-                F.epsI = epsI;
                 F.R = I.R;
                 F.ldr = I.ldr;
                 F.zhi = zbase + (int64_t)I.zrow * pl.ldz;
@@ -684,7 +700,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 S.a1 = 1.0;
                 S.b1 = -LN2_D;
                 S.a2 = 1.0;
-                S.epsI = hp_tier == 1 ? DF_EPS_I * tie : 0.0;
+                S.epsI = hp_tier == 1 ? eps2 : 0.0;
             } else {
                 PairParams P{};
                 P.C = I.C;
@@ -710,7 +726,12 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 S.a1 = a1;
                 S.b1 = -LN2_D;
                 S.a2 = a2;
-                S.epsI = epsI;
+                S.epsI = 0.0;
+                S.use_model = 1;
+                S.model = em;
+                S.C = I.C;
+                S.ldc = I.d;
+                S.isd = isd;
             }
             S.p = p;
             S.n = n;
@@ -722,6 +743,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             S.E = I.E;
             S.hist = hist_row;
             S.Iout = stop_after_score0 ? Iout : nullptr;
+            S.epsOut = stop_after_score0 ? epsOut : nullptr;
             S.I32 = hp ? nullptr : I.I32;
             sc.push_back(S);
             // candidates of an FP32-scored step go to double-float first; a
@@ -730,15 +752,15 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             fd1.push_back(hpp(1, 1, I.fmom));
             fd2.push_back(hpp(1, 0, I.fmom));
             f64.push_back(hpp(1, 1, I.fmom));
-            const double e2 = DF_EPS_I * tie;
+            const double e2 = eps2;
             const int ns1 = ss.hp1_nsplit[k];
             const int64_t fst = (int64_t)I.d * p * 4;
             rd1.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, ns1, fst, Uc, I.state, hist_row,
-                                             1, e2});
+                                             1, e2, 0});
             rd2.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, ns1, fst, Uc, I.state, hist_row,
-                                             1, e2});
+                                             1, e2, 1});
             r64.push_back(RefineSelectParams{I.fmom, I.fhz, p, n, ns1, fst, Uc, I.state, hist_row,
-                                             2, 0.0});
+                                             2, 0.0, 1});
             rg.push_back(regress_params(I, t, p, Uc, Un, ss.reg_sps[k], false));
             nsplit_hz[k] = ss.reg_nsplit[k];
             maxcols = std::max(maxcols, p - 1);
@@ -915,7 +937,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
 // Make ctx->plan match the batch shape (reusing arenas and graph when equal).
 static lingam_status ensure_plan(lingam_ctx *ctx, const std::vector<InstSpec> &spec, bool scores,
                                  bool lcoef, bool rows, bool stop_after_score0 = false,
-                                 double *Iout = nullptr)
+                                 double *Iout = nullptr, double *epsOut = nullptr)
 {
     Plan &pl = ctx->plan;
     const int prec = ctx->opts.precision;
@@ -932,7 +954,7 @@ static lingam_status ensure_plan(lingam_ctx *ctx, const std::vector<InstSpec> &s
         lingam_status st = layout_plan(ctx, pl, spec, prec, scores, lcoef, rows);
         if (st) return st;
     }
-    lingam_status st = capture_plan(ctx, stop_after_score0, Iout);
+    lingam_status st = capture_plan(ctx, stop_after_score0, Iout, epsOut);
     if (st) return st;
     CK(cudaEventRecord(ctx->g1, ctx->s));
     CK(cudaEventSynchronize(ctx->g1));
@@ -957,6 +979,17 @@ static lingam_status check_args(lingam_ctx *ctx, const void *X, int64_t n, int64
     if (d > 6000) return fail(ctx, LINGAM_ERR_ARG, "d > 6000 is not supported");
     if (n > ((int64_t)1 << 30)) return fail(ctx, LINGAM_ERR_ARG, "n > 2^30 is not supported");
     if (d > n) return fail(ctx, LINGAM_ERR_DEGENERATE, "d > n: the covariance is singular");
+    return LINGAM_OK;
+}
+
+static lingam_status check_perm(lingam_ctx *ctx, const int32_t *order, int64_t d)
+{
+    std::vector<char> seen((size_t)d, 0);
+    for (int64_t k = 0; k < d; ++k) {
+        if (order[k] < 0 || order[k] >= d || seen[order[k]])
+            return fail(ctx, LINGAM_ERR_ARG, "order is not a permutation of 0..d-1");
+        seen[order[k]] = 1;
+    }
     return LINGAM_OK;
 }
 
@@ -1196,7 +1229,7 @@ lingam_status lingam_causal_order(lingam_ctx *ctx, const void *X, int64_t n, int
 
 lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
                                    int64_t ld, int32_t layout, double *I_out, double *M_out,
-                                   lingam_stream_t stream)
+                                   double *eps_out, lingam_stream_t stream)
 {
     if (!ctx) return LINGAM_ERR_ARG;
     ctx->err.clear();
@@ -1206,38 +1239,32 @@ lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, in
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     if ((st = begin_call(ctx, user))) return st;
     CK(ensure(ctx->aW, (size_t)d * d * 8));
+    CK(ensure(ctx->aL, (size_t)d * d * 8));
     CK(cudaMemsetAsync(ctx->aW.p, 0, (size_t)d * d * 8, ctx->s));
+    CK(cudaMemsetAsync(ctx->aL.p, 0, (size_t)d * d * 8, ctx->s));
     std::vector<InstSpec> spec{{n, d}};
-    if ((st = ensure_plan(ctx, spec, false, false, false, true, ptr<double>(ctx->aW)))) return st;
+    if ((st = ensure_plan(ctx, spec, false, false, false, true, ptr<double>(ctx->aW),
+                          ptr<double>(ctx->aL))))
+        return st;
     if ((st = load_single(ctx, X, n, d, ld, layout))) return st;
     std::vector<DevState> hs;
     if ((st = run_plan(ctx, nullptr, nullptr, hs))) return st;
     if (I_out) CK(cudaMemcpyAsync(I_out, ctx->aW.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
     if (M_out)
         CK(cudaMemcpyAsync(M_out, ctx->plan.inst[0].M, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->s));
+    if (eps_out)
+        CK(cudaMemcpyAsync(eps_out, ctx->aL.p, (size_t)d * d * 8, cudaMemcpyDeviceToHost, ctx->s));
     if ((st = end_call(ctx, user))) return st;
     return status_to_code(ctx, hs[0].status);
 }
 
-lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
-                                   int32_t layout, const int32_t *order, double *B_out,
-                                   int32_t B_on_device, lingam_stream_t stream)
+// Least-squares adjacency on `order` into ctx->aW (device, d x d).  With
+// keep_cov the covariance before elimination is left in ctx->eIn.
+static lingam_status adjacency_core(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
+                                    int64_t ld, int32_t layout, const int32_t *order,
+                                    bool keep_cov, uint32_t **status_out)
 {
-    if (!ctx) return LINGAM_ERR_ARG;
-    ctx->err.clear();
-    if (!order || !B_out) return fail(ctx, LINGAM_ERR_ARG, "order or B_out is NULL");
-    lingam_status st = check_args(ctx, X, n, d, ld, layout);
-    if (st) return st;
-    {
-        std::vector<char> seen((size_t)d, 0);
-        for (int64_t k = 0; k < d; ++k) {
-            if (order[k] < 0 || order[k] >= d || seen[order[k]])
-                return fail(ctx, LINGAM_ERR_ARG, "order is not a permutation of 0..d-1");
-            seen[order[k]] = 1;
-        }
-    }
-    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    if ((st = begin_call(ctx, user))) return st;
+    lingam_status st;
     const int di = (int)d, ni = (int)n;
     const int64_t ldr = roundup(n, 32);
     const int ks = gram_ksplit(ni, di, ctx->num_sms);
@@ -1261,12 +1288,66 @@ lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, in
     CK(launch_center(ptr<double>(ctx->aR), ldr, ni, di, ctx->s));
     CK(launch_gram_f64(ptr<double>(ctx->aR), ldr, ni, di, ptr<double>(ctx->aCpart), ks,
                        ptr<double>(ctx->aC), d, ptr<double>(ctx->aRef), ctx->s));
+    if (keep_cov) {
+        CK(ensure(ctx->eIn, (size_t)d * d * 8));
+        CK(cudaMemcpyAsync(ctx->eIn.p, ctx->aC.p, (size_t)d * d * 8, cudaMemcpyDeviceToDevice,
+                           ctx->s));
+    }
     for (int t = 0; t + 1 < di; ++t)
         CK(launch_ldl_step(ptr<double>(ctx->aC), d, ptr<int32_t>(ctx->aPiv), t, di,
                            ptr<double>(ctx->aL), d, ctx->s));
     CK(launch_unit_lower_inverse(ptr<double>(ctx->aL), d, ptr<int32_t>(ctx->aPiv), di,
                                  ptr<double>(ctx->aW), d, ctx->s));
+    *status_out = status;
+    return LINGAM_OK;
+}
+
+lingam_status lingam_fit_adjacency(lingam_ctx *ctx, const void *X, int64_t n, int64_t d, int64_t ld,
+                                   int32_t layout, const int32_t *order, double *B_out,
+                                   int32_t B_on_device, lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!order || !B_out) return fail(ctx, LINGAM_ERR_ARG, "order or B_out is NULL");
+    lingam_status st = check_args(ctx, X, n, d, ld, layout);
+    if (st) return st;
+    if ((st = check_perm(ctx, order, d))) return st;
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = begin_call(ctx, user))) return st;
+    uint32_t *status = nullptr;
+    if ((st = adjacency_core(ctx, X, n, d, ld, layout, order, false, &status))) return st;
     CK(cudaMemcpyAsync(B_out, ctx->aW.p, (size_t)d * d * 8,
+                       B_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
+    uint32_t hst = 0;
+    CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = end_call(ctx, user))) return st;
+    return status_to_code(ctx, hst);
+}
+
+lingam_status lingam_prune_adjacency(lingam_ctx *ctx, const void *X, int64_t n, int64_t d,
+                                     int64_t ld, int32_t layout, const int32_t *order,
+                                     double gamma, int32_t n_lambda, double eps, double *B_out,
+                                     int32_t B_on_device, lingam_stream_t stream)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!order || !B_out) return fail(ctx, LINGAM_ERR_ARG, "order or B_out is NULL");
+    if (!(gamma > 0.0) || n_lambda < 2 || n_lambda > 1000 || !(eps > 0.0 && eps < 1.0))
+        return fail(ctx, LINGAM_ERR_ARG, "need gamma > 0, 2 <= n_lambda <= 1000, 0 < eps < 1");
+    lingam_status st = check_args(ctx, X, n, d, ld, layout);
+    if (st) return st;
+    if ((st = check_perm(ctx, order, d))) return st;
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = begin_call(ctx, user))) return st;
+    uint32_t *status = nullptr;
+    if ((st = adjacency_core(ctx, X, n, d, ld, layout, order, true, &status))) return st;
+    CK(ensure(ctx->eL, (size_t)d * d * 8));
+    CK(ensure(ctx->eW, (size_t)4 * d * d * 8));
+    CK(ensure(ctx->eT, (size_t)d * d * 8));
+    CK(launch_prune(ptr<double>(ctx->eIn), ptr<double>(ctx->aW), ptr<int32_t>(ctx->aPiv), (int)d,
+                    (int)n, gamma, n_lambda, eps, 1e-10, ptr<double>(ctx->eL), ptr<double>(ctx->eW),
+                    ptr<double>(ctx->eT), ctx->s));
+    CK(cudaMemcpyAsync(B_out, ctx->eT.p, (size_t)d * d * 8,
                        B_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
     uint32_t hst = 0;
     CK(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, ctx->s));
@@ -1479,17 +1560,6 @@ static lingam_status device_view(lingam_ctx *ctx, const void *src, size_t bytes,
     CK(ensure(stage, bytes));
     CK(cudaMemcpyAsync(stage.p, src, bytes, cudaMemcpyHostToDevice, ctx->s));
     *out = stage.p;
-    return LINGAM_OK;
-}
-
-static lingam_status check_perm(lingam_ctx *ctx, const int32_t *order, int64_t d)
-{
-    std::vector<char> seen((size_t)d, 0);
-    for (int64_t k = 0; k < d; ++k) {
-        if (order[k] < 0 || order[k] >= d || seen[order[k]])
-            return fail(ctx, LINGAM_ERR_ARG, "order is not a permutation of 0..d-1");
-        seen[order[k]] = 1;
-    }
     return LINGAM_OK;
 }
 

@@ -1,30 +1,85 @@
-"""GPU: the per-entry error bounds that drive the re-score tiers hold with
-margin.  I(i, j) of every first-step pair from each form is compared with the
-FP64 form on the same device input; the bounds are the ones the library uses
-(FP32 plain 5e-6, fast 1.5e-6, double-float 1e-12), and each must stay at
-least 2x (double-float: 10x) above the largest error seen.  The FP64 form
-itself is pinned to the oracle in test_gpu_order.py."""
+"""GPU: the error bounds that drive the re-score tiers hold with margin.
+
+I(i, j) of every first-step pair from each form is compared with the FP64 form
+on the same device input.  FP32 and MIXED: every entry's error must stay
+within half of the bound the library itself computes for that entry from its
+moment-error model (the bound adapts to the entry's moments and to the
+conditioning 1/sqrt(1 - rho^2) of the pair).  Double-float: within a tenth of
+its fixed 1e-12.  The FP64 form itself is pinned to the oracle in
+test_gpu_order.py.  The workloads cover light and heavy tails, skewed noise,
+VAR innovations, n = 1e6, and a near-collinear chain."""
 import numpy as np
 import pytest
 
+import gen
+import oracle
+
 pytestmark = pytest.mark.gpu
 
-BOUND = {"fp32": 5.0e-6, "mixed": 1.5e-6, "df": 1.0e-12}
-MARGIN = {"fp32": 2.0, "mixed": 2.0, "df": 10.0}
+
+def _collinear(seed=31, n=20000, d=40):
+    # x_k = 0.995 x_{k-1} + small Laplace noise: |rho| close to 1 for neighbours
+    st = gen.Stream(seed)
+    E = st.laplace(1.0, n * d).reshape(n, d)
+    X = np.empty((n, d))
+    X[:, 0] = E[:, 0]
+    for k in range(1, d):
+        X[:, k] = 0.995 * X[:, k - 1] + 0.1 * E[:, k]
+    return X[:, st.permutation(d)].astype(np.float32)
 
 
-@pytest.mark.parametrize("name", ["cfg3", "cfg2", "long_n"])
+def _data(name, datasets):
+    if name == "collinear":
+        return _collinear()
+    if name == "cfg4_innovations":
+        _, E = oracle.var_fit(datasets("cfg4").Xt, 1)
+        return E.astype(np.float32)
+    if name == "cfg3_head":
+        return np.ascontiguousarray(datasets("cfg3").X[:, :400])
+    return datasets(name).X
+
+
+@pytest.mark.parametrize("name", ["cfg3_head", "cfg2", "cfg1", "long_n", "cfg4_innovations",
+                                  "collinear"])
 def test_error_bounds_hold_with_margin(datasets, name):
     import torch
     import paper_2403_03772_gb300 as pkg
-    ds = datasets(name)
-    X32 = torch.from_numpy(ds.X).to("cuda:0")
+    X = _data(name, datasets)
+    X32 = torch.from_numpy(np.ascontiguousarray(X)).to("cuda:0")
     with pkg.Context(0, "fp64") as c:
         I64, _ = c.step_measures(X32.double())
-    worst = {}
-    for prec in ["fp32", "mixed", "df"]:
+    off = ~np.eye(X.shape[1], dtype=bool)
+    for prec in ["fp32", "mixed"]:
         with pkg.Context(0, prec) as c:
-            I, _ = c.step_measures(X32)
-        worst[prec] = float(np.max(np.abs(I - I64)))
-    for prec, err in worst.items():
-        assert err * MARGIN[prec] <= BOUND[prec], (prec, err, worst)
+            I, _, eps = c.step_measures(X32, bounds=True)
+        err = np.abs(I - I64)[off]
+        util = np.max(err / eps[off])
+        # FP32-scored steps: the model bound (5x above the errors seen); steps
+        # with d <= 32 are scored in double-float with a fixed bound
+        assert util <= (0.5 if X.shape[1] > 32 else 0.1), (name, prec, util, float(np.max(err)))
+    with pkg.Context(0, "df") as c:
+        I, _, eps = c.step_measures(X32, bounds=True)
+    assert np.all(eps[off] == 1e-12)
+    assert np.max(np.abs(I - I64)[off]) <= 1e-13, name
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2_head", "collinear_head"])
+def test_tensor_core_covariance_is_fp64_class(datasets, name):
+    """With d <= 32 every pair is scored in double-float, so the MIXED form
+    (tensor-core covariance, single instance) and the FP32 form (FP64 SIMT
+    covariance) differ only through the covariance; their I must agree to
+    the double-float bound of the MIXED form."""
+    import torch
+    import paper_2403_03772_gb300 as pkg
+    if name == "cfg2_head":
+        X = np.ascontiguousarray(datasets("cfg2").X[:, :30])
+    elif name == "collinear_head":
+        X = np.ascontiguousarray(_collinear()[:, :30])
+    else:
+        X = datasets(name).X
+    X32 = torch.from_numpy(X).to("cuda:0")
+    with pkg.Context(0, "mixed") as c:
+        Im, _ = c.step_measures(X32)
+    with pkg.Context(0, "fp32") as c:
+        If, _ = c.step_measures(X32)
+    assert np.max(np.abs(Im - If)) <= 1e-10, name

@@ -95,3 +95,46 @@ def test_bootstrap_edge_stats(ctx):
         oprob, omean = oracle.bootstrap_edge_stats(np.stack(Bs), thr)
         assert np.array_equal(prob, oprob)
         assert np.max(np.abs(mean - omean)) <= 1e-15
+
+
+def _assert_rows_on_oracle_path(X, order, B):
+    """Every row of the GPU's pruned B is a point of the oracle's adaptive
+    lasso path whose BIC is the minimum up to 1e-3 (two path points whose
+    BIC differ by less than that are a tie of the model selection, and a
+    1e-10 change in the adaptive weights can swap them)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    Xc = X - X.mean(axis=0)
+    C = Xc.T @ Xc / n
+    for pos, k in enumerate(order):
+        pred = order[:pos]
+        if pos == 0:
+            assert np.all(B[k] == 0)
+            continue
+        path = oracle.adaptive_lasso_path(C, k, pred, n)
+        row = B[k, pred]
+        if not path:
+            assert np.all(row == 0)
+            continue
+        best = min(b for _, _, b in path)
+        near = [b for _, b, bic in path if bic <= best + 1e-3]
+        assert any(np.array_equal(row != 0, b != 0) and np.max(np.abs(row - b)) < 1e-6
+                   for b in near), (int(k), row, near)
+        others = np.delete(np.arange(B.shape[0]), pred)
+        assert np.all(B[k, others] == 0)
+
+
+@pytest.mark.parametrize("seed,n,d", [(71, 40000, 10), (1002, 5000, 40)])
+def test_pruned_adjacency_matches_oracle(ctx, seed, n, d):
+    ds = gen.cfg1(seed=seed, n=n, d=d) if d <= 10 else gen.cfg2(seed=seed, n=n, d=d)
+    B = ctx.prune_adjacency(ds.X, ds.order)
+    _assert_rows_on_oracle_path(ds.X, ds.order, B)
+
+
+def test_pruned_adjacency_of_the_estimated_order(ctx, datasets):
+    ds = datasets("cfg1")
+    order = ctx.causal_order(ds.X)
+    B = ctx.prune_adjacency(ds.X, order)
+    _assert_rows_on_oracle_path(ds.X, order, B)
+    # a pruned row never has more edges than its least-squares row
+    assert np.count_nonzero(B) <= np.count_nonzero(ctx.fit_adjacency(ds.X, order))
