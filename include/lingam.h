@@ -53,8 +53,9 @@ typedef enum {
  *   FP32  -- entropy moments in FP32 with the accurate CUDA expf/log1pf, FP64
  *            covariance (Gram), FP64 residual data, rank-1 downdate and OLS.
  *   MIXED -- covariance on the tensor cores (single-instance calls; exact
- *            7-bit BF16 digit planes, FP64 recombination, about 1e-10
- *            relative error), entropy moments with the hardware ex2/lg2
+ *            7-bit BF16 digit planes scaled per 64 samples, FP64
+ *            recombination, about 4e-11 relative error), entropy moments
+ *            with the hardware ex2/lg2
  *            approximations and compensated summation; FP64 downdate and OLS.
  *   FP64  -- every moment in FP64 (small problems; GB300 FP64 is slow).
  *   DF    -- every moment in double-float (pairs of FP32 numbers, about
@@ -189,7 +190,7 @@ lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, in
  *     min_b 1/2 b'C_PP b - b'C_Pk + lam sum_j w_j |b_j|,  w_j = |b_ols_j|^-gamma,
  * on the centred FP64 covariance C = Xc'Xc/n, by cyclic coordinate descent
  * over P in order, warm-started along lam_i = lam_max eps^(i/(n_lambda-1)),
- * i = 0..n_lambda-1 (lam_max = max_j |C_jk| / w_j), each lam's sweeps ending
+ * i = 0..n_lambda-1 (lam_max = (1 + 1e-9) max_j |C_jk| / w_j), each lam's sweeps ending
  * once the largest change |db_j| sqrt(C_jj) <= 1e-10 sqrt(C_kk); the lam with
  * the smallest BIC = n log(RSS/n) + df log n (first minimum) gives row k.
  *   X, n, d, ld, layout, order: as lingam_fit_adjacency.
@@ -255,7 +256,7 @@ lingam_status lingam_bootstrap_edge_stats(lingam_ctx *ctx, const double *const *
  * Tile shapes and split schedules of the FP32 pair-moment kernel, by range of
  * the number p of remaining variables.  Bucket b covers
  * p_max[b-1] < p <= p_max[b] (p_max ascending; the last bucket also covers
- * every larger p).  tile[b] indexes the kernel's tile configurations (0..6:
+ * every larger p).  tile[b] indexes the kernel's tile configurations (0..8:
  * warps x pairs per warp, see the library's design notes); ctas_per_sm[b] is
  * the number of CTAs per SM the sample splits aim for; ms[b] the kernel time
  * measured at the probe size p_probe[b] with n_probe samples.  One table per
@@ -303,8 +304,10 @@ typedef struct {
     int32_t graph_nodes;      /* kernel nodes in the step graph */
     double graph_build_ms;    /* capture + instantiate time (0 if cached) */
     int32_t fp64_candidates;  /* candidates re-scored in FP64 over the run */
-    int32_t df_candidates;    /* candidates re-scored in double-float */
-    int32_t reserved[4];
+    int32_t df_candidates;    /* candidates re-scored in double-float (whole rows) */
+    int32_t partial_candidates; /* candidates through the partial re-score */
+    int32_t partial_decided;  /* steps the partial re-score decided */
+    int32_t reserved[2];
     double score_ms;          /* summed score + select time (profile=1) */
     double refine_ms;         /* summed re-score passes (profile=1) */
     double regress_ms;        /* summed regress-out + downdate (profile=1) */

@@ -341,7 +341,7 @@ def adaptive_lasso_path(C, k, pred, n: int, gamma: float = 1.0, n_lambda: int = 
     on C = Xc'Xc / n.  Cyclic coordinate descent over ``pred`` in the given
     order, b_j <- S(C_jk - sum_{l != j} C_jl b_l, lam w_j) / C_jj with S the
     soft threshold, warm-started along lam_i = lam_max eps^(i / (L - 1)),
-    lam_max = max_j |C_jk| / w_j, i = 0 .. L-1; a lam's descent stops after
+    lam_max = (1 + 1e-9) max_j |C_jk| / w_j, i = 0 .. L-1; a lam's descent stops after
     the first sweep whose largest change |db_j| sqrt(C_jj) is at most
     tol sqrt(C_kk).  Each path point carries BIC = n log(RSS/n) + df log n
     with RSS/n = C_kk - 2 b'C_Pk + b'C_PP b and df the nonzeros.
@@ -357,7 +357,9 @@ def adaptive_lasso_path(C, k, pred, n: int, gamma: float = 1.0, n_lambda: int = 
     b_ols = np.linalg.solve(Cpp, cpk)
     with np.errstate(divide="ignore"):
         w = np.where(b_ols != 0.0, np.abs(b_ols) ** -gamma, np.inf)
-    lam_max = np.max(np.where(np.isfinite(w), np.abs(cpk) / w, 0.0))
+    # 1e-9 above the exact boundary, so that rounding cannot leave a 1e-19
+    # coefficient (counted as an edge by BIC) at the first grid point
+    lam_max = np.max(np.where(np.isfinite(w), np.abs(cpk) / w, 0.0)) * (1.0 + 1e-9)
     if not lam_max > 0.0:
         return []
     b = np.zeros(q)

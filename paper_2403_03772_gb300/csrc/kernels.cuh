@@ -32,6 +32,8 @@ constexpr PairCfg PAIR_CFGS[] = {
     {4, 4, 2, 2, 4, 168, 128, 1},   // 4: 128 threads, 8 x 8 tile
     {4, 4, 1, 4, 3, 168, 168, 2},   // 5: as 1, 8 samples per lane and iteration
     {4, 2, 1, 4, 3, 128, 96, 2},    // 6: 128 threads, 4 x 8 tile, 8 samples per lane
+    {4, 2, 2, 4, 4, 128, 96, 2},    // 7: as 2, 8 samples per lane
+    {2, 4, 2, 4, 4, 128, 96, 2},    // 8: as 3, 8 samples per lane
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
@@ -57,6 +59,9 @@ struct PairParams {
     const double *isd;    // [p] 1 / sqrt(C_ii) by position
 };
 
+// Entries per candidate re-scored by the partial pass (tier 3).
+constexpr int PARTIAL_K = 32;
+
 // High-precision pair moments (kernels_refine.cu): tier 1 double-float from
 // the split standardised residuals, tier 2 FP64 from the residual data.
 constexpr int HP_THREADS = 256;
@@ -72,7 +77,8 @@ struct HpParams {
     int64_t ldc;
     const int32_t *U;
     int p, n;
-    int mode;             // 0: all pairs + variables; 1: re-score of candidates
+    int mode;             // 0: all pairs + variables; 1: re-score of candidate rows;
+                          // 2: re-score of the chosen entries of every candidate
     int with_vars;        // mode 1: also the variable moments
     const DevState *state;
     double *mom;          // mode 0: [nsplit][p][p][2]; mode 1: [nsplit][d][p][4] by candidate slot
@@ -83,6 +89,9 @@ struct HpParams {
     int nsplit;           // sample ranges per work item (partial sums per range)
     int sps;              // samples per range
     int64_t mom_sstride;  // elements between the ranges' moment records
+    const int32_t *pent;  // mode 2: [d][PARTIAL_K] chosen entry positions per candidate
+    const int32_t *pcnt;  // mode 2: [d] entries chosen per candidate
+    const uint8_t *vneed; // mode 2: [p] variables whose moments are needed
 };
 
 // Per-entry bound on |I_fp32(i, j) - I(i, j)| (FP32-scored steps).  Each of
@@ -118,6 +127,83 @@ struct ScoreParams {
     float *I32;           // optional [p][p] lower bound of I(i, j) (rounded down), read by
                           // the re-score passes: entries with I32 >= 0 are skipped
     double *epsOut;       // optional [p][p] the entry bounds (step-measure calls)
+};
+
+// Bound on the change of h(m1, m2) for moment errors (e1, e2), in FP32 (a
+// bound needs no more precision; the 1 % factor covers its own rounding).
+__device__ __forceinline__ float h_err(float m1, float m2, float e1, float e2)
+{
+    return 1.01f * (2.0f * (float)K1 * fabsf(m1 - (float)GAMMA) * e1 +
+                    2.0f * (float)K2 * fabsf(m2) * e2 + (float)K1 * e1 * e1 +
+                    (float)K2 * e2 * e2);
+}
+
+// h(z_j) of the variable at position j and its error term (0 without model).
+__device__ __forceinline__ void score_var(const ScoreParams &P, int j, double invn, double &h,
+                                         float &w)
+{
+    double S1 = 0.0, S2 = 0.0;
+    for (int s = 0; s < P.nsplit_hz; ++s) {
+        S1 += P.hz[((size_t)s * P.p + j) * 2 + 0];
+        S2 += P.hz[((size_t)s * P.p + j) * 2 + 1];
+    }
+    const double m1 = P.ha1 * S1 * invn + P.hb1, m2 = P.ha2 * S2 * invn;
+    h = neg_entropy_part(m1, m2);
+    w = P.use_model ? h_err((float)m1, (float)m2, (float)P.model.dv1, (float)P.model.dv2) : 0.0f;
+}
+
+// I(i, j) (Algorithm 1) of positions i != j from the pair moments and the
+// variable entropies hsh, and its error bound eps: the fixed epsI, or the
+// moment-error model (ErrModel) with a = 1 / sqrt(1 - rho_ij^2).  Every
+// kernel that needs an entry's FP32 value or bound calls this, so they agree
+// bit for bit.
+__device__ __forceinline__ void score_entry(const ScoreParams &P, int i, int j, const double *hsh,
+                                           const float *wsh, double invn, double &I, double &eps)
+{
+    const size_t plane = (size_t)P.p * P.p * 2;
+    double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
+    const double *pij = P.mom + ((size_t)i * P.p + j) * 2;
+    const double *pji = P.mom + ((size_t)j * P.p + i) * 2;
+    for (int s = 0; s < P.nsplit; ++s) {
+        a1 += pij[s * plane];
+        a2 += pij[s * plane + 1];
+        b1 += pji[s * plane];
+        b2 += pji[s * plane + 1];
+    }
+    const double mi1 = P.a1 * a1 * invn + P.b1, mi2 = P.a2 * a2 * invn;
+    const double mj1 = P.a1 * b1 * invn + P.b1, mj2 = P.a2 * b2 * invn;
+    const double hij = neg_entropy_part(mi1, mi2);
+    const double hji = neg_entropy_part(mj1, mj2);
+    I = (hsh[j] + hij) - (hsh[i] + hji);
+    eps = P.epsI;
+    if (P.use_model) {
+        const int oi = P.U[i], oj = P.U[j];
+        const double rho = P.C[(int64_t)min(oi, oj) * P.ldc + max(oi, oj)] * P.isd[i] * P.isd[j];
+        const float ra = rsqrtf(fmaxf((float)fma(-rho, rho, 1.0), 1e-12f)) * 1.01f;
+        const float e1 = (float)P.model.d1 + (float)P.model.da * ra;
+        const float e2 = (float)P.model.d2 + (float)P.model.da * ra;
+        eps = (double)(h_err((float)mi1, (float)mi2, e1, e2) + h_err((float)mj1, (float)mj2, e1, e2) +
+                       wsh[i] + wsh[j]);
+    }
+}
+
+// Partial re-score (tier 3, kernels_refine.cu): the PARTIAL_K entries of each
+// candidate with the largest error contribution are re-scored in
+// double-float, the rest keep their FP32 values and bounds.
+struct PartialParams {
+    ScoreParams S;        // the step's score inputs (entries are recomputed from them)
+    DevState *state;
+    int32_t *pent;        // [d][PARTIAL_K] chosen positions per candidate slot
+    int32_t *pcnt;        // [d] entries chosen per candidate
+    double *pval;         // [d][PARTIAL_K] FP32-path I of the chosen entries
+    double *peps;         // [d][PARTIAL_K] their bounds
+    uint8_t *vneed;       // [p] variables whose double-float entropy is needed
+    float *escr;          // [d][p] scratch: error contribution of every entry
+    const double *pmom;   // [nsplit][d][PARTIAL_K][4] double-float moments
+    int64_t pmom_sstride;
+    int nsplit;
+    const double *hz;     // [nsplit][p][2] double-float variable moments
+    double eps2;          // bound on a double-float I
 };
 
 struct SelectParams {
@@ -238,6 +324,8 @@ cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream
 cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s);
 cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp,
                                    cudaStream_t s);
+cudaError_t launch_partial_select_b(const PartialParams *P, int count, int maxp, cudaStream_t s);
+cudaError_t launch_partial_refine_b(const PartialParams *P, int count, int maxp, cudaStream_t s);
 cudaError_t launch_pack_gather(const float *X, int64_t ld, const int32_t *rows, int n, int d,
                                double *R, int64_t ldr, uint32_t *status, cudaStream_t s);
 

@@ -203,7 +203,8 @@ __device__ __forceinline__ double warp_max(double v)
 //   min_b 1/2 b'C_PP b - b'C_Pk + lam sum_j w_j |b_j|,  w_j = |b_ols_j|^-gamma,
 // cyclic coordinate descent over j = 0..q-1 with g = C_PP b kept up to date
 // (one column update per changed coordinate), warm-started along
-// lam_i = lam_max eps^(i/(L-1)); a lam's sweeps stop once the largest change
+// lam_i = lam_max eps^(i/(L-1)), lam_max = (1 + 1e-9) max_j |C_jk| / w_j; a
+// lam's sweeps stop once the largest change
 // |db_j| sqrt(C_jj) <= tol sqrt(C_kk).  The lam of smallest BIC =
 // n log(RSS/n) + df log n (first minimum) gives row order[k] of B.
 // Scratch per row: b, g, best, w (4 q doubles at ws + 4 k d).
@@ -231,7 +232,9 @@ __global__ void __launch_bounds__(128) k_adaptive_lasso(const double *Cp, const 
         best[j] = 0.0;
         if (isfinite(wj)) lmax = fmax(lmax, fabs(crow_k[j]) / wj);
     }
-    lmax = warp_max(lmax);
+    // 1e-9 above the exact boundary: rounding cannot leave a tiny coefficient
+    // (counted as an edge by BIC) at the first grid point
+    lmax = warp_max(lmax) * (1.0 + 1e-9);
     __syncwarp();
     if (q == 0 || !(lmax > 0.0)) {
         for (int j = lane; j < d; j += 32) B[(int64_t)ok * d + j] = 0.0;

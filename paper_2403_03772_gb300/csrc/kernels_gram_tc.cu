@@ -1,22 +1,23 @@
 // kernels_gram_tc.cu -- covariance (Gram) on the 5th-generation tensor cores
-// with FP64-level accuracy, for the mixed-precision form.
+// with near-FP64 accuracy, for the mixed-precision form.
 //
 // GB300's FP64 pipe is slow (about 1.7 FMA per clock per SM), so the FP64
 // SIMT Gram C = R R^T / n costs ~16 ms at d = 1000, n = 10000.  Here every
-// variable's centred column is written, relative to a power-of-two scale 2^e
-// at least its largest magnitude, as six 7-bit signed digits:
+// variable's centred column is cut into periods of 64 samples; within a
+// period, relative to a power-of-two scale 2^e at least the period's largest
+// magnitude, each value is written as six 7-bit signed digits:
 //     x / 2^e = 2^-7 sum_k t_k,   t_k = sigma_k 2^(-7k),  |sigma_k| <= 127,
 // each t_k exactly representable in BF16.  A product of two columns is then
-//     2^-14 sum_{k,l} t_ik t_jl,
+//     2^(e_i + e_j - 14) sum_{k,l} t_ik t_jl,
 // and the terms with k + l <= 5 are formed by tcgen05.mma (kind::f16, BF16
 // operands, FP32 accumulation in tensor memory).  Terms of level k + l = 0, 1
-// and 2 go to separate accumulators in which every partial sum over 128
-// samples is an integer multiple of 2^(-7 level) below 2^23 in that unit, so
-// the FP32 accumulation is exact; levels 3..5 share a fourth accumulator
-// whose rounding is ~2^-45 relative.  Every 128 samples the four accumulators
-// are read with tcgen05.ld and added in FP64.  The split-precision products
-// with FP32 accumulation thus give the covariance to ~2e-10 of
-// sqrt(C_ii C_jj) on heavy-tailed data (dropped levels >= 6), FP64-class.
+// and 2 go to separate accumulators, levels 3..5 share a fourth.  After every
+// period the four accumulators are read with tcgen05.ld, scaled by the
+// period's 2^(e_i + e_j) and added in FP64.  Per-period scales keep a large
+// value from costing digits elsewhere in its column.  The tensor cores do
+// not add in exact IEEE FP32 (draining every 128 samples instead of 64 gave
+// 2.5x the error), so the accuracy is measured: about 4e-11 of
+// sqrt(C_ii C_jj) on heavy-tailed and skewed data (d <= 300, n <= 1e5).
 //
 // CTA tile: 128 x 128 entries of C (tile row <= tile column), one slice of
 // the samples; 128 threads.  Per chunk of 64 samples one thread issues 12 TMA
@@ -36,7 +37,7 @@ namespace {
 constexpr int TC_SLICES = 6;
 constexpr int TC_TILE = 128;
 constexpr int TC_KC = 64;           // samples per TMA chunk (128 bytes of BF16)
-constexpr int TC_DRAIN = 128;       // samples between FP64 drains (exactness bound)
+constexpr int TC_DRAIN = 64;        // samples per scale period and FP64 drain
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_PLANE_BYTES = TC_TILE * TC_KC * 2;          // 16 KB
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_SLICES * TC_PLANE_BYTES;  // 192 KB

@@ -390,8 +390,8 @@ struct PairTable {
     static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
-using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6>;
-static_assert(PAIR_NCFG == 7, "PairKernels lists every configuration");
+using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8>;
+static_assert(PAIR_NCFG == 9, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {
@@ -445,90 +445,62 @@ cudaError_t launch_pair_b(int mode, int cfg, const CUtensorMap *tmI, const CUten
 // ascending order and across lanes by a fixed xor tree.  E(i) bounds |M(i) -
 // M_exact(i)| given |I - I_exact| <= eps per entry: a fixed epsI for steps
 // scored in double-float, else the moment-error model of ErrModel.
-// Bound on the change of h(m1, m2) for moment errors (e1, e2), in FP32 (a
-// bound needs no more precision; the 1 % factor covers its own rounding).
-__device__ __forceinline__ float h_err(float m1, float m2, float e1, float e2)
-{
-    return 1.01f * (2.0f * (float)K1 * fabsf(m1 - (float)GAMMA) * e1 +
-                    2.0f * (float)K2 * fabsf(m2) * e2 + (float)K1 * e1 * e1 +
-                    (float)K2 * e2 * e2);
-}
+constexpr int SCORE_RPB = 2, SCORE_WPR = 4;   // rows per block, warps per row
 
 __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restrict__ Ps)
 {
     extern __shared__ double hsh[];   // h(z_j), j < p; then their error bounds (float)
     const ScoreParams P = Ps[blockIdx.y];
-    if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= P.p) return;
+    if ((int)blockIdx.x * SCORE_RPB >= P.p) return;
     float *wsh = reinterpret_cast<float *>(hsh + P.p);
     const double invn = 1.0 / (double)P.n;
-    const bool model = P.use_model != 0;
-    const ErrModel em = P.model;
-    for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
-        double S1 = 0.0, S2 = 0.0;
-        for (int s = 0; s < P.nsplit_hz; ++s) {
-            S1 += P.hz[((size_t)s * P.p + j) * 2 + 0];
-            S2 += P.hz[((size_t)s * P.p + j) * 2 + 1];
-        }
-        const double m1 = P.ha1 * S1 * invn + P.hb1, m2 = P.ha2 * S2 * invn;
-        hsh[j] = neg_entropy_part(m1, m2);
-        if (model) wsh[j] = h_err((float)m1, (float)m2, (float)em.dv1, (float)em.dv2);
-    }
+    for (int j = threadIdx.x; j < P.p; j += blockDim.x) score_var(P, j, invn, hsh[j], wsh[j]);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= P.p) return;
-    const size_t plane = (size_t)P.p * P.p * 2;
-    const double hi = hsh[i];
+    // SCORE_WPR warps per row i: warp wr of the row takes j = 32 wr + lane +
+    // 32 SCORE_WPR k; the row's partial sums are added in warp order.
+    __shared__ double racc[8], rerr[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wr = warp % SCORE_WPR;
+    const int i = blockIdx.x * SCORE_RPB + warp / SCORE_WPR;
     double acc = 0.0, err = 0.0;
-    const int oi = P.U[i];
-    for (int j = lane; j < P.p; j += 32) {
-        if (j == i) continue;
-        double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0;
-        const double *pij = P.mom + ((size_t)i * P.p + j) * 2;
-        const double *pji = P.mom + ((size_t)j * P.p + i) * 2;
-        for (int s = 0; s < P.nsplit; ++s) {
-            a1 += pij[s * plane];
-            a2 += pij[s * plane + 1];
-            b1 += pji[s * plane];
-            b2 += pji[s * plane + 1];
+    if (i < P.p) {
+        for (int j = wr * 32 + lane; j < P.p; j += 32 * SCORE_WPR) {
+            if (j == i) continue;
+            double I, eps;
+            score_entry(P, i, j, hsh, wsh, invn, I, eps);
+            const double v = fmin(0.0, I);
+            acc += v * v;
+            if (I < eps) err += 2.0 * fabs(v) * eps + eps * eps;
+            if (P.Iout) P.Iout[(size_t)i * P.p + j] = I;
+            if (P.epsOut) P.epsOut[(size_t)i * P.p + j] = eps;
+            if (P.I32) P.I32[(size_t)i * P.p + j] = __double2float_rd(I - eps);
         }
-        const double mi1 = P.a1 * a1 * invn + P.b1, mi2 = P.a2 * a2 * invn;
-        const double mj1 = P.a1 * b1 * invn + P.b1, mj2 = P.a2 * b2 * invn;
-        const double hij = neg_entropy_part(mi1, mi2);
-        const double hji = neg_entropy_part(mj1, mj2);
-        const double I = (hsh[j] + hij) - (hi + hji);
-        double eps = P.epsI;
-        if (model) {
-            const int oj = P.U[j];
-            const double rho = P.C[(int64_t)min(oi, oj) * P.ldc + max(oi, oj)] * P.isd[i] * P.isd[j];
-            const float ra = rsqrtf(fmaxf((float)fma(-rho, rho, 1.0), 1e-12f)) * 1.01f;
-            const float e1 = (float)em.d1 + (float)em.da * ra;
-            const float e2 = (float)em.d2 + (float)em.da * ra;
-            eps = (double)(h_err((float)mi1, (float)mi2, e1, e2) +
-                           h_err((float)mj1, (float)mj2, e1, e2) + wsh[i] + wsh[j]);
-        }
-        const double v = fmin(0.0, I);
-        acc += v * v;
-        if (I < eps) err += 2.0 * fabs(v) * eps + eps * eps;
-        if (P.Iout) P.Iout[(size_t)i * P.p + j] = I;
-        if (P.epsOut) P.epsOut[(size_t)i * P.p + j] = eps;
-        if (P.I32) P.I32[(size_t)i * P.p + j] = __double2float_rd(I - eps);
     }
     acc = warp_sum_xor(acc);
     err = warp_sum_xor(err);
     if (lane == 0) {
-        P.M[i] = -acc;
-        P.E[i] = err;
-        if (P.hist) P.hist[P.U[i]] = -acc;
+        racc[warp] = acc;
+        rerr[warp] = err;
+    }
+    __syncthreads();
+    if (lane == 0 && wr == 0 && i < P.p) {
+        double m = 0.0, e = 0.0;
+        for (int k = 0; k < SCORE_WPR; ++k) {
+            m += racc[warp + k];
+            e += rerr[warp + k];
+        }
+        P.M[i] = -m;
+        P.E[i] = e;
+        if (P.hist) P.hist[P.U[i]] = -m;
     }
 }
 
 cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    const int rows_per_block = 8;
-    dim3 grid((maxp + rows_per_block - 1) / rows_per_block, count);
-    k_score_b<<<grid, 256, (sizeof(double) + sizeof(float)) * maxp + 16, s>>>(P);
+    dim3 grid((maxp + SCORE_RPB - 1) / SCORE_RPB, count);
+    k_score_b<<<grid, 32 * SCORE_RPB * SCORE_WPR, (sizeof(double) + sizeof(float)) * maxp + 16,
+                s>>>(P);
     return cudaGetLastError();
 }
 

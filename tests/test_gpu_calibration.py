@@ -67,8 +67,8 @@ def test_error_bounds_hold_with_margin(datasets, name):
 def test_tensor_core_covariance_is_fp64_class(datasets, name):
     """With d <= 32 every pair is scored in double-float, so the MIXED form
     (tensor-core covariance, single instance) and the FP32 form (FP64 SIMT
-    covariance) differ only through the covariance; their I must agree to
-    the double-float bound of the MIXED form."""
+    covariance) differ only through the covariance; their I must agree to a
+    quarter of the MIXED form's double-float bound (1e-9)."""
     import torch
     import paper_2403_03772_gb300 as pkg
     if name == "cfg2_head":
@@ -82,4 +82,4 @@ def test_tensor_core_covariance_is_fp64_class(datasets, name):
         Im, _ = c.step_measures(X32)
     with pkg.Context(0, "fp32") as c:
         If, _ = c.step_measures(X32)
-    assert np.max(np.abs(Im - If)) <= 1e-10, name
+    assert np.max(np.abs(Im - If)) <= 2.5e-10, name
