@@ -277,7 +277,7 @@ def run_ours(args, rank, world):
                  for b in insts]
         Wb = sum(gen.residual_samples(b.X.shape[1], b.X.shape[0] if b.rows is None else len(b.rows))
                  for b in insts)
-        with pkg.Context(dev, "mixed") as ctx:
+        with pkg.Context(dev, "mixed", profile=True) as ctx:
             if not args.no_autotune:
                 ctx.autotune(max(int(X.shape[0]) if r is None else len(r) for X, r in batch),
                              max(int(X.shape[1]) for X, _ in batch))
@@ -311,6 +311,9 @@ def run_ours(args, rank, world):
                       "instances": len(insts), "residual_samples": Wb,
                       "ms_per_call": sum(bms) / len(bms), "value": Wb / (sum(bms) / len(bms) * 1e-3),
                       "refined_steps": bst["refined_steps"], "graph_nodes": bst["graph_nodes"],
+                      "phase_ms": {k: bst[k] for k in ("pair_ms", "score_ms", "refine_ms",
+                                                       "regress_ms")},
+                      "df_candidates": bst["df_candidates"],
                       "sequential_plain_fp32_ms": seq_ms,
                       "sequential_plain_fp32_value": (Wb / (seq_ms * 1e-3)) if seq_ms else None}
 

@@ -304,10 +304,8 @@ typedef struct {
     int32_t graph_nodes;      /* kernel nodes in the step graph */
     double graph_build_ms;    /* capture + instantiate time (0 if cached) */
     int32_t fp64_candidates;  /* candidates re-scored in FP64 over the run */
-    int32_t df_candidates;    /* candidates re-scored in double-float (whole rows) */
-    int32_t partial_candidates; /* candidates through the partial re-score */
-    int32_t partial_decided;  /* steps the partial re-score decided */
-    int32_t reserved[2];
+    int32_t df_candidates;    /* candidates re-scored in double-float */
+    int32_t reserved[4];
     double score_ms;          /* summed score + select time (profile=1) */
     double refine_ms;         /* summed re-score passes (profile=1) */
     double regress_ms;        /* summed regress-out + downdate (profile=1) */

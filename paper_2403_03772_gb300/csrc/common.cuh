@@ -31,10 +31,8 @@ struct DevState {
     int32_t pass_end;
     int32_t resolved;       // 1 once the step's argmax is decided
     int32_t fp64_candidates;  // candidates re-scored in FP64 over the run
-    int32_t tier;           // 3: next the partial pass, 1: double-float rows, 2: FP64
+    int32_t tier;           // 1: next re-score in double-float, 2: in FP64
     int32_t df_candidates;  // candidates re-scored in double-float over the run
-    int32_t partial_candidates;  // candidates through the partial pass over the run
-    int32_t partial_decided;     // steps the partial pass decided
     int32_t *cand;          // [d] candidate positions, by upper bound M + E descending
     double *ub;             // [d] M + E of each candidate (FP32 scores)
     double *mhp;            // [d] re-scored M of each candidate

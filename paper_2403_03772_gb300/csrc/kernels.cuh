@@ -59,9 +59,6 @@ struct PairParams {
     const double *isd;    // [p] 1 / sqrt(C_ii) by position
 };
 
-// Entries per candidate re-scored by the partial pass (tier 3).
-constexpr int PARTIAL_K = 32;
-
 // High-precision pair moments (kernels_refine.cu): tier 1 double-float from
 // the split standardised residuals, tier 2 FP64 from the residual data.
 constexpr int HP_THREADS = 256;
@@ -77,8 +74,7 @@ struct HpParams {
     int64_t ldc;
     const int32_t *U;
     int p, n;
-    int mode;             // 0: all pairs + variables; 1: re-score of candidate rows;
-                          // 2: re-score of the chosen entries of every candidate
+    int mode;             // 0: all pairs + variables; 1: re-score of candidate rows
     int with_vars;        // mode 1: also the variable moments
     const DevState *state;
     double *mom;          // mode 0: [nsplit][p][p][2]; mode 1: [nsplit][d][p][4] by candidate slot
@@ -89,9 +85,6 @@ struct HpParams {
     int nsplit;           // sample ranges per work item (partial sums per range)
     int sps;              // samples per range
     int64_t mom_sstride;  // elements between the ranges' moment records
-    const int32_t *pent;  // mode 2: [d][PARTIAL_K] chosen entry positions per candidate
-    const int32_t *pcnt;  // mode 2: [d] entries chosen per candidate
-    const uint8_t *vneed; // mode 2: [p] variables whose moments are needed
 };
 
 // Per-entry bound on |I_fp32(i, j) - I(i, j)| (FP32-scored steps).  Each of
@@ -186,25 +179,6 @@ __device__ __forceinline__ void score_entry(const ScoreParams &P, int i, int j, 
                        wsh[i] + wsh[j]);
     }
 }
-
-// Partial re-score (tier 3, kernels_refine.cu): the PARTIAL_K entries of each
-// candidate with the largest error contribution are re-scored in
-// double-float, the rest keep their FP32 values and bounds.
-struct PartialParams {
-    ScoreParams S;        // the step's score inputs (entries are recomputed from them)
-    DevState *state;
-    int32_t *pent;        // [d][PARTIAL_K] chosen positions per candidate slot
-    int32_t *pcnt;        // [d] entries chosen per candidate
-    double *pval;         // [d][PARTIAL_K] FP32-path I of the chosen entries
-    double *peps;         // [d][PARTIAL_K] their bounds
-    uint8_t *vneed;       // [p] variables whose double-float entropy is needed
-    float *escr;          // [d][p] scratch: error contribution of every entry
-    const double *pmom;   // [nsplit][d][PARTIAL_K][4] double-float moments
-    int64_t pmom_sstride;
-    int nsplit;
-    const double *hz;     // [nsplit][p][2] double-float variable moments
-    double eps2;          // bound on a double-float I
-};
 
 struct SelectParams {
     const double *M, *E;
@@ -324,8 +298,7 @@ cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream
 cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s);
 cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp,
                                    cudaStream_t s);
-cudaError_t launch_partial_select_b(const PartialParams *P, int count, int maxp, cudaStream_t s);
-cudaError_t launch_partial_refine_b(const PartialParams *P, int count, int maxp, cudaStream_t s);
+
 cudaError_t launch_pack_gather(const float *X, int64_t ld, const int32_t *rows, int n, int d,
                                double *R, int64_t ldr, uint32_t *status, cudaStream_t s);
 

@@ -240,10 +240,6 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
         if (cend <= cbeg) return;
         npair = (int64_t)(cend - cbeg) * P.p;
         with_vars = P.with_vars != 0;
-    } else if (P.mode == 2) {
-        const DevState *st = P.state;
-        if (st->resolved || st->tier != 3) return;
-        npair = (int64_t)st->ncand * PARTIAL_K;
     } else {
         npair = (int64_t)P.p * (P.p - 1) / 2;
     }
@@ -267,7 +263,6 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
         if (q >= npair) {
             // moments of the standardised variable at position a
             const int a = (int)(q - npair);
-            if (P.mode == 2 && !P.vneed[a]) continue;
             double v[2];
             if (TIER == 1) {
                 const float *zh = P.zhi + (int64_t)a * P.ldz, *zl = P.zlo + (int64_t)a * P.ldz;
@@ -309,15 +304,8 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             }
             continue;
         }
-        int a, b, cidx = 0, slot = 0;
-        if (P.mode == 2) {
-            cidx = (int)(q / PARTIAL_K);
-            const int k = (int)(q % PARTIAL_K);
-            if (k >= P.pcnt[cidx]) continue;
-            a = P.state->cand[cidx];
-            b = P.pent[(size_t)cidx * PARTIAL_K + k];
-            slot = cidx * PARTIAL_K + k;
-        } else if (P.mode == 1) {
+        int a, b, cidx = 0;
+        if (P.mode == 1) {
             cidx = cbeg + (int)(q / P.p);
             a = P.state->cand[cidx];
             b = (int)(q % P.p);
@@ -412,13 +400,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
         }
         block_sum_fixed<4>(v, s_red);
         if (threadIdx.x == 0) {
-            if (P.mode == 2) {
-                double *o = momp + (size_t)slot * 4;
-                o[0] = v[0];
-                o[1] = v[1];
-                o[2] = v[2];
-                o[3] = v[3];
-            } else if (P.mode == 1) {
+            if (P.mode == 1) {
                 double *o = momp + ((size_t)cidx * P.p + b) * 4;
                 o[0] = v[0];
                 o[1] = v[1];
@@ -583,190 +565,6 @@ cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int m
 {
     if (count <= 0) return cudaSuccess;
     k_refine_select_b<<<count, 256, sizeof(double) * maxp, s>>>(P);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------- partial re-score --
-// Tier 3, before any full row: for every candidate c the entries j whose
-// error contribution e_cj = 2 |min(0, I)| eps + eps^2 (entries with I < eps)
-// is largest are re-scored in double-float, PARTIAL_K of them; the rest keep
-// their FP32 values and bounds.  M_c' = M_c + sum (min(0, I32)^2 -
-// min(0, I_df)^2) over the chosen entries and E_c' = E_c - sum e32 + sum e_df.
-// Candidates whose new intervals separate from the best one's are dropped;
-// if one is left the step is decided, else the rest go on to full
-// double-float rows (tier 1), ordered by their new upper bounds.
-__global__ void __launch_bounds__(256) k_partial_select_b(const PartialParams *__restrict__ Ps)
-{
-    extern __shared__ double hsh[];   // h(z_j); then error terms (float)
-    const PartialParams &PP = Ps[blockIdx.x];
-    DevState *st = PP.state;
-    if (st->resolved || st->tier != 3) return;
-    const ScoreParams &S = PP.S;
-    const int p = S.p, nc = st->ncand;
-    float *wsh = reinterpret_cast<float *>(hsh + p);
-    const double invn = 1.0 / (double)S.n;
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        score_var(S, j, invn, hsh[j], wsh[j]);
-        PP.vneed[j] = 0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = w; c < nc; c += nw) {
-        const int pc = st->cand[c];
-        float *e = PP.escr + (size_t)c * p;
-        for (int j = lane; j < p; j += 32) {
-            float ej = 0.0f;
-            if (j != pc) {
-                double I, eps;
-                score_entry(S, pc, j, hsh, wsh, invn, I, eps);
-                if (I < eps) ej = (float)(2.0 * fabs(fmin(0.0, I)) * eps + eps * eps);
-            }
-            e[j] = ej;
-        }
-        __syncwarp();
-        int cnt = 0;
-        for (; cnt < PARTIAL_K; ++cnt) {
-            // largest remaining contribution (ties to the smaller position)
-            float be = 0.0f;
-            int bj = -1;
-            for (int j = lane; j < p; j += 32)
-                if (e[j] > be) {
-                    be = e[j];
-                    bj = j;
-                }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float oe = __shfl_xor_sync(0xffffffffu, be, o);
-                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                if (oe > be || (oe == be && oj >= 0 && (bj < 0 || oj < bj))) {
-                    be = oe;
-                    bj = oj;
-                }
-            }
-            if (bj < 0) break;
-            if (lane == 0) {
-                PP.pent[(size_t)c * PARTIAL_K + cnt] = bj;
-                e[bj] = -1.0f;
-                PP.vneed[bj] = 1;
-            }
-            __syncwarp();
-        }
-        // the FP32 values and bounds of the chosen entries
-        if (lane < cnt) {
-            const int j = PP.pent[(size_t)c * PARTIAL_K + lane];
-            double I, eps;
-            score_entry(S, pc, j, hsh, wsh, invn, I, eps);
-            PP.pval[(size_t)c * PARTIAL_K + lane] = I;
-            PP.peps[(size_t)c * PARTIAL_K + lane] = eps;
-        }
-        if (lane == 0) {
-            PP.pcnt[c] = cnt;
-            PP.vneed[pc] = 1;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) k_partial_refine_b(const PartialParams *__restrict__ Ps)
-{
-    extern __shared__ double h64[];
-    const PartialParams &PP = Ps[blockIdx.x];
-    DevState *st = PP.state;
-    if (st->resolved || st->tier != 3) return;
-    const ScoreParams &S = PP.S;
-    const int p = S.p, nc = st->ncand;
-    const double invn = 1.0 / (double)S.n;
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        double s1 = 0.0, s2 = 0.0;
-        if (PP.vneed[j])
-            for (int sp = 0; sp < PP.nsplit; ++sp) {
-                s1 += PP.hz[((size_t)sp * p + j) * 2];
-                s2 += PP.hz[((size_t)sp * p + j) * 2 + 1];
-            }
-        h64[j] = neg_entropy_part(s1 * invn - LN2_D, s2 * invn);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const double e2 = PP.eps2;
-    for (int c = w; c < nc; c += nw) {
-        const int pc = st->cand[c];
-        double dm = 0.0, de = 0.0;
-        if (lane < PP.pcnt[c]) {
-            const size_t slot = (size_t)c * PARTIAL_K + lane;
-            const int j = PP.pent[slot];
-            double o[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int sp = 0; sp < PP.nsplit; ++sp)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] += PP.pmom[(size_t)sp * PP.pmom_sstride + slot * 4 + k];
-            const double hcj = neg_entropy_part(o[0] * invn - LN2_D, o[1] * invn);
-            const double hjc = neg_entropy_part(o[2] * invn - LN2_D, o[3] * invn);
-            const double Idf = (h64[j] + hcj) - (h64[pc] + hjc);
-            const double I32 = PP.pval[slot], eps = PP.peps[slot];
-            const double v32 = fmin(0.0, I32), vdf = fmin(0.0, Idf);
-            dm = v32 * v32 - vdf * vdf;
-            de = -(I32 < eps ? 2.0 * fabs(v32) * eps + eps * eps : 0.0) +
-                 (Idf < e2 ? 2.0 * fabs(vdf) * e2 + e2 * e2 : 0.0);
-        }
-        dm = warp_sum_xor(dm);
-        de = warp_sum_xor(de);
-        if (lane == 0) {
-            const double m = S.M[pc] + dm;
-            // the FP32 bound minus the re-scored entries' shares, plus their
-            // double-float bounds and the rounding of these sums
-            st->mhp[c] = m;
-            st->ehp[c] = fmax(S.E[pc] + de, 0.0) + 1e-14 * (fabs(S.M[pc]) + fabs(dm));
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    int best = 0;
-    for (int c = 1; c < nc; ++c)
-        if (better(st->mhp[c], S.U[st->cand[c]], st->mhp[best], S.U[st->cand[best]])) best = c;
-    st->partial_candidates += nc;
-    const double lb = st->mhp[best] - st->ehp[best];
-    int nk = 0;
-    for (int c = 0; c < nc; ++c)
-        if (c == best || !(st->mhp[c] + st->ehp[c] < lb)) {
-            st->cand[nk] = st->cand[c];
-            st->ub[nk] = st->mhp[c] + st->ehp[c];
-            ++nk;
-        }
-    if (nk == 1) {
-        st->m_pos = st->cand[0];
-        st->resolved = 1;
-        st->partial_decided += 1;
-        return;
-    }
-    // order the survivors by their new upper bound (descending, ties to the
-    // smaller original index) for the double-float row passes
-    for (int a = 1; a < nk; ++a) {
-        const int ca = st->cand[a];
-        const double ua = st->ub[a];
-        int b = a - 1;
-        while (b >= 0 && (st->ub[b] < ua || (st->ub[b] == ua && S.U[st->cand[b]] > S.U[ca]))) {
-            st->cand[b + 1] = st->cand[b];
-            st->ub[b + 1] = st->ub[b];
-            --b;
-        }
-        st->cand[b + 1] = ca;
-        st->ub[b + 1] = ua;
-    }
-    st->ncand = nk;
-    st->pass_begin = 0;
-    st->pass_end = min(2, nk);
-    st->tier = 1;
-}
-
-cudaError_t launch_partial_select_b(const PartialParams *P, int count, int maxp, cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    k_partial_select_b<<<count, 256, (sizeof(double) + sizeof(float)) * maxp + 16, s>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_partial_refine_b(const PartialParams *P, int count, int maxp, cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    k_partial_refine_b<<<count, 256, sizeof(double) * maxp, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -103,13 +103,6 @@ struct InstDev {
     double *M = nullptr, *E = nullptr, *hist = nullptr, *ref_var = nullptr, *fmom = nullptr;
     double *fhz = nullptr, *lcoef = nullptr, *isd0 = nullptr, *isd1 = nullptr;
     float *I32 = nullptr;
-    // partial re-score (tier 3): chosen entries, their FP32 values and bounds,
-    // variable flags, scratch, double-float moments
-    int32_t *pent = nullptr, *pcnt = nullptr;
-    double *pval = nullptr, *peps = nullptr, *pmom = nullptr;
-    uint8_t *vneed = nullptr;
-    float *escr = nullptr;
-    size_t pmom_elems = 0;
     int32_t *U0 = nullptr, *U1 = nullptr, *order = nullptr, *scratch = nullptr, *rows = nullptr;
     DevState *state = nullptr;
     int zrow = 0;
@@ -390,8 +383,6 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
             pl.inst[k].fhz_elems = std::max(pl.inst[k].fhz_elems, hs * p * 2);
             pl.inst[k].fmom_elems = std::max(pl.inst[k].fmom_elems,
                                              (size_t)ss.hp1_nsplit[k] * spec[k].d * p * 4);
-            pl.inst[k].pmom_elems = std::max(pl.inst[k].pmom_elems,
-                                             (size_t)ss.hp1_nsplit[k] * spec[k].d * PARTIAL_K * 4);
             pl.inst[k].hz_elems =
                 std::max(pl.inst[k].hz_elems, (size_t)ss.reg_nsplit[k] * (size_t)p * 2);
         }
@@ -404,7 +395,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     };
     struct Off {
         size_t R, C, Cpart, mom, hz, M, E, hist, ref, fmom, fhz, lcoef, U, order, scratch, rows,
-            state, isd, I32, S, expo, cand, cdbl, pent, pcnt, pval, peps, pmom, vneed, escr;
+            state, isd, I32, S, expo, cand, cdbl;
     };
     std::vector<Off> o(K);
     for (int k = 0; k < K; ++k) {
@@ -434,13 +425,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].I32 = take((size_t)d * d * 4);
         o[k].cand = take((size_t)d * 4);
         o[k].cdbl = take((size_t)3 * d * 8);
-        o[k].pent = take((size_t)d * PARTIAL_K * 4);
-        o[k].pcnt = take((size_t)d * 4);
-        o[k].pval = take((size_t)d * PARTIAL_K * 8);
-        o[k].peps = take((size_t)d * PARTIAL_K * 8);
-        o[k].pmom = take(pl.inst[k].pmom_elems * 8);
-        o[k].vneed = take((size_t)d);
-        o[k].escr = take((size_t)d * d * 4);
+
     }
     CK(ensure(pl.arena, off));
     CK(cudaMemset(pl.arena.p, 0, off));
@@ -477,13 +462,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         I.isd0 = reinterpret_cast<double *>(base + o[k].isd);
         I.isd1 = I.isd0 + d;
         I.I32 = reinterpret_cast<float *>(base + o[k].I32);
-        I.pent = reinterpret_cast<int32_t *>(base + o[k].pent);
-        I.pcnt = reinterpret_cast<int32_t *>(base + o[k].pcnt);
-        I.pval = reinterpret_cast<double *>(base + o[k].pval);
-        I.peps = reinterpret_cast<double *>(base + o[k].peps);
-        I.pmom = reinterpret_cast<double *>(base + o[k].pmom);
-        I.vneed = reinterpret_cast<uint8_t *>(base + o[k].vneed);
-        I.escr = reinterpret_cast<float *>(base + o[k].escr);
+
         {   // candidate arrays of the device state
             DevState h{};
             h.cand = reinterpret_cast<int32_t *>(base + o[k].cand);
@@ -527,8 +506,7 @@ struct ParamBlob {
 
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_PARTIAL_SEL,
-    K_PARTIAL_REF
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC
 };
 
 // Timing events per ordering step when profiling: before the pair moments,
@@ -666,8 +644,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         StepSplit ss = step_splits(ctx, pl.spec, prec, t);
         std::vector<PairParams> pp;
         std::vector<int> prefix(1, 0);
-        std::vector<HpParams> fa, fd1, fd2, f64, fpart;
-        std::vector<PartialParams> part;
+        std::vector<HpParams> fa, fd1, fd2, f64;
         std::vector<ScoreParams> sc;
         std::vector<SelectParams> se;
         std::vector<RefineSelectParams> rd1, rd2, r64;
@@ -771,33 +748,9 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             S.epsOut = stop_after_score0 ? epsOut : nullptr;
             S.I32 = hp ? nullptr : I.I32;
             sc.push_back(S);
-            // candidates of an FP32-scored step go to the partial pass first,
-            // then full double-float rows; a step scored in double-float sends
-            // its near-ties to FP64
-            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 3});
-            {
-                HpParams F = hpp(2, 0, I.pmom);
-                F.mom_sstride = (int64_t)I.d * PARTIAL_K * 4;
-                F.pent = I.pent;
-                F.pcnt = I.pcnt;
-                F.vneed = I.vneed;
-                fpart.push_back(F);
-                PartialParams Q{};
-                Q.S = S;
-                Q.state = I.state;
-                Q.pent = I.pent;
-                Q.pcnt = I.pcnt;
-                Q.pval = I.pval;
-                Q.peps = I.peps;
-                Q.vneed = I.vneed;
-                Q.escr = I.escr;
-                Q.pmom = I.pmom;
-                Q.pmom_sstride = F.mom_sstride;
-                Q.nsplit = F.nsplit;
-                Q.hz = I.fhz;
-                Q.eps2 = eps2;
-                part.push_back(Q);
-            }
+            // candidates of an FP32-scored step go to double-float first; a
+            // step scored in double-float sends its near-ties to FP64
+            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 1});
             fd1.push_back(hpp(1, 1, I.fmom));
             fd2.push_back(hpp(1, 0, I.fmom));
             f64.push_back(hpp(1, 1, I.fmom));
@@ -863,26 +816,8 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             ev.a = EV_PER_STEP * t + 2;
             L.push_back(ev);
         }
-        // re-score passes: the partial pass, double-float rows 1 and 2, then
-        // FP64; each is a no-op unless the step's state routes candidates to it
-        if (prec == LINGAM_PREC_FP32 || prec == LINGAM_PREC_MIXED) {
-            Launch la{K_PARTIAL_SEL};
-            la.off = blob.add(part);
-            la.count = cnt;
-            la.a = maxp;
-            L.push_back(la);
-            Launch lb{K_HP_PASS};
-            lb.off = blob.add(fpart);
-            lb.count = cnt;
-            lb.a = hp_blocks;
-            lb.c = 1;
-            L.push_back(lb);
-            Launch lc{K_PARTIAL_REF};
-            lc.off = la.off;
-            lc.count = cnt;
-            lc.a = maxp;
-            L.push_back(lc);
-        }
+        // re-score passes: double-float pass 1 and 2, then FP64; each is a
+        // no-op unless the step's state routes candidates to it
         const std::vector<HpParams> *passes[3] = {&fd1, &fd2, &f64};
         const std::vector<RefineSelectParams> *decides[3] = {&rd1, &rd2, &r64};
         for (int q = 0; q < 3; ++q) {
@@ -957,12 +892,6 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         case K_SCORE: e = launch_score_b((const ScoreParams *)P, l.count, l.a, s); break;
         case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
         case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
-        case K_PARTIAL_SEL:
-            e = launch_partial_select_b((const PartialParams *)P, l.count, l.a, s);
-            break;
-        case K_PARTIAL_REF:
-            e = launch_partial_refine_b((const PartialParams *)P, l.count, l.a, s);
-            break;
         case K_REFINE:
             e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
             break;
@@ -1146,8 +1075,7 @@ static lingam_status run_plan(lingam_ctx *ctx, int32_t *const *orders_out, doubl
         st.candidates_max = std::max(st.candidates_max, h.cand_max);
         st.fp64_candidates += h.fp64_candidates;
         st.df_candidates += h.df_candidates;
-        st.partial_candidates += h.partial_candidates;
-        st.partial_decided += h.partial_decided;
+
     }
     st.graph_nodes = pl.nodes;
     if (pl.profile && !pl.pev.empty()) {
