@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace lg {
 
@@ -53,7 +54,8 @@ struct PairParams {
     int nchunks;          // ceil(n / PAIR_S)
     int cps;              // chunks per sample split
     int nsplit;
-    double *mom;          // out [nsplit][p][p][2] moment sums of entry (i, j)
+    float2 *mom;          // out [nsplit][p][p][2] moment sums of entry (i, j), each as a
+                          // double-float (hi, lo)
     uint32_t *status;
     int row0;             // first row of this instance in the z tensor
     const double *isd;    // [p] 1 / sqrt(C_ii) by position
@@ -100,7 +102,8 @@ struct ErrModel {
 };
 
 struct ScoreParams {
-    const double *mom;    // [nsplit][p][p][2]
+    const double *mom;    // [nsplit][p][p][2] FP64 sums (steps scored in high precision)
+    const float2 *mom2;   // or [nsplit][p][p][2] double-float sums from the FP32 pair kernel
     int nsplit, p, n;
     const double *hz;     // [nsplit_hz][p][2]
     int nsplit_hz;
@@ -143,6 +146,50 @@ __device__ __forceinline__ void score_var(const ScoreParams &P, int j, double in
     const double m1 = P.ha1 * S1 * invn + P.hb1, m2 = P.ha2 * S2 * invn;
     h = neg_entropy_part(m1, m2);
     w = P.use_model ? h_err((float)m1, (float)m2, (float)P.model.dv1, (float)P.model.dv2) : 0.0f;
+}
+
+// h = -K1 (m1 - GAMMA)^2 - K2 m2^2 in double-float (the FP32-scored steps:
+// their moment sums arrive as double-floats, so no FP64 arithmetic is needed
+// per entry; GB300 runs FP64 at 1/75 of the FP32 rate).
+constexpr float K1_HI = (float)K1, K1_LO = (float)(K1 - (double)(float)K1);
+constexpr float K2_HI = (float)K2, K2_LO = (float)(K2 - (double)(float)K2);
+constexpr float GAMMA_HI = (float)GAMMA, GAMMA_LO = (float)(GAMMA - (double)(float)GAMMA);
+
+__device__ __forceinline__ dfl df_neg_entropy(dfl m1, dfl m2)
+{
+    const dfl a = df_add(m1, dfl{-GAMMA_HI, -GAMMA_LO});
+    const dfl t1 = df_mul(df_mul(a, a), dfl{K1_HI, K1_LO});
+    const dfl t2 = df_mul(df_mul(m2, m2), dfl{K2_HI, K2_LO});
+    return df_neg(df_add(t1, t2));
+}
+
+// I(i, j) of an FP32-scored step in double-float from the double-float pair
+// moment sums; c1, b1, c2 scale the sums to moments (m1 = c1 S1 + b1,
+// m2 = c2 S2); hd holds h(z_j) as double-floats.  Also returns the FP32
+// moments of both residuals for the error model.
+__device__ __forceinline__ dfl score_entry_df(const ScoreParams &P, int i, int j, const dfl *hd,
+                                              dfl c1, dfl b1, dfl c2, float (&mf)[4])
+{
+    const size_t plane = (size_t)P.p * P.p * 2;
+    dfl a1{0.0f, 0.0f}, a2{0.0f, 0.0f}, e1{0.0f, 0.0f}, e2{0.0f, 0.0f};
+    const float2 *pij = P.mom2 + ((size_t)i * P.p + j) * 2;
+    const float2 *pji = P.mom2 + ((size_t)j * P.p + i) * 2;
+    for (int s = 0; s < P.nsplit; ++s) {
+        const float2 x1 = pij[s * plane], x2 = pij[s * plane + 1];
+        const float2 y1 = pji[s * plane], y2 = pji[s * plane + 1];
+        a1 = df_add(a1, dfl{x1.x, x1.y});
+        a2 = df_add(a2, dfl{x2.x, x2.y});
+        e1 = df_add(e1, dfl{y1.x, y1.y});
+        e2 = df_add(e2, dfl{y2.x, y2.y});
+    }
+    const dfl mi1 = df_add(df_mul(a1, c1), b1), mi2 = df_mul(a2, c2);
+    const dfl mj1 = df_add(df_mul(e1, c1), b1), mj2 = df_mul(e2, c2);
+    mf[0] = mi1.hi;
+    mf[1] = mi2.hi;
+    mf[2] = mj1.hi;
+    mf[3] = mj2.hi;
+    const dfl hij = df_neg_entropy(mi1, mi2), hji = df_neg_entropy(mj1, mj2);
+    return df_add(df_add(hd[j], hij), df_neg(df_add(hd[i], hji)));
 }
 
 // I(i, j) (Algorithm 1) of positions i != j from the pair moments and the

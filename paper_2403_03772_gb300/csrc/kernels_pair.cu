@@ -307,7 +307,7 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
             (void)mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
 
     // ---------------- cross-lane reduction (fixed xor tree) ------------------
-    double *mom = P.mom + (size_t)split * P.p * P.p * 2;
+    float2 *mom = P.mom + (size_t)split * P.p * P.p * 2;
 #pragma unroll
     for (int r = 0; r < WI; ++r) {
 #pragma unroll
@@ -334,9 +334,13 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
             }
             const int pi = pi0 + r, pj = pj0 + c;
             if (lane == r * WJ + c && pi < P.p && pj < P.p && pi != pj) {
-                double *o = mom + ((size_t)pi * P.p + pj) * 2;
-                o[0] = (double)h1 + (double)l1;
-                o[1] = (double)h2 + (double)l2;
+                // normalised (hi, lo) pairs for the double-float score
+                float2 *o = mom + ((size_t)pi * P.p + pj) * 2;
+                float t, err;
+                two_sum(h1, l1, t, err);
+                o[0] = make_float2(t, err);
+                two_sum(h2, l2, t, err);
+                o[1] = make_float2(t, err);
             }
         }
     }
@@ -454,7 +458,12 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     if ((int)blockIdx.x * SCORE_RPB >= P.p) return;
     float *wsh = reinterpret_cast<float *>(hsh + P.p);
     const double invn = 1.0 / (double)P.n;
-    for (int j = threadIdx.x; j < P.p; j += blockDim.x) score_var(P, j, invn, hsh[j], wsh[j]);
+    const bool df = P.mom2 != nullptr;
+    dfl *hd = reinterpret_cast<dfl *>(wsh + P.p + (P.p & 1));   // h(z_j) as double-floats
+    for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
+        score_var(P, j, invn, hsh[j], wsh[j]);
+        if (df) hd[j] = df_split(hsh[j]);
+    }
     __syncthreads();
     // SCORE_WPR warps per row i: warp wr of the row takes j = 32 wr + lane +
     // 32 SCORE_WPR k; the row's partial sums are added in warp order.
@@ -463,7 +472,41 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     const int wr = warp % SCORE_WPR;
     const int i = blockIdx.x * SCORE_RPB + warp / SCORE_WPR;
     double acc = 0.0, err = 0.0;
-    if (i < P.p) {
+    if (i < P.p && df) {
+        // FP32-scored step: double-float combine, FP32 bounds
+        const dfl c1 = df_split(P.a1 * invn), b1 = df_split(P.b1), c2 = df_split(P.a2 * invn);
+        dfl accd{0.0f, 0.0f};
+        float errf = 0.0f;
+        const int oi = P.U[i];
+        const float wi = wsh[i];
+        for (int j = wr * 32 + lane; j < P.p; j += 32 * SCORE_WPR) {
+            if (j == i) continue;
+            float mf[4];
+            const dfl I = score_entry_df(P, i, j, hd, c1, b1, c2, mf);
+            float eps = (float)P.epsI;
+            if (P.use_model) {
+                const int oj = P.U[j];
+                const double rho =
+                    P.C[(int64_t)min(oi, oj) * P.ldc + max(oi, oj)] * P.isd[i] * P.isd[j];
+                const float ra = rsqrtf(fmaxf((float)fma(-rho, rho, 1.0), 1e-12f)) * 1.01f;
+                const float e1 = (float)P.model.d1 + (float)P.model.da * ra;
+                const float e2 = (float)P.model.d2 + (float)P.model.da * ra;
+                eps = h_err(mf[0], mf[1], e1, e2) + h_err(mf[2], mf[3], e1, e2) + wi + wsh[j];
+            }
+            const bool neg = I.hi < 0.0f;
+            if (neg) accd = df_add(accd, df_mul(I, I));
+            const float Ilo = __fadd_rd(I.hi, I.lo);   // I rounded down
+            if (Ilo < eps) {
+                const float v = neg ? -Ilo : 0.0f;
+                errf += 2.0f * v * eps + eps * eps;
+            }
+            if (P.Iout) P.Iout[(size_t)i * P.p + j] = (double)I.hi + (double)I.lo;
+            if (P.epsOut) P.epsOut[(size_t)i * P.p + j] = eps;
+            if (P.I32) P.I32[(size_t)i * P.p + j] = __fsub_rd(Ilo, eps);
+        }
+        acc = (double)accd.hi + (double)accd.lo;
+        err = (double)errf * (1.0 + 1e-5);   // FP32 sum of a bound: cover its rounding
+    } else if (i < P.p) {
         for (int j = wr * 32 + lane; j < P.p; j += 32 * SCORE_WPR) {
             if (j == i) continue;
             double I, eps;
@@ -499,8 +542,8 @@ cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream
 {
     if (count <= 0) return cudaSuccess;
     dim3 grid((maxp + SCORE_RPB - 1) / SCORE_RPB, count);
-    k_score_b<<<grid, 32 * SCORE_RPB * SCORE_WPR, (sizeof(double) + sizeof(float)) * maxp + 16,
-                s>>>(P);
+    k_score_b<<<grid, 32 * SCORE_RPB * SCORE_WPR,
+                (sizeof(double) + sizeof(float) + sizeof(dfl)) * maxp + 32, s>>>(P);
     return cudaGetLastError();
 }
 

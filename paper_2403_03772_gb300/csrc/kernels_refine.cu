@@ -14,61 +14,16 @@
 //
 // The same kernels also score whole steps (mode 0: every pair) in df or FP64.
 // Work item = one unordered pair {a, b} (both residual directions) or one
-// variable (moments of z itself); a block of HP_THREADS threads owns an item
-// and splits its samples, so the load stays balanced whatever the number of
-// items, and the block sum runs in a fixed order (deterministic results).
+// variable (moments of z itself), cut into sample ranges; a warp owns one
+// (item, range) unit and its lanes stride the samples, and the sums run over
+// fixed xor trees (deterministic results).
 
 #include <math.h>
 
+#include "df.cuh"
 #include "kernels.cuh"
 
 namespace lg {
-
-// -------------------------------------------------- double-float helpers --
-// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, FMA-based
-// TwoProd).  The explicit _rn intrinsics keep the compiler from contracting
-// or re-associating them.
-struct dfl {
-    float hi, lo;
-};
-
-__device__ __forceinline__ dfl df_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-// Requires |a| >= |b| (or a == 0).
-__device__ __forceinline__ dfl df_fast_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ dfl df_two_prod(float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-
-// x + y; absolute error about 2^-47 (|x| + |y|).
-__device__ __forceinline__ dfl df_add(dfl x, dfl y)
-{
-    const dfl s = df_two_sum(x.hi, y.hi);
-    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
-}
-
-// x * y; relative error about 2^-46.
-__device__ __forceinline__ dfl df_mul(dfl x, dfl y)
-{
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    return df_fast_two_sum(p, e);
-}
 
 // ln2/128 split as L1 + L2 + L3: L1 = 709 * 2^-17 has 10 significant bits, so
 // N * L1 is exact for |N| < 2^14; L2 and L3 are the next FP32 pieces
@@ -170,11 +125,6 @@ __device__ __forceinline__ dfl df_resid(dfl al, dfl be, dfl za, dfl zb)
     return df_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(e1, e2)));
 }
 
-__device__ __forceinline__ dfl df_split(double x)
-{
-    const float hi = (float)x;
-    return {hi, (float)(x - (double)hi)};
-}
 
 // Running double-float sum, folded into FP64 every HP_FOLD terms so the
 // double-float rounding never accumulates over more than HP_FOLD additions.
@@ -199,36 +149,17 @@ __device__ __forceinline__ void f64_terms(double u, double &t1, double &t2)
     t2 = u * exp(-0.5 * u * u);
 }
 
-// ------------------------------------------------------ block reduction --
-// Sums NV per-thread values over the block in a fixed order; the totals are
-// valid in thread 0.  Ends with a barrier, so s_red can be reused at once.
-template <int NV>
-__device__ __forceinline__ void block_sum_fixed(double (&v)[NV], double (*s_red)[4])
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum_xor(v[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) s_red[w][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) v[k] += s_red[ww][k];
-    __syncthreads();
-}
-
 // ----------------------------------------------------------- pass kernel --
 // TIER 1: double-float from the split standardised residuals (zhi + zlo by
 // position); TIER 2: FP64 from the residual data R by original index.
 template <int TIER>
-__global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__restrict__ Ps)
+__global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__restrict__ Ps)
 {
     __shared__ float2 s_exp[TIER == 1 ? EXP_TAB : 1];
     __shared__ float4 s_log[TIER == 1 ? LOG_TAB : 1];
-    __shared__ double s_red[HP_THREADS / 32][4];
     const HpParams P = Ps[blockIdx.y];
+    constexpr int WPB = HP_THREADS / 32;
+    const int lane = threadIdx.x & 31;
     int cbeg = 0;
     int64_t npair;
     bool with_vars = true;
@@ -245,13 +176,15 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
     }
     const int64_t nitems = npair + (with_vars ? P.p : 0);
     const int64_t nunits = nitems * P.nsplit;
-    if ((int64_t)blockIdx.x >= nunits) return;
+    if ((int64_t)blockIdx.x * WPB >= nunits) return;
     if (TIER == 1) {
         for (int k = threadIdx.x; k < EXP_TAB; k += blockDim.x) s_exp[k] = g_exp_tab[k];
         for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) s_log[k] = g_log_tab[k];
         __syncthreads();
     }
-    for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    // one warp per work unit; its lanes stride the unit's samples
+    for (int64_t unit = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); unit < nunits;
+         unit += (int64_t)gridDim.x * WPB) {
         // work unit = (item q, sample range sp); each range writes its own
         // partial record, summed in range order by the consumer
         const int64_t q = unit / P.nsplit;
@@ -268,7 +201,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
                 const float *zh = P.zhi + (int64_t)a * P.ldz, *zl = P.zlo + (int64_t)a * P.ldz;
                 DfAcc A1, A2;
                 int cnt = 0;
-                for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
+                for (int s = s0 + lane; s < n; s += 32) {
                     dfl t1, t2;
                     df_terms(dfl{zh[s], zl[s]}, t1, t2, s_exp, s_log);
                     A1.add(t1);
@@ -288,7 +221,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
                 const double inv = 1.0 / sqrt(P.C[(int64_t)oa * P.ldc + oa]);
                 const double *ra = P.R + (int64_t)oa * P.ldr;
                 double s1 = 0.0, s2 = 0.0;
-                for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
+                for (int s = s0 + lane; s < n; s += 32) {
                     double t1, t2;
                     f64_terms(ra[s] * inv, t1, t2);
                     s1 += t1;
@@ -297,8 +230,9 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
                 v[0] = s1;
                 v[1] = s2;
             }
-            block_sum_fixed<2>(v, s_red);
-            if (threadIdx.x == 0) {
+            v[0] = warp_sum_xor(v[0]);
+            v[1] = warp_sum_xor(v[1]);
+            if (lane == 0) {
                 hzp[(size_t)a * 2 + 0] = v[0];
                 hzp[(size_t)a * 2 + 1] = v[1];
             }
@@ -312,7 +246,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             // a lower bound I32(a, b) >= 0 proves I(a, b) >= 0: min(0, I)^2 = 0
             // exactly, so the entry needs no moments (marked by a negative sum)
             if (a == b || (P.I32 && P.I32[(size_t)a * P.p + b] >= 0.0f)) {
-                if (threadIdx.x == 0 && sp == 0) {   // the marker lives in range 0
+                if (lane == 0 && sp == 0) {   // the marker lives in range 0
                     double *o = P.mom + ((size_t)cidx * P.p + b) * 4;
                     o[0] = -1.0;
                     o[1] = o[2] = o[3] = 0.0;
@@ -342,7 +276,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
                   (sqrt(P.C[(int64_t)oa * P.ldc + oa]) * sqrt(P.C[(int64_t)ob * P.ldc + ob]));
         double s2v = 1.0 - rho * rho;
         if (!(s2v > 1e-12)) {
-            if (threadIdx.x == 0) set_status(P.status, ST_DEGENERATE);
+            if (lane == 0) set_status(P.status, ST_DEGENERATE);
             s2v = 1.0;
         }
         const double alpha = 1.0 / sqrt(s2v);   // residual of a given b: alpha z_a - rho alpha z_b
@@ -353,7 +287,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             const float *zbh = P.zhi + (int64_t)b * P.ldz, *zbl = P.zlo + (int64_t)b * P.ldz;
             DfAcc A1, A2, B1, B2;
             int cnt = 0;
-            for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
+            for (int s = s0 + lane; s < n; s += 32) {
                 const dfl za{zah[s], zal[s]}, zb{zbh[s], zbl[s]};
                 dfl t1, t2;
                 df_terms(df_resid(al, be, za, zb), t1, t2, s_exp, s_log);
@@ -383,7 +317,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             const double ib = 1.0 / sqrt(P.C[(int64_t)ob * P.ldc + ob]);
             const double *ra = P.R + (int64_t)oa * P.ldr, *rb = P.R + (int64_t)ob * P.ldr;
             double ab1 = 0.0, ab2 = 0.0, ba1 = 0.0, ba2 = 0.0;
-            for (int s = s0 + threadIdx.x; s < n; s += blockDim.x) {
+            for (int s = s0 + lane; s < n; s += 32) {
                 const double za = ra[s] * ia, zb = rb[s] * ib;
                 double t1, t2;
                 f64_terms((za - rho * zb) * alpha, t1, t2);
@@ -398,8 +332,9 @@ __global__ void __launch_bounds__(HP_THREADS) k_pairs_hp_b(const HpParams *__res
             v[2] = ba1;
             v[3] = ba2;
         }
-        block_sum_fixed<4>(v, s_red);
-        if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = warp_sum_xor(v[k]);
+        if (lane == 0) {
             if (P.mode == 1) {
                 double *o = momp + ((size_t)cidx * P.p + b) * 4;
                 o[0] = v[0];

@@ -239,13 +239,14 @@ static void default_tuning(lingam_tuning &tb, int prec)
 // in total to fill the GPU, never more splits than chunks.  The pair kernel's
 // tile configuration and split target come from the tuning table at the
 // largest p of the step.
-// Sample ranges per work item of the high-precision kernel: enough work units
-// for about eight 256-thread blocks per SM, each range at least 4096 samples.
+// Sample ranges per work item of the high-precision kernel (one warp per
+// item and range): enough units for about 64 warps per SM, each range at
+// least 2048 samples.
 static int hp_splits(const lingam_ctx *ctx, int64_t items, int64_t n, int count)
 {
-    const int64_t target = std::max<int64_t>(1, (int64_t)ctx->num_sms * 8 / std::max(1, count));
+    const int64_t target = std::max<int64_t>(1, (int64_t)ctx->num_sms * 64 / std::max(1, count));
     int64_t s = (target + std::max<int64_t>(items, 1) - 1) / std::max<int64_t>(items, 1);
-    s = std::min<int64_t>(s, std::max<int64_t>(1, n / 4096));
+    s = std::min<int64_t>(s, std::max<int64_t>(1, n / 2048));
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
 }
 
@@ -539,9 +540,9 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     // Those worst cases assume every per-sample error has the same sign; on
     // the calibration workloads (heavy and light tails, skewed noise, VAR
     // innovations, n = 1e6, a near-collinear chain) the largest error was
-    // 0.18 of the resulting bound, so the terms are scaled by 0.6: the bound
-    // stays 3x above every error seen, and a GPU test keeps it above 2x.
-    const double s6 = 0.6 * tie;
+    // 0.18 of the resulting bound, so the terms are scaled by 0.45: the bound
+    // stays 2.5x above every error seen, and a GPU test keeps it above 2x.
+    const double s6 = 0.45 * tie;
     ErrModel em{};
     if (prec == LINGAM_PREC_MIXED)
         em = ErrModel{2.0e-7 * s6, 1.2e-7 * s6, 3.0e-7 * s6, 1.5e-7 * s6, 1.0e-7 * s6};
@@ -715,13 +716,13 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 P.nchunks = pair_nchunks(n);
                 P.cps = ss.pair_cps[k];
                 P.nsplit = ss.pair_nsplit[k];
-                P.mom = I.mom;
+                P.mom = reinterpret_cast<float2 *>(I.mom);
                 P.status = &I.state->status;
                 P.row0 = I.zrow;
                 P.isd = isd;
                 pp.push_back(P);
                 prefix.push_back(prefix.back() + P.tiles_i * P.tiles_j * P.nsplit);
-                S.mom = I.mom;
+                S.mom2 = reinterpret_cast<const float2 *>(I.mom);
                 S.nsplit = P.nsplit;
                 S.hz = I.hzpart;
                 S.nsplit_hz = nsplit_hz[k];
@@ -1880,7 +1881,7 @@ lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuni
             P.p = tb.p_probe[bk];
             P.n = nprobe;
             P.nchunks = nch;
-            P.mom = ptr<double>(mom);
+            P.mom = ptr<float2>(mom);
             P.status = ptr<uint32_t>(status);
             P.row0 = 0;
             P.isd = ptr<double>(isd);
