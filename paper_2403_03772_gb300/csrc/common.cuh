@@ -195,6 +195,20 @@ struct CompSum {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Instance of a flattened batched grid: prefix[k] is the first block of
+// instance k (prefix has count + 1 entries, ascending); returns the largest
+// k with prefix[k] <= b.
+__device__ __forceinline__ int find_instance(const int *prefix, int count, int b)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Block-wide sum in a fixed order (warp xor trees, then warp 0 over the
 // per-warp totals); the result is valid in warp 0.
 __device__ __forceinline__ double block_sum(double v, double *sh)

@@ -254,7 +254,6 @@ struct RegressParams {
     double *R;            // FP64 residual data [d][ldr], updated in place
     int64_t ldr;
     float *z;             // FP32 standardised residuals [d][ldz], compacted by position
-    float *zlo;           // optional: z_exact - z as FP32 (double-float low part)
     int64_t ldz;
     const double *C;
     int64_t ldc;
@@ -271,6 +270,20 @@ struct RegressParams {
     int64_t ldl;
     uint32_t *status;
     double *isd_out;      // [p'] 1 / sqrt(variance) of the next step's positions
+};
+
+// Low parts of the standardised columns (k_zlo_b): z = zhi + zlo.
+struct ZloParams {
+    const double *R;      // FP64 residual data [d][ldr] by original index
+    int64_t ldr;
+    const float *zhi;     // [p][ldz] by position
+    float *zlo;           // out [p][ldz]
+    int64_t ldz;
+    const double *isd;    // [p] 1 / sqrt(C_ii) by position
+    const int32_t *U;
+    int p, n;
+    const DevState *state;
+    int always;           // 1: every pair scored in double-float at this step
 };
 
 struct GramParams {
@@ -315,9 +328,14 @@ cudaError_t launch_gram_f64(const double *R, int64_t ldr, int n, int d, double *
 cudaError_t launch_gram_b(const GramParams *P, int count, int maxd, int maxksplit, cudaStream_t s);
 int gram_ksplit(int n, int d, int num_sms);
 cudaError_t launch_iota_b(const IotaParams *P, int count, int maxd, cudaStream_t s);
-cudaError_t launch_regress_b(const RegressParams *P, int count, bool init, int maxcols,
-                             int maxsplit, cudaStream_t s);
-cudaError_t launch_downdate_b(const DowndateParams *P, int count, int maxp, cudaStream_t s);
+// Flattened batched launches: prefix[k] = first block of instance k (count + 1
+// entries); the *_blocks functions give an instance's block count.
+int regress_blocks(int cols, int n, int sps);
+cudaError_t launch_regress_b(const RegressParams *P, const int *prefix, int count, bool init,
+                             int total_blocks, cudaStream_t s);
+int downdate_blocks(int p);
+cudaError_t launch_downdate_b(const DowndateParams *P, const int *prefix, int count,
+                              int total_blocks, cudaStream_t s);
 cudaError_t launch_finish_b(const FinishParams *P, int count, cudaStream_t s);
 
 cudaError_t pair_kernel_setup();
@@ -338,10 +356,11 @@ inline void pair_split(int64_t tiles, int64_t target, int nchunks, int *cps, int
     *cps = (nchunks + ns - 1) / ns;
     *nsplit = (nchunks + *cps - 1) / *cps;
 }
-cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks_per_inst,
-                              cudaStream_t s);
+cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks, cudaStream_t s);
 cudaError_t df_tables_setup();
-cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream_t s);
+int score_blocks(int p);
+cudaError_t launch_score_b(const ScoreParams *P, const int *prefix, int count, int total_blocks,
+                           int maxp, cudaStream_t s);
 cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s);
 cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp,
                                    cudaStream_t s);
@@ -363,6 +382,7 @@ cudaError_t launch_var_transform(const double *B0, const double *M, int lags, in
                                  cudaStream_t s);
 cudaError_t launch_iota_plain(int32_t *v, int q, cudaStream_t s);
 cudaError_t launch_fill_nan(double *p, size_t count, cudaStream_t s);
+cudaError_t launch_zlo_b(const ZloParams *P, int count, int blocks, cudaStream_t s);
 cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStream_t s);
 
 // Tensor-core covariance (kernels_gram_tc.cu): slice planes S [6][d_pad][ldk]

@@ -353,13 +353,8 @@ __device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUte
                                               const PairParams *__restrict__ Ps,
                                               const int *__restrict__ prefix, int count)
 {
-    int lo = 0, hi = count - 1;
     const int b = blockIdx.x;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
+    const int lo = find_instance(prefix, count, b);
     const PairParams P = Ps[lo];
     const int local = b - prefix[lo];
     const int tiles = P.tiles_i * P.tiles_j;
@@ -451,11 +446,15 @@ cudaError_t launch_pair_b(int mode, int cfg, const CUtensorMap *tmI, const CUten
 // scored in double-float, else the moment-error model of ErrModel.
 constexpr int SCORE_RPB = 2, SCORE_WPR = 4;   // rows per block, warps per row
 
-__global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restrict__ Ps)
+// One launch covers every instance: prefix[k] is the first block of instance
+// k (ceil(p / SCORE_RPB) blocks each).
+__global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restrict__ Ps,
+                                                   const int *__restrict__ prefix, int count)
 {
     extern __shared__ double hsh[];   // h(z_j), j < p; then their error bounds (float)
-    const ScoreParams P = Ps[blockIdx.y];
-    if ((int)blockIdx.x * SCORE_RPB >= P.p) return;
+    const int inst = find_instance(prefix, count, blockIdx.x);
+    const ScoreParams P = Ps[inst];
+    const int rb = blockIdx.x - prefix[inst];   // row block of the instance
     float *wsh = reinterpret_cast<float *>(hsh + P.p);
     const double invn = 1.0 / (double)P.n;
     const bool df = P.mom2 != nullptr;
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     __shared__ double racc[8], rerr[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wr = warp % SCORE_WPR;
-    const int i = blockIdx.x * SCORE_RPB + warp / SCORE_WPR;
+    const int i = rb * SCORE_RPB + warp / SCORE_WPR;
     double acc = 0.0, err = 0.0;
     if (i < P.p && df) {
         // FP32-scored step: double-float combine, FP32 bounds
@@ -538,12 +537,14 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     }
 }
 
-cudaError_t launch_score_b(const ScoreParams *P, int count, int maxp, cudaStream_t s)
+int score_blocks(int p) { return (p + SCORE_RPB - 1) / SCORE_RPB; }
+
+cudaError_t launch_score_b(const ScoreParams *P, const int *prefix, int count, int total_blocks,
+                           int maxp, cudaStream_t s)
 {
-    if (count <= 0) return cudaSuccess;
-    dim3 grid((maxp + SCORE_RPB - 1) / SCORE_RPB, count);
-    k_score_b<<<grid, 32 * SCORE_RPB * SCORE_WPR,
-                (sizeof(double) + sizeof(float) + sizeof(dfl)) * maxp + 32, s>>>(P);
+    if (count <= 0 || total_blocks <= 0) return cudaSuccess;
+    k_score_b<<<total_blocks, 32 * SCORE_RPB * SCORE_WPR,
+                (sizeof(double) + sizeof(float) + sizeof(dfl)) * maxp + 32, s>>>(P, prefix, count);
     return cudaGetLastError();
 }
 

@@ -306,13 +306,18 @@ cudaError_t launch_iota_b(const IotaParams *P, int count, int maxd, cudaStream_t
 // (accurate FP32 functions, compensated FP32 sums per thread, FP64 block
 // sums).  INIT=true only standardises
 // (first step, no regression).
+// One launch covers every instance: prefix[k] is the first block of instance
+// k, which has (columns x sample splits) blocks.
 template <bool INIT>
-__global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restrict__ Ps)
+__global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restrict__ Ps,
+                                                   const int *__restrict__ prefix, int count)
 {
     __shared__ double sh[32];
-    const RegressParams P = Ps[blockIdx.z];
-    const int col = blockIdx.x;
-    if (col >= (INIT ? P.p : P.p - 1) || (int)blockIdx.y * P.sps >= P.n) return;
+    const int inst = find_instance(prefix, count, blockIdx.x);
+    const RegressParams P = Ps[inst];
+    const int nsp = (P.n + P.sps - 1) / P.sps;
+    const int local = blockIdx.x - prefix[inst];
+    const int col = local / nsp, split = local % nsp;
     int pos = col, m = -1, mpos = -1;
     double coef = 0.0, var;
     if (!INIT) {
@@ -338,8 +343,7 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
     double *ri = P.R + (int64_t)i * P.ldr;
     const double *rm = INIT ? nullptr : P.R + (int64_t)m * P.ldr;
     float *zo = P.z + (int64_t)col * P.ldz;
-    float *zl = P.zlo ? P.zlo + (int64_t)col * P.ldz : nullptr;
-    const int s0 = blockIdx.y * P.sps, s1 = min(P.n, s0 + P.sps);
+    const int s0 = split * P.sps, s1 = min(P.n, s0 + P.sps);
     CompSum a1, a2;
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         double r = ri[s];
@@ -347,10 +351,8 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
             r = r - coef * rm[s];
             ri[s] = r;
         }
-        const double zx = r * isd;
-        const float z = (float)zx;
+        const float z = (float)(r * isd);
         zo[s] = z;
-        if (zl) zl[s] = (float)(zx - (double)z);
         const float az = fabsf(z);
         a1.add(az + log1pf(expf(-2.0f * az)));
         a2.add(z * expf(-0.5f * z * z));
@@ -359,11 +361,11 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
     const double t2 = block_sum(a2.value(), sh);
     if (threadIdx.x == 0) {
         const int np = INIT ? P.p : P.p - 1;
-        double *o = P.hzpart + ((size_t)blockIdx.y * np + col) * 2;
+        double *o = P.hzpart + ((size_t)split * np + col) * 2;
         o[0] = t1;
         o[1] = t2;
-        if (blockIdx.y == 0) P.isd_out[col] = isd;
-        if (!INIT && blockIdx.y == 0) {
+        if (split == 0) P.isd_out[col] = isd;
+        if (!INIT && split == 0) {
             P.Unext[col] = i;
             if (P.lcoef) P.lcoef[(int64_t)i * P.ldl + m] = coef;
             if (col == 0) P.order[P.t] = m;
@@ -371,15 +373,16 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
     }
 }
 
-cudaError_t launch_regress_b(const RegressParams *P, int count, bool init, int maxcols,
-                             int maxsplit, cudaStream_t s)
+int regress_blocks(int cols, int n, int sps) { return cols * ((n + sps - 1) / sps); }
+
+cudaError_t launch_regress_b(const RegressParams *P, const int *prefix, int count, bool init,
+                             int total_blocks, cudaStream_t s)
 {
-    if (count <= 0 || maxcols <= 0) return cudaSuccess;
-    dim3 grid(maxcols, maxsplit, count);
+    if (count <= 0 || total_blocks <= 0) return cudaSuccess;
     if (init)
-        k_regress_b<true><<<grid, 256, 0, s>>>(P);
+        k_regress_b<true><<<total_blocks, 256, 0, s>>>(P, prefix, count);
     else
-        k_regress_b<false><<<grid, 256, 0, s>>>(P);
+        k_regress_b<false><<<total_blocks, 256, 0, s>>>(P, prefix, count);
     return cudaGetLastError();
 }
 
@@ -405,13 +408,47 @@ cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStrea
     return cudaGetLastError();
 }
 
+// Low parts of the standardised columns for the double-float re-score,
+// z_lo = fl32(R_i / sigma_i - z_hi) with the same FP64 product the regress
+// kernel rounded to z_hi; only for steps that re-score (state routed to the
+// double-float tier) or score every pair in double-float (`always`).
+__global__ void k_zlo_b(const ZloParams *__restrict__ Ps, int count)
+{
+    for (int inst = 0; inst < count; ++inst) {
+        const ZloParams &P = Ps[inst];
+        if (!P.always && (P.state->resolved || P.state->tier != 1)) continue;
+        const int64_t total = (int64_t)P.p * P.n;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int a = (int)(e / P.n), s = (int)(e % P.n);
+            const double zx = P.R[(int64_t)P.U[a] * P.ldr + s] * P.isd[a];
+            const int64_t q = (int64_t)a * P.ldz + s;
+            P.zlo[q] = (float)(zx - (double)P.zhi[q]);
+        }
+    }
+}
+
+cudaError_t launch_zlo_b(const ZloParams *P, int count, int blocks, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_zlo_b<<<blocks, 256, 0, s>>>(P, count);
+    return cudaGetLastError();
+}
+
 // Rank-1 downdate of the covariance of the remaining variables (FP64):
 // C_ij <- C_ij - C_im C_jm / C_mm, written symmetric-exact.
-__global__ void k_downdate_b(const DowndateParams *__restrict__ Ps)
+// One launch covers every instance: prefix[k] is the first block of
+// instance k, whose (p - 1)^2 entries take ceil((p-1)/32) x ceil((p-1)/8)
+// blocks of 32 x 8 threads.
+__global__ void k_downdate_b(const DowndateParams *__restrict__ Ps, const int *__restrict__ prefix,
+                             int count)
 {
-    const DowndateParams P = Ps[blockIdx.z];
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int inst = find_instance(prefix, count, blockIdx.x);
+    const DowndateParams P = Ps[inst];
+    const int tx = (P.p - 1 + 31) / 32;
+    const int local = blockIdx.x - prefix[inst];
+    const int r = (local / tx) * blockDim.y + threadIdx.y;
+    const int c = (local % tx) * blockDim.x + threadIdx.x;
     if (r >= P.p - 1 || c >= P.p - 1) return;
     const int mpos = P.state->m_pos;
     const int m = P.U[mpos];
@@ -424,11 +461,13 @@ __global__ void k_downdate_b(const DowndateParams *__restrict__ Ps)
     C[(int64_t)i * ldc + j] -= (cim * cjm) / cmm;
 }
 
-cudaError_t launch_downdate_b(const DowndateParams *P, int count, int maxp, cudaStream_t s)
+int downdate_blocks(int p) { return p < 2 ? 0 : ((p - 1 + 31) / 32) * ((p - 1 + 7) / 8); }
+
+cudaError_t launch_downdate_b(const DowndateParams *P, const int *prefix, int count,
+                              int total_blocks, cudaStream_t s)
 {
-    if (count <= 0 || maxp < 2) return cudaSuccess;
-    dim3 block(32, 8), grid((maxp - 1 + 31) / 32, (maxp - 1 + 7) / 8, count);
-    k_downdate_b<<<grid, block, 0, s>>>(P);
+    if (count <= 0 || total_blocks <= 0) return cudaSuccess;
+    k_downdate_b<<<total_blocks, dim3(32, 8), 0, s>>>(P, prefix, count);
     return cudaGetLastError();
 }
 

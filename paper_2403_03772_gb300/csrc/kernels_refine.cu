@@ -152,13 +152,11 @@ __device__ __forceinline__ void f64_terms(double u, double &t1, double &t2)
 // ----------------------------------------------------------- pass kernel --
 // TIER 1: double-float from the split standardised residuals (zhi + zlo by
 // position); TIER 2: FP64 from the residual data R by original index.
+// The work of one instance, for the global warp index w0 of nw warps.
 template <int TIER>
-__global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__restrict__ Ps)
+__device__ __forceinline__ void hp_instance(const HpParams &P, const float2 *s_exp,
+                                            const float4 *s_log, int64_t w0, int64_t nw)
 {
-    __shared__ float2 s_exp[TIER == 1 ? EXP_TAB : 1];
-    __shared__ float4 s_log[TIER == 1 ? LOG_TAB : 1];
-    const HpParams P = Ps[blockIdx.y];
-    constexpr int WPB = HP_THREADS / 32;
     const int lane = threadIdx.x & 31;
     int cbeg = 0;
     int64_t npair;
@@ -176,15 +174,8 @@ __global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__
     }
     const int64_t nitems = npair + (with_vars ? P.p : 0);
     const int64_t nunits = nitems * P.nsplit;
-    if ((int64_t)blockIdx.x * WPB >= nunits) return;
-    if (TIER == 1) {
-        for (int k = threadIdx.x; k < EXP_TAB; k += blockDim.x) s_exp[k] = g_exp_tab[k];
-        for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) s_log[k] = g_log_tab[k];
-        __syncthreads();
-    }
     // one warp per work unit; its lanes stride the unit's samples
-    for (int64_t unit = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); unit < nunits;
-         unit += (int64_t)gridDim.x * WPB) {
+    for (int64_t unit = w0; unit < nunits; unit += nw) {
         // work unit = (item q, sample range sp); each range writes its own
         // partial record, summed in range order by the consumer
         const int64_t q = unit / P.nsplit;
@@ -353,15 +344,32 @@ __global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__
     }
 }
 
-cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks_per_inst,
-                              cudaStream_t s)
+// Every warp of the grid works on every instance in turn, so the whole GPU
+// serves whichever instances have work (in a batch usually a few).
+template <int TIER>
+__global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__restrict__ Ps,
+                                                             int count)
+{
+    __shared__ float2 s_exp[TIER == 1 ? EXP_TAB : 1];
+    __shared__ float4 s_log[TIER == 1 ? LOG_TAB : 1];
+    if (TIER == 1) {
+        for (int k = threadIdx.x; k < EXP_TAB; k += blockDim.x) s_exp[k] = g_exp_tab[k];
+        for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) s_log[k] = g_log_tab[k];
+        __syncthreads();
+    }
+    constexpr int WPB = HP_THREADS / 32;
+    const int64_t w0 = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * WPB;
+    for (int inst = 0; inst < count; ++inst) hp_instance<TIER>(Ps[inst], s_exp, s_log, w0, nw);
+}
+
+cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    const dim3 grid(blocks_per_inst, count);
     if (tier == 1)
-        k_pairs_hp_b<1><<<grid, HP_THREADS, 0, s>>>(P);
+        k_pairs_hp_b<1><<<blocks, HP_THREADS, 0, s>>>(P, count);
     else
-        k_pairs_hp_b<2><<<grid, HP_THREADS, 0, s>>>(P);
+        k_pairs_hp_b<2><<<blocks, HP_THREADS, 0, s>>>(P, count);
     return cudaGetLastError();
 }
 

@@ -240,11 +240,12 @@ static void default_tuning(lingam_tuning &tb, int prec)
 // tile configuration and split target come from the tuning table at the
 // largest p of the step.
 // Sample ranges per work item of the high-precision kernel (one warp per
-// item and range): enough units for about 64 warps per SM, each range at
-// least 2048 samples.
+// item and range): enough units for the pass's 24 resident warps per SM,
+// each range at least 2048 samples.
 static int hp_splits(const lingam_ctx *ctx, int64_t items, int64_t n, int count)
 {
-    const int64_t target = std::max<int64_t>(1, (int64_t)ctx->num_sms * 64 / std::max(1, count));
+    (void)count;   // the pass serves instances in turn with the whole grid
+    const int64_t target = (int64_t)ctx->num_sms * 24;   // resident warps of the pass
     int64_t s = (target + std::max<int64_t>(items, 1) - 1) / std::max<int64_t>(items, 1);
     s = std::min<int64_t>(s, std::max<int64_t>(1, n / 2048));
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
@@ -492,6 +493,15 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     return make_tensor_maps(ctx, pl);
 }
 
+// First block of every instance in a flattened batched launch (count + 1
+// entries, the last one the total).
+static std::vector<int> block_prefix(const std::vector<int> &blocks)
+{
+    std::vector<int> pre(1, 0);
+    for (int b : blocks) pre.push_back(pre.back() + b);
+    return pre;
+}
+
 // Parameter arrays of every launch, gathered host-side and uploaded at once.
 struct ParamBlob {
     std::vector<char> bytes;
@@ -507,7 +517,7 @@ struct ParamBlob {
 
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO
 };
 
 // Timing events per ordering step when profiling: before the pair moments,
@@ -599,7 +609,6 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         P.R = I.R;
         P.ldr = I.ldr;
         P.z = zbase + (int64_t)I.zrow * pl.ldz;
-        P.zlo = zlobase ? zlobase + (int64_t)I.zrow * pl.ldz : nullptr;
         P.ldz = pl.ldz;
         P.C = I.C;
         P.ldc = I.d;
@@ -628,11 +637,15 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             nsplit_hz[k] = ss0.reg_nsplit[k];
             maxsplit = std::max(maxsplit, ss0.reg_nsplit[k]);
         }
+        std::vector<int> nb(K);
+        for (int k = 0; k < K; ++k)
+            nb[k] = regress_blocks((int)pl.inst[k].d, (int)pl.inst[k].n, r[k].sps);
+        const std::vector<int> pre = block_prefix(nb);
         Launch lr{K_REG_INIT};
         lr.off = blob.add(r);
+        lr.off2 = blob.add(pre);
         lr.count = K;
-        lr.a = pl.maxd;
-        lr.b = maxsplit;
+        lr.a = pre.back();
         L.push_back(lr);
     }
     if (profile) {
@@ -646,6 +659,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         std::vector<PairParams> pp;
         std::vector<int> prefix(1, 0);
         std::vector<HpParams> fa, fd1, fd2, f64;
+        std::vector<ZloParams> zl_all, zl_cond;   // low parts: every-pair steps / re-scores
         std::vector<ScoreParams> sc;
         std::vector<SelectParams> se;
         std::vector<RefineSelectParams> rd1, rd2, r64;
@@ -693,6 +707,22 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 F.mom_sstride = mode == 0 ? (int64_t)p * p * 2 : (int64_t)I.d * p * 4;
                 return F;
             };
+            if (zlobase) {
+                ZloParams Z{};
+                Z.R = I.R;
+                Z.ldr = I.ldr;
+                Z.zhi = zbase + (int64_t)I.zrow * pl.ldz;
+                Z.zlo = zlobase + (int64_t)I.zrow * pl.ldz;
+                Z.ldz = pl.ldz;
+                Z.isd = isd;
+                Z.U = Uc;
+                Z.p = p;
+                Z.n = n;
+                Z.state = I.state;
+                Z.always = hp ? 1 : 0;
+                if (hp && hp_tier == 1) zl_all.push_back(Z);
+                else if (!hp) zl_cond.push_back(Z);
+            }
             ScoreParams S{};
             if (hp) {
                 fa.push_back(hpp(0, 1, I.mom));
@@ -772,7 +802,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         }
         if (sc.empty()) break;
         const int cnt = (int)sc.size();
-        const int hp_blocks = std::max(1, ctx->num_sms * 8 / cnt);
+        const int hp_blocks = ctx->num_sms * 3;   // resident 256-thread blocks of the pass
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t;
@@ -789,11 +819,18 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             l.c = pmode;
             L.push_back(l);
         }
+        if (!zl_all.empty()) {
+            Launch l{K_ZLO};
+            l.off = blob.add(zl_all);
+            l.count = (int)zl_all.size();
+            l.a = ctx->num_sms * 4;
+            L.push_back(l);
+        }
         if (!fa.empty()) {
             Launch l{K_HP_ALL};
             l.off = blob.add(fa);
             l.count = (int)fa.size();
-            l.a = std::max(1, ctx->num_sms * 8 / (int)fa.size());
+            l.a = ctx->num_sms * 3;
             l.c = step_hp_tier(prec);
             L.push_back(l);
         }
@@ -802,10 +839,20 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             ev.a = EV_PER_STEP * t + 1;
             L.push_back(ev);
         }
+        std::vector<int> nbs, nbr, nbd;
+        for (int q = 0; q < cnt; ++q) {
+            nbs.push_back(score_blocks(sc[q].p));
+            nbr.push_back(regress_blocks(rg[q].p - 1, rg[q].n, rg[q].sps));
+            nbd.push_back(downdate_blocks(dd[q].p));
+        }
+        const std::vector<int> pres = block_prefix(nbs), prer = block_prefix(nbr),
+                               pred = block_prefix(nbd);
         Launch ls{K_SCORE};
         ls.off = blob.add(sc);
+        ls.off2 = blob.add(pres);
         ls.count = cnt;
         ls.a = maxp;
+        ls.b = pres.back();
         L.push_back(ls);
         if (stop_after_score0) break;
         Launch lse{K_SELECT};
@@ -818,7 +865,15 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             L.push_back(ev);
         }
         // re-score passes: double-float pass 1 and 2, then FP64; each is a
-        // no-op unless the step's state routes candidates to it
+        // no-op unless the step's state routes candidates to it (as is the
+        // low-part kernel the double-float passes read)
+        if (!zl_cond.empty()) {
+            Launch l{K_ZLO};
+            l.off = blob.add(zl_cond);
+            l.count = (int)zl_cond.size();
+            l.a = ctx->num_sms * 4;
+            L.push_back(l);
+        }
         const std::vector<HpParams> *passes[3] = {&fd1, &fd2, &f64};
         const std::vector<RefineSelectParams> *decides[3] = {&rd1, &rd2, &r64};
         for (int q = 0; q < 3; ++q) {
@@ -842,14 +897,15 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         }
         Launch lr{K_REGRESS};
         lr.off = blob.add(rg);
+        lr.off2 = blob.add(prer);
         lr.count = cnt;
-        lr.a = maxcols;
-        lr.b = maxsplit;
+        lr.a = prer.back();
         L.push_back(lr);
         Launch ld{K_DOWNDATE};
         ld.off = blob.add(dd);
+        ld.off2 = blob.add(pred);
         ld.count = cnt;
-        ld.a = maxp;
+        ld.a = pred.back();
         L.push_back(ld);
         if (profile) {
             Launch ev{K_EVENT};
@@ -883,23 +939,31 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         case K_GRAM: e = launch_gram_b((const GramParams *)P, l.count, l.a, l.b, s); ++nodes; break;
         case K_IOTA: e = launch_iota_b((const IotaParams *)P, l.count, l.a, s); break;
         case K_REG_INIT:
-            e = launch_regress_b((const RegressParams *)P, l.count, true, l.a, l.b, s);
+            e = launch_regress_b((const RegressParams *)P, (const int *)(pb + l.off2), l.count,
+                                 true, l.a, s);
             break;
         case K_PAIR:
             e = launch_pair_b(l.c, l.b, &pl.tmI[l.b], &pl.tmJ[l.b], (const PairParams *)P,
                               (const int *)(pb + l.off2), l.count, l.a, s);
             break;
         case K_HP_ALL: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
-        case K_SCORE: e = launch_score_b((const ScoreParams *)P, l.count, l.a, s); break;
+        case K_SCORE:
+            e = launch_score_b((const ScoreParams *)P, (const int *)(pb + l.off2), l.count, l.b,
+                               l.a, s);
+            break;
         case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
         case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
         case K_REFINE:
             e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
             break;
         case K_REGRESS:
-            e = launch_regress_b((const RegressParams *)P, l.count, false, l.a, l.b, s);
+            e = launch_regress_b((const RegressParams *)P, (const int *)(pb + l.off2), l.count,
+                                 false, l.a, s);
             break;
-        case K_DOWNDATE: e = launch_downdate_b((const DowndateParams *)P, l.count, l.a, s); break;
+        case K_DOWNDATE:
+            e = launch_downdate_b((const DowndateParams *)P, (const int *)(pb + l.off2), l.count,
+                                  l.a, s);
+            break;
         case K_FINISH: e = launch_finish_b((const FinishParams *)P, l.count, s); break;
         case K_EVENT:
             e = cudaEventRecordWithFlags(pl.pev[l.a], s, cudaEventRecordExternal);
@@ -912,6 +976,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             nodes += 2;
             break;
         }
+        case K_ZLO: e = launch_zlo_b((const ZloParams *)P, l.count, l.a, s); break;
         case K_FILL_NAN:
             e = launch_fill_nan(pl.inst[l.c].hist, (size_t)pl.inst[l.c].d * pl.inst[l.c].d, s);
             break;

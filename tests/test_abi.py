@@ -94,3 +94,13 @@ def test_create_reports_errors_without_crashing(lib):
     code = handle.lingam_create(ctypes.byref(h), 0, None)
     assert code != 0 and not h.value
     assert len(handle.lingam_last_error(None)) > 0
+
+
+def test_library_has_no_undefined_internal_symbols(lib):
+    """Every kernel launcher the library calls is defined in it (a missing
+    definition would only show up when the library is loaded on a GPU machine)."""
+    path, _ = lib
+    out = subprocess.run(["nm", "-D", "--undefined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    missing = [line.split()[-1] for line in out.splitlines() if "_ZN2lg" in line]
+    assert not missing, missing
