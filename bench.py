@@ -277,10 +277,12 @@ def run_ours(args, rank, world):
                  for b in insts]
         Wb = sum(gen.residual_samples(b.X.shape[1], b.X.shape[0] if b.rows is None else len(b.rows))
                  for b in insts)
+        btune = None
         with pkg.Context(dev, "mixed", profile=True) as ctx:
             if not args.no_autotune:
-                ctx.autotune(max(int(X.shape[0]) if r is None else len(r) for X, r in batch),
-                             max(int(X.shape[1]) for X, _ in batch))
+                btune = ctx.autotune(max(int(X.shape[0]) if r is None else len(r) for X, r in batch),
+                                     max(int(X.shape[1]) for X, _ in batch),
+                                     instances=len(batch))
             for _ in range(args.warmup):
                 ctx.causal_order_batch(batch)
             torch.cuda.synchronize()
@@ -313,6 +315,8 @@ def run_ours(args, rank, world):
                       "refined_steps": bst["refined_steps"], "graph_nodes": bst["graph_nodes"],
                       "phase_ms": {k: bst[k] for k in ("pair_ms", "score_ms", "refine_ms",
                                                        "regress_ms")},
+                      "tuning": ({k: btune[k] for k in ("p_max", "tile", "ctas_per_sm", "ms")}
+                                 if btune else None),
                       "df_candidates": bst["df_candidates"],
                       "sequential_plain_fp32_ms": seq_ms,
                       "sequential_plain_fp32_value": (Wb / (seq_ms * 1e-3)) if seq_ms else None}

@@ -256,7 +256,7 @@ lingam_status lingam_bootstrap_edge_stats(lingam_ctx *ctx, const double *const *
  * Tile shapes and split schedules of the FP32 pair-moment kernel, by range of
  * the number p of remaining variables.  Bucket b covers
  * p_max[b-1] < p <= p_max[b] (p_max ascending; the last bucket also covers
- * every larger p).  tile[b] indexes the kernel's tile configurations (0..8:
+ * every larger p).  tile[b] indexes the kernel's tile configurations (0..9:
  * warps x pairs per warp, see the library's design notes); ctas_per_sm[b] is
  * the number of CTAs per SM the sample splits aim for; ms[b] the kernel time
  * measured at the probe size p_probe[b] with n_probe samples.  One table per
@@ -276,13 +276,16 @@ typedef struct {
 /*
  * Autotuner: times every tile configuration with three split schedules on
  * synthetic standardised data of n samples (capped at 131072) at probe sizes
- * p = 64, 128, ..., up to min(d, 2048), and keeps the fastest per bucket for
- * the context's current precision form (FP32 or MIXED; other forms return
- * LINGAM_ERR_ARG).  Later calls of that form use the table.  *out (optional)
- * receives it.  Allocates and frees its own scratch; invalidates the cached
- * step graph.
+ * p = 64, 128, ..., up to min(d, 2048), each probe launched as `instances`
+ * copies in one batch (1 for single problems; the batch size for
+ * lingam_causal_order_batch, within 2 GB of scratch), and keeps the fastest
+ * per bucket for the context's current precision form (FP32 or MIXED; other
+ * forms return LINGAM_ERR_ARG).  Later calls of that form use the table.
+ * *out (optional) receives it.  Allocates and frees its own scratch;
+ * invalidates the cached step graph.
  */
-lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuning *out);
+lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, int32_t instances,
+                              lingam_tuning *out);
 
 /* Install a table (for example one saved from an earlier lingam_autotune on
  * the same GPU model) for the form t->precision; checks its entries. */

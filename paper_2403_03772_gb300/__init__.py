@@ -96,7 +96,7 @@ SIGNATURES = {
     "lingam_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "lingam_peak_probe": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "lingam_step_scores_noalloc": (_I32, [_P, _I64, _I64, _I64, _P, _P]),
-    "lingam_autotune": (_I32, [_P, _I64, _I64, ctypes.POINTER(Tuning)]),
+    "lingam_autotune": (_I32, [_P, _I64, _I64, _I32, ctypes.POINTER(Tuning)]),
     "lingam_total_effects": (_I32, [_P, _P, _I64, _P, _P, _I32, _P]),
     "lingam_prune_adjacency": (_I32, [_P, _P, _I64, _I64, _I64, _I32, _P, _D, _I32, _D, _P, _I32,
                                       _P]),
@@ -380,17 +380,18 @@ class Context:
         self._check(self._lib.lingam_get_stats(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_ if k != "reserved"}
 
-    def autotune(self, n: int, d: int, cache: str | None = None) -> dict:
+    def autotune(self, n: int, d: int, cache: str | None = None, instances: int = 1) -> dict:
         """Tile shapes and split schedules of the FP32 pair kernel for problems
-        of n samples and up to d variables, in the context's form.  With
-        ``cache`` (a JSON file) a table saved for the same GPU model, form and
-        sizes is installed instead of re-measuring, and a new one is saved."""
+        of n samples and up to d variables (``instances`` of them per batch),
+        in the context's form.  With ``cache`` (a JSON file) a table saved for
+        the same GPU model, form and sizes is installed instead of
+        re-measuring, and a new one is saved."""
         import json
         key = None
         if cache:
             torch = _torch()
             dev = torch.cuda.get_device_name(0) if torch and torch.cuda.is_available() else "gpu"
-            key = f"{dev}|{self.precision}|n={int(n)}|d={int(d)}"
+            key = f"{dev}|{self.precision}|n={int(n)}|d={int(d)}|k={int(instances)}"
             try:
                 with open(cache) as f:
                     saved = json.load(f)
@@ -401,7 +402,8 @@ class Context:
                 self._check(self._lib.lingam_set_tuning(self._h, ctypes.byref(t)))
                 return saved[key]
         t = Tuning()
-        self._check(self._lib.lingam_autotune(self._h, int(n), int(d), ctypes.byref(t)))
+        self._check(self._lib.lingam_autotune(self._h, int(n), int(d), int(instances),
+                                              ctypes.byref(t)))
         out = t.to_dict()
         if cache:
             try:

@@ -20,21 +20,23 @@ struct PairCfg {
     int wi, wj, wgi, wgj, stages;
     int reg_fast, reg_acc;   // register cap per thread (fast / accurate form)
     int groups;              // groups of 4 samples per lane and iteration (1 or 2)
+    int fold;                // chunks between compensated folds of the FP32 partial sums
     constexpr int ti() const { return wi * wgi; }
     constexpr int tj() const { return wj * wgj; }
     constexpr int warps() const { return wgi * wgj; }
     constexpr int threads() const { return 32 * wgi * wgj; }
 };
 constexpr PairCfg PAIR_CFGS[] = {
-    {4, 4, 2, 4, 4, 248, 128, 1},   // 0: 256 threads, 8 x 16 tile
-    {4, 4, 1, 4, 3, 168, 128, 1},   // 1: 128 threads, 4 x 16 tile
-    {4, 2, 2, 4, 4, 128, 96, 1},    // 2: 256 threads, 8 x 8 tile
-    {2, 4, 2, 4, 4, 128, 96, 1},    // 3: 256 threads, 4 x 16 tile
-    {4, 4, 2, 2, 4, 168, 128, 1},   // 4: 128 threads, 8 x 8 tile
-    {4, 4, 1, 4, 3, 168, 168, 2},   // 5: as 1, 8 samples per lane and iteration
-    {4, 2, 1, 4, 3, 128, 96, 2},    // 6: 128 threads, 4 x 8 tile, 8 samples per lane
-    {4, 2, 2, 4, 4, 128, 96, 2},    // 7: as 2, 8 samples per lane
-    {2, 4, 2, 4, 4, 128, 96, 2},    // 8: as 3, 8 samples per lane
+    {4, 4, 2, 4, 4, 248, 128, 1, 4},   // 0: 256 threads, 8 x 16 tile
+    {4, 4, 1, 4, 3, 168, 128, 1, 4},   // 1: 128 threads, 4 x 16 tile
+    {4, 2, 2, 4, 4, 128, 96, 1, 4},    // 2: 256 threads, 8 x 8 tile
+    {2, 4, 2, 4, 4, 128, 96, 1, 4},    // 3: 256 threads, 4 x 16 tile
+    {4, 4, 2, 2, 4, 168, 128, 1, 4},   // 4: 128 threads, 8 x 8 tile
+    {4, 4, 1, 4, 3, 168, 168, 2, 4},   // 5: as 1, 8 samples per lane and iteration
+    {4, 2, 1, 4, 3, 128, 96, 2, 4},    // 6: 128 threads, 4 x 8 tile, 8 samples per lane
+    {4, 2, 2, 4, 4, 128, 96, 2, 4},    // 7: as 2, 8 samples per lane
+    {2, 4, 2, 4, 4, 128, 96, 2, 4},    // 8: as 3, 8 samples per lane
+    {4, 2, 1, 4, 3, 128, 96, 2, 8},    // 9: as 6, folds every 8 chunks
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk

@@ -249,7 +249,7 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     for (int r = 0; r < WI; ++r)
 #pragma unroll
         for (int c = 0; c < WJ; ++c) a1[r][c] = a2[r][c] = 0.0f;
-    constexpr int FOLD = 4;
+    constexpr int FOLD = G.fold;
 
     for (int k = 0; k < nck; ++k) {
         if (threadIdx.x == 0 && k + STAGES - 1 < nck && !*abort_flag) {
@@ -389,8 +389,8 @@ struct PairTable {
     static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
-using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8>;
-static_assert(PAIR_NCFG == 9, "PairKernels lists every configuration");
+using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9>;
+static_assert(PAIR_NCFG == 10, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {

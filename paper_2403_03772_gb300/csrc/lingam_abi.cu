@@ -240,12 +240,12 @@ static void default_tuning(lingam_tuning &tb, int prec)
 // tile configuration and split target come from the tuning table at the
 // largest p of the step.
 // Sample ranges per work item of the high-precision kernel (one warp per
-// item and range): enough units for the pass's 24 resident warps per SM,
-// each range at least 2048 samples.
+// item and range): about 64 units per SM (many items are skipped at run
+// time, and units differ in length), each range at least 2048 samples.
 static int hp_splits(const lingam_ctx *ctx, int64_t items, int64_t n, int count)
 {
     (void)count;   // the pass serves instances in turn with the whole grid
-    const int64_t target = (int64_t)ctx->num_sms * 24;   // resident warps of the pass
+    const int64_t target = (int64_t)ctx->num_sms * 64;
     int64_t s = (target + std::max<int64_t>(items, 1) - 1) / std::max<int64_t>(items, 1);
     s = std::min<int64_t>(s, std::max<int64_t>(1, n / 2048));
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
@@ -802,7 +802,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         }
         if (sc.empty()) break;
         const int cnt = (int)sc.size();
-        const int hp_blocks = ctx->num_sms * 3;   // resident 256-thread blocks of the pass
+        const int hp_blocks = ctx->num_sms * 8;   // 64 warps per SM, 24 resident
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t;
@@ -830,7 +830,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             Launch l{K_HP_ALL};
             l.off = blob.add(fa);
             l.count = (int)fa.size();
-            l.a = ctx->num_sms * 3;
+            l.a = ctx->num_sms * 8;
             l.c = step_hp_tier(prec);
             L.push_back(l);
         }
@@ -1831,23 +1831,34 @@ lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam
 
 // Times one pair-kernel launch of configuration cfg on the synthetic columns
 // (minimum of three runs after a warm-up).
+// `copies` identical instances in one launch (a batch of that many problems),
+// each writing its own moments; the splits aim at the batch's total tiles as
+// the plan's do.
 static lingam_status time_pair(lingam_ctx *ctx, int mode, int cfg, const CUtensorMap *tI,
-                               const CUtensorMap *tJ, PairParams P, PairParams *dP, int *dprefix,
+                               const CUtensorMap *tJ, PairParams P, int copies,
+                               int64_t mom_per_copy, PairParams *dP, int *dprefix,
                                int ctas_target, cudaEvent_t a, cudaEvent_t b, double *ms_out)
 {
     const int tiles = pair_tiles(P.p, cfg);
     P.tiles_i = (P.p + PAIR_CFGS[cfg].ti() - 1) / PAIR_CFGS[cfg].ti();
     P.tiles_j = (P.p + PAIR_CFGS[cfg].tj() - 1) / PAIR_CFGS[cfg].tj();
-    pair_split(tiles, (int64_t)ctx->num_sms * ctas_target, P.nchunks, &P.cps, &P.nsplit);
-    const int total = tiles * P.nsplit;
-    const int prefix[2] = {0, total};
-    CK(cudaMemcpyAsync(dP, &P, sizeof(PairParams), cudaMemcpyHostToDevice, ctx->s));
-    CK(cudaMemcpyAsync(dprefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice, ctx->s));
-    CK(launch_pair_b(mode, cfg, tI, tJ, dP, dprefix, 1, total, ctx->s));
+    pair_split((int64_t)tiles * copies, (int64_t)ctx->num_sms * ctas_target, P.nchunks, &P.cps,
+               &P.nsplit);
+    std::vector<PairParams> ps(copies, P);
+    std::vector<int> prefix(copies + 1, 0);
+    for (int k = 0; k < copies; ++k) {
+        ps[k].mom = P.mom + (size_t)k * mom_per_copy;
+        prefix[k + 1] = prefix[k] + tiles * P.nsplit;
+    }
+    const int total = prefix[copies];
+    CK(cudaMemcpyAsync(dP, ps.data(), sizeof(PairParams) * copies, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(dprefix, prefix.data(), sizeof(int) * (copies + 1), cudaMemcpyHostToDevice,
+                       ctx->s));
+    CK(launch_pair_b(mode, cfg, tI, tJ, dP, dprefix, copies, total, ctx->s));
     double best = 1e30;
     for (int r = 0; r < 3; ++r) {
         CK(cudaEventRecord(a, ctx->s));
-        CK(launch_pair_b(mode, cfg, tI, tJ, dP, dprefix, 1, total, ctx->s));
+        CK(launch_pair_b(mode, cfg, tI, tJ, dP, dprefix, copies, total, ctx->s));
         CK(cudaEventRecord(b, ctx->s));
         CK(cudaEventSynchronize(b));
         float ms = 0;
@@ -1858,7 +1869,8 @@ static lingam_status time_pair(lingam_ctx *ctx, int mode, int cfg, const CUtenso
     return LINGAM_OK;
 }
 
-lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuning *out)
+lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, int32_t instances,
+                              lingam_tuning *out)
 {
     if (!ctx) return LINGAM_ERR_ARG;
     ctx->err.clear();
@@ -1866,6 +1878,7 @@ lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuni
     if (prec != LINGAM_PREC_FP32 && prec != LINGAM_PREC_MIXED)
         return fail(ctx, LINGAM_ERR_ARG, "autotune needs the FP32 or MIXED form");
     if (n < 2 || d < 2 || d > 6000) return fail(ctx, LINGAM_ERR_ARG, "need n >= 2, 2 <= d <= 6000");
+    if (instances < 1) return fail(ctx, LINGAM_ERR_ARG, "need instances >= 1");
     CK(cudaSetDevice(ctx->device));
     destroy_plan(ctx->plan);
     const int mode = prec == LINGAM_PREC_MIXED ? PAIR_FAST : PAIR_ACCURATE;
@@ -1886,16 +1899,26 @@ lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuni
     pmax = std::max(pmax, 2);
     const int64_t ldz = roundup(std::max<int64_t>(nprobe, PAIR_S), 64);
     const int nch = pair_nchunks(nprobe);
-    int64_t mom_elems = 0;
-    for (int b = 0; b < tb.count; ++b)
-        for (int c = 0; c < PAIR_NCFG; ++c)
-            for (int m = 1; m <= 4; m *= 2) {
-                int cps = 1, ns = 1;
-                pair_split(pair_tiles(tb.p_probe[b], c),
-                           (int64_t)ctx->num_sms * pair_ctas_per_sm(mode, c) * m, nch, &cps, &ns);
-                mom_elems = std::max<int64_t>(mom_elems,
-                                              (int64_t)ns * tb.p_probe[b] * tb.p_probe[b] * 2);
-            }
+    // copies of the probe instance per launch: the batch size, within 2 GB of
+    // moment output
+    int copies = 1;
+    int64_t mom_per_copy = 0;
+    for (int cp = std::min(instances, 4096); cp >= 1; cp = (cp > 1 ? std::max(1, cp / 2) : 0)) {
+        int64_t per = 0;
+        for (int b = 0; b < tb.count; ++b)
+            for (int c = 0; c < PAIR_NCFG; ++c)
+                for (int m = 1; m <= 4; m *= 2) {
+                    int cps = 1, ns = 1;
+                    pair_split((int64_t)pair_tiles(tb.p_probe[b], c) * cp,
+                               (int64_t)ctx->num_sms * pair_ctas_per_sm(mode, c) * m, nch, &cps,
+                               &ns);
+                    per = std::max<int64_t>(per, (int64_t)ns * tb.p_probe[b] * tb.p_probe[b] * 2);
+                }
+        copies = cp;
+        mom_per_copy = per;
+        if ((double)per * cp * sizeof(float2) <= 2.0e9 || cp == 1) break;
+    }
+    const int64_t mom_elems = mom_per_copy * copies;
     Buf z, C, U, isd, mom, status, dP, dpre;
     auto cleanup = [&]() {
         release(z);
@@ -1913,10 +1936,10 @@ lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuni
         CK(ensure(C, (size_t)pmax * pmax * 8, true));      // rho = 0 for every pair
         CK(ensure(U, (size_t)pmax * 4));
         CK(ensure(isd, (size_t)pmax * 8));
-        CK(ensure(mom, (size_t)mom_elems * 8));
+        CK(ensure(mom, (size_t)mom_elems * sizeof(float2)));
         CK(ensure(status, 256, true));
-        CK(ensure(dP, sizeof(PairParams)));
-        CK(ensure(dpre, 64));
+        CK(ensure(dP, sizeof(PairParams) * copies));
+        CK(ensure(dpre, sizeof(int) * (copies + 1)));
         CK(launch_fill_test_z(ptr<float>(z), ldz, pmax, nprobe, ctx->s));
         CK(launch_iota_plain(ptr<int32_t>(U), pmax, ctx->s));
         std::vector<double> ones(pmax, 1.0);
@@ -1955,8 +1978,9 @@ lingam_status lingam_autotune(lingam_ctx *ctx, int64_t n, int64_t d, lingam_tuni
                 for (int m = 1; m <= 4; m *= 2) {
                     const int target = pair_ctas_per_sm(mode, c) * m;
                     double ms = 0;
-                    lingam_status s2 = time_pair(ctx, mode, c, &tI[c], &tJ[c], P, ptr<PairParams>(dP),
-                                                 ptr<int>(dpre), target, a, b, &ms);
+                    lingam_status s2 =
+                        time_pair(ctx, mode, c, &tI[c], &tJ[c], P, copies, mom_per_copy,
+                                  ptr<PairParams>(dP), ptr<int>(dpre), target, a, b, &ms);
                     if (s2) return s2;
                     if (ms < best) {
                         best = ms;

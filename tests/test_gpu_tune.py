@@ -9,7 +9,7 @@ from gpu_util import read_golden_order, scores_close
 
 pytestmark = pytest.mark.gpu
 
-N_CFG = 9
+N_CFG = 10
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +63,7 @@ def test_tuned_batch_matches_oracle(torch_cuda):
         X[:, 1:] += 0.5 * X[:, :-1]
         insts.append((X, None))
     with pkg.Context(0, "mixed") as c:
-        c.autotune(1500, 70)
+        c.autotune(1500, 70, instances=3)
         orders = c.causal_order_batch(insts)
     for (X, _), o in zip(insts, orders):
         assert list(o) == list(oracle.causal_order(X))
