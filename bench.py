@@ -204,18 +204,22 @@ def time_form(ctx, X, steps, warmup, flush_buf, torch, rank, world):
 
 
 def run_one_order(args):
-    """One order of the headline workload in the first form, bracketed by
+    """One order of a workload (--workload) in the first form, bracketed by
     cudaProfilerStart/Stop so that a profiler started with
     --profile-from-start off sees exactly one order's launches (after the
     autotuner and a warm-up order)."""
     import torch
     import paper_2403_03772_gb300 as pkg
     torch.cuda.set_device(0)
-    ds = gen.cfg3()
+    ds = {"long_n": lambda: gen.long_n(seed=gen.SEEDS[6]), "cfg2": gen.cfg2,
+          "cfg3": gen.cfg3}[args.workload]()
     X = torch.from_numpy(ds.X).to("cuda:0")
     prec = args.forms[0]
     with pkg.Context(0, prec) as ctx:
-        if prec in ("mixed", "fp32") and not args.no_autotune:
+        if prec in ("mixed", "fp32") and args.tile is not None:
+            ctx.set_tuning({"count": 1, "precision": pkg.PREC[prec], "p_max": [2 ** 31 - 1],
+                            "tile": [args.tile], "ctas_per_sm": [args.ctas]})
+        elif prec in ("mixed", "fp32") and not args.no_autotune:
             ctx.autotune(ds.n, ds.d)
         ctx.causal_order(X)
         torch.cuda.synchronize()
@@ -223,7 +227,11 @@ def run_one_order(args):
         order = ctx.causal_order(X)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        print(json.dumps({"one_order": prec, "graph_nodes": ctx.stats()["graph_nodes"],
+        st = ctx.stats()
+        print(json.dumps({"one_order": prec, "workload": args.workload,
+                          "graph_nodes": st["graph_nodes"],
+                          **{k: st[k] for k in ("refined_steps", "df_candidates",
+                                                "fp64_candidates", "genuine_ties")},
                           "order_head": [int(v) for v in order[:8]]}), flush=True)
     return 0
 
@@ -342,6 +350,8 @@ def run_ours(args, rank, world):
                          k: sum(s[k] for s in lst) / len(lst)
                          for k in ("pair_ms", "score_ms", "refine_ms", "regress_ms")},
                      "df_candidates": lst[-1]["df_candidates"],
+                     "fp64_candidates": lst[-1]["fp64_candidates"],
+                     "genuine_ties": lst[-1]["genuine_ties"],
                      "refined_steps": lst[-1]["refined_steps"],
                      "order_head": [int(v) for v in lorder[:8]]}
         del Xl
@@ -469,6 +479,12 @@ def main():
     ap.add_argument("--no-long-n", dest="long_n", action="store_false")
     ap.add_argument("--one-order", action="store_true",
                     help="run one profiler-bracketed order of the headline workload and exit")
+    ap.add_argument("--workload", choices=["cfg3", "long_n", "cfg2"], default="cfg3",
+                    help="--one-order workload: d=1000, n=1e4 (default), d=100, n=1e6 or "
+                         "d=100, n=5000")
+    ap.add_argument("--tile", type=int, default=None,
+                    help="--one-order: one pair-kernel tile configuration instead of the autotuner")
+    ap.add_argument("--ctas", type=int, default=4, help="--one-order --tile: CTAs per SM")
     ap.add_argument("--batched-sequential", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the untuned pair-kernel tiles (one 8 x 16 configuration)")

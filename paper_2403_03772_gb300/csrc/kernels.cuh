@@ -21,6 +21,7 @@ struct PairCfg {
     int reg_fast, reg_acc;   // register cap per thread (fast / accurate form)
     int groups;              // groups of 4 samples per lane and iteration (1 or 2)
     int fold;                // chunks between compensated folds of the FP32 partial sums
+    int packed;              // fast form: two samples per paired-FP32 instruction
     constexpr int ti() const { return wi * wgi; }
     constexpr int tj() const { return wj * wgj; }
     constexpr int warps() const { return wgi * wgj; }
@@ -37,6 +38,9 @@ constexpr PairCfg PAIR_CFGS[] = {
     {4, 2, 2, 4, 4, 128, 96, 2, 4},    // 7: as 2, 8 samples per lane
     {2, 4, 2, 4, 4, 128, 96, 2, 4},    // 8: as 3, 8 samples per lane
     {4, 2, 1, 4, 3, 128, 96, 2, 8},    // 9: as 6, folds every 8 chunks
+    {4, 2, 1, 4, 3, 128, 96, 2, 8, 1}, // 10: as 9, paired FP32 (f32x2) arithmetic
+    {4, 4, 1, 4, 3, 168, 168, 2, 8, 1},// 11: as 5, paired, folds every 8 chunks
+    {4, 2, 2, 4, 4, 128, 96, 2, 8, 1}, // 12: as 7, paired, folds every 8 chunks
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
@@ -89,6 +93,9 @@ struct HpParams {
     int nsplit;           // sample ranges per work item (partial sums per range)
     int sps;              // samples per range
     int64_t mom_sstride;  // elements between the ranges' moment records
+    int64_t woff;         // warp that takes this instance's first unit: the
+                          // instances of one launch start where the previous
+                          // one's expected units end, so all warps share the work
 };
 
 // Per-entry bound on |I_fp32(i, j) - I(i, j)| (FP32-scored steps).  Each of

@@ -59,7 +59,13 @@ constexpr float FAST_C3 = (float)(LOG2E_D / KSC);
 // sum_s log2(1 + y_s); the second sum is taken as log2 of the product of
 // the 4 G factors (1 + y_s) in (1, 2^(4G)], one MUFU lg2 per 4 G samples (the
 // logarithm of a product is the sum of the logarithms).
-template <int MODE, bool TAIL, int WI, int WJ, int S, int G>
+//
+// Paired form (PK, full chunks of the fast form): samples 2h and 2h + 1 of a
+// lane travel together through the f32x2 multiply / FMA instructions of
+// sm_100-class GPUs (one issue slot for two FP32 results); each lane keeps two
+// interleaved partial sums of u exp(-u^2/2) and two product chains, joined
+// once per pair and iteration.  The MUFU ex2/lg2 work is unchanged.
+template <int MODE, bool TAIL, int WI, int WJ, int S, int G, bool PK>
 __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
                                            const float *__restrict__ cols,
                                            const float (&ca)[WI][WJ], const float (&cb)[WI][WJ],
@@ -97,7 +103,30 @@ __device__ __forceinline__ void pair_chunk(const float *__restrict__ rows,
         for (int r = 0; r < WI; ++r) {
 #pragma unroll
             for (int c = 0; c < WJ; ++c) {
-                if (MODE == PAIR_FAST) {
+                if (MODE == PAIR_FAST && PK && !TAIL) {
+                    const float2 A = make_float2(ca[r][c], ca[r][c]);
+                    const float2 NB = make_float2(-cb[r][c], -cb[r][c]);
+                    const float2 C2 = make_float2(FAST_C2, FAST_C2);
+                    float2 acc = make_float2(a2[r][c], 0.0f), pr = make_float2(1.0f, 1.0f);
+                    float asum = 0.0f;
+#pragma unroll
+                    for (int h = 0; h < V / 2; ++h) {
+                        const float2 zi2 = make_float2(zi[r][2 * h], zi[r][2 * h + 1]);
+                        const float2 zj2 = make_float2(zj[c][2 * h], zj[c][2 * h + 1]);
+                        const float2 u = __ffma2_rn(A, zi2, __fmul2_rn(NB, zj2));
+                        const float2 sq = __fmul2_rn(u, u);
+                        const float2 e = make_float2(ex2_approx(-sq.x), ex2_approx(-sq.y));
+                        acc = __ffma2_rn(u, e, acc);
+                        const float2 q = __fmul2_rn(u, C2);   // C2 < 0: exp(-2|u|) = ex2(-|q|)
+                        const float2 y = make_float2(ex2_approx(-fabsf(q.x)),
+                                                     ex2_approx(-fabsf(q.y)));
+                        pr = h == 0 ? make_float2(1.0f + y.x, 1.0f + y.y) : __ffma2_rn(y, pr, pr);
+                        asum = h == 0 ? fabsf(u.x) + fabsf(u.y)
+                                      : asum + fabsf(u.x) + fabsf(u.y);
+                    }
+                    a2[r][c] = acc.x + acc.y;
+                    a1[r][c] += fmaf(asum, FAST_C3, lg2_approx(pr.x * pr.y));
+                } else if (MODE == PAIR_FAST) {
                     float yv[V], au[V];
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -154,6 +183,7 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     constexpr uint32_t STAGE_FLOATS = (TI + TJ) * S;
     constexpr uint32_t STAGE_BYTES = STAGE_FLOATS * 4;
     constexpr bool COMP = true;   // compensated (hi, lo) folds in both forms
+    constexpr bool PK = G.packed != 0;
 
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -270,9 +300,11 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
         const int valid = min(S, P.n - (c0 + k) * S);
         if (COMP) {
             if (valid == S)
-                pair_chunk<MODE, false, WI, WJ, S, G.groups>(rows, cols, ca, cb, a1, a2, lane, valid);
+                pair_chunk<MODE, false, WI, WJ, S, G.groups, PK>(rows, cols, ca, cb, a1, a2, lane,
+                                                                 valid);
             else
-                pair_chunk<MODE, true, WI, WJ, S, G.groups>(rows, cols, ca, cb, a1, a2, lane, valid);
+                pair_chunk<MODE, true, WI, WJ, S, G.groups, PK>(rows, cols, ca, cb, a1, a2, lane,
+                                                                valid);
             // fold the partial sums of FOLD chunks into (hi, lo) pairs
             if ((k % FOLD) == FOLD - 1 || k == nck - 1) {
 #pragma unroll
@@ -291,9 +323,11 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
             }
         } else {
             if (valid == S)
-                pair_chunk<MODE, false, WI, WJ, S, G.groups>(rows, cols, ca, cb, s1, s2, lane, valid);
+                pair_chunk<MODE, false, WI, WJ, S, G.groups, PK>(rows, cols, ca, cb, s1, s2, lane,
+                                                                 valid);
             else
-                pair_chunk<MODE, true, WI, WJ, S, G.groups>(rows, cols, ca, cb, s1, s2, lane, valid);
+                pair_chunk<MODE, true, WI, WJ, S, G.groups, PK>(rows, cols, ca, cb, s1, s2, lane,
+                                                                valid);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -389,8 +423,8 @@ struct PairTable {
     static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
-using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9>;
-static_assert(PAIR_NCFG == 10, "PairKernels lists every configuration");
+using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12>;
+static_assert(PAIR_NCFG == 13, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {

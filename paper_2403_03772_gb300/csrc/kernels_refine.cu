@@ -175,7 +175,8 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const float2 *s_e
     const int64_t nitems = npair + (with_vars ? P.p : 0);
     const int64_t nunits = nitems * P.nsplit;
     // one warp per work unit; its lanes stride the unit's samples
-    for (int64_t unit = w0; unit < nunits; unit += nw) {
+    const int64_t first = (w0 + nw - P.woff % nw) % nw;
+    for (int64_t unit = first; unit < nunits; unit += nw) {
         // work unit = (item q, sample range sp); each range writes its own
         // partial record, summed in range order by the consumer
         const int64_t q = unit / P.nsplit;

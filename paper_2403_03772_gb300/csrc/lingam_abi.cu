@@ -801,6 +801,18 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             dd.push_back(DowndateParams{I.C, I.d, Uc, p, I.state});
         }
         if (sc.empty()) break;
+        // each instance of a high-precision launch starts at the warp after
+        // the previous one's expected units (every unit of an every-pair
+        // pass, two candidate rows of a re-score pass)
+        for (std::vector<HpParams> *v : {&fa, &fd1, &fd2, &f64}) {
+            int64_t off = 0;
+            for (HpParams &F : *v) {
+                F.woff = off;
+                const int64_t items = F.mode == 0 ? (int64_t)F.p * (F.p - 1) / 2 + F.p
+                                                  : 2 * (int64_t)F.p + (F.with_vars ? F.p : 0);
+                off += items * F.nsplit;
+            }
+        }
         const int cnt = (int)sc.size();
         const int hp_blocks = ctx->num_sms * 8;   // 64 warps per SM, 24 resident
         if (profile) {

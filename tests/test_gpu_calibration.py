@@ -49,9 +49,10 @@ def test_error_bounds_hold_with_margin(datasets, name):
     with pkg.Context(0, "fp64") as c:
         I64, _ = c.step_measures(X32.double())
     off = ~np.eye(X.shape[1], dtype=bool)
-    # the default tiles, and the configuration with the longest plain-FP32
-    # partial sums (folds every 8 chunks)
-    for prec, tile in [("fp32", None), ("mixed", None), ("mixed", 9), ("fp32", 9)]:
+    # the default tiles, the configuration with the longest plain-FP32
+    # partial sums (folds every 8 chunks) and two paired-FP32 (f32x2) ones
+    for prec, tile in [("fp32", None), ("mixed", None), ("mixed", 9), ("fp32", 9),
+                       ("mixed", 10), ("fp32", 12)]:
         with pkg.Context(0, prec) as c:
             if tile is not None:
                 c.set_tuning({"count": 1, "precision": pkg.PREC[prec], "p_max": [2 ** 31 - 1],
