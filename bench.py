@@ -398,16 +398,29 @@ def run_ours(args, rank, world):
                "lg2": lg2 / (sms * l_mhz * 1e6), "fp64_fma": dfma / 2 / (sms * d_mhz * 1e6)}
     run_mhz = clk.get("sm_mhz") or f_mhz
     # fast form per residual-sample: 2 MUFU ex2 (exp(-u^2/2), exp(-2|u|)), one
-    # lg2 per four samples (the log of the product of four 1 + y), and 7.25
-    # FP32-pipe ops (u: FMUL + FFMA; u^2; u e accumulate; |u| scale; product
-    # chain 1; |u| sum 0.75; lg2 combine 0.5).  Three ceilings per SM and
+    # lg2 per 4 x groups samples (the log of the product of the 1 + y), and
+    # 7.25 FP32-pipe lane ops (u: multiply + FMA; u^2; u e accumulate; |u|
+    # scale; product chain; |u| sum; lg2 combine), issued as 7.25 scalar
+    # instructions or, with paired-FP32 tiles, 4.4 (six of the seven as
+    # f32x2).  Weighted by the residual-samples each tuned tile serves in
+    # one order (the pair kernel runs for p > 32).  Three ceilings per SM and
     # clock: MUFU, FP32 pipe, and instruction issue (4 warp-instructions).
-    mix = {"mufu_ex2": 2.0, "mufu_lg2": 0.25, "fp32_pipe": 7.25}
+    tune = forms[head].get("tuning") or {"p_max": [2 ** 31 - 1], "tile": [0]}
+    wsum = lg2w = issw = 0.0
+    for p in range(33, d + 1):
+        b = next((i for i, pm in enumerate(tune["p_max"]) if p <= pm), len(tune["p_max"]) - 1)
+        g = pkg.lingam_pair_tile_info(tune["tile"][b])
+        w = p * (p - 1.0)
+        lg2w += w / (4.0 * g["groups"])
+        issw += w * (4.4 if g["packed"] else 7.25)
+        wsum += w
+    mix = {"mufu_ex2": 2.0, "mufu_lg2": lg2w / wsum, "fp32_pipe": 7.25,
+           "fp32_instructions": issw / wsum}
     hz = sms * run_mhz * 1e6
     mufu_rate = 1.0 / (mix["mufu_ex2"] / (per_clk["ex2"] * hz) +
                        mix["mufu_lg2"] / (per_clk["lg2"] * hz))
     fp32_rate = per_clk["fp32_ops"] * hz / mix["fp32_pipe"]
-    issue_rate = 128.0 * hz / (mix["mufu_ex2"] + mix["mufu_lg2"] + mix["fp32_pipe"])
+    issue_rate = 128.0 * hz / (mix["mufu_ex2"] + mix["mufu_lg2"] + mix["fp32_instructions"])
     peak = min(mufu_rate, fp32_rate, issue_rate)
     f = forms[head]
     achieved = f["pair_units"] / (f["pair_ms"] * 1e-3) if f["pair_ms"] > 0 else 0.0

@@ -256,8 +256,8 @@ lingam_status lingam_bootstrap_edge_stats(lingam_ctx *ctx, const double *const *
  * Tile shapes and split schedules of the FP32 pair-moment kernel, by range of
  * the number p of remaining variables.  Bucket b covers
  * p_max[b-1] < p <= p_max[b] (p_max ascending; the last bucket also covers
- * every larger p).  tile[b] indexes the kernel's tile configurations (0..9:
- * warps x pairs per warp, see the library's design notes); ctas_per_sm[b] is
+ * every larger p).  tile[b] indexes the kernel's tile configurations
+ * (0 .. LINGAM_PAIR_TILES-1, described by lingam_pair_tile_info); ctas_per_sm[b] is
  * the number of CTAs per SM the sample splits aim for; ms[b] the kernel time
  * measured at the probe size p_probe[b] with n_probe samples.  One table per
  * form that runs the FP32 kernel (precision FP32 or MIXED).
@@ -294,6 +294,19 @@ lingam_status lingam_set_tuning(lingam_ctx *ctx, const lingam_tuning *t);
 /* Current table of form `precision` (the untuned default is one bucket,
  * tile 0, 4 CTAs per SM). */
 lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam_tuning *out);
+
+/* Number of pair-kernel tile configurations. */
+#define LINGAM_PAIR_TILES 13
+
+/*
+ * Shape of tile configuration `tile` (no context or GPU needed): out[8] =
+ * {pairs per warp along i, along j, warps along i, along j, TMA ring stages,
+ * groups of 4 samples per lane and iteration (one MUFU lg2 per 4 x groups
+ * samples in the fast form), chunks of 256 samples between compensated
+ * folds, paired-FP32 (f32x2) arithmetic 0/1}.  LINGAM_ERR_ARG for a tile
+ * outside 0 .. LINGAM_PAIR_TILES-1 or a null out.
+ */
+lingam_status lingam_pair_tile_info(int32_t tile, int32_t *out);
 
 /* Counters of the last lingam_causal_order / batch call on ctx. */
 typedef struct {

@@ -105,6 +105,7 @@ SIGNATURES = {
     "lingam_bootstrap_edge_stats": (_I32, [_P, _P, _I32, _I64, _D, _P, _P, _P]),
     "lingam_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "lingam_get_tuning": (_I32, [_P, _I32, ctypes.POINTER(Tuning)]),
+    "lingam_pair_tile_info": (_I32, [_I32, ctypes.POINTER(_I32)]),
 }
 
 
@@ -463,3 +464,19 @@ def lingam_causal_order_batch(ctx: Context, instances, adjacency: bool = False):
 
 def lingam_step_measures(ctx: Context, X):
     return ctx.step_measures(X)
+
+
+PAIR_TILES = 13
+_TILE_KEYS = ("wi", "wj", "wgi", "wgj", "stages", "groups", "fold", "packed")
+
+
+def lingam_pair_tile_info(tile: int) -> dict:
+    """Shape of pair-kernel tile configuration `tile` (no GPU needed): pairs
+    per warp (wi x wj), warps (wgi x wgj), TMA stages, groups of 4 samples per
+    lane and iteration (one lg2 per 4 x groups samples in the fast form),
+    chunks between compensated folds, paired-FP32 arithmetic."""
+    out = (ctypes.c_int32 * 8)()
+    st = load().lingam_pair_tile_info(int(tile), out)
+    if st != 0:
+        raise LingamError(st, f"lingam_pair_tile_info({tile}): no such tile configuration")
+    return dict(zip(_TILE_KEYS, list(out)))

@@ -5,9 +5,10 @@
 // each other the argmax is decided by re-scoring the candidates:
 //
 //   tier 1  double-float ("df"): every quantity carried as an unevaluated sum
-//           hi + lo of two FP32 numbers (about 48 significant bits), with
-//           table-driven exp and log written for it, so the work runs on the
-//           FP32 pipe.  Each I(i, j) carries a bound epsI2 on its error.
+//           hi + lo of two FP32 numbers (about 48 significant bits), the two
+//           moment functions evaluated from tables by Taylor series, so the
+//           work runs on the FP32 pipe.  Each I(i, j) carries a bound epsI2
+//           on its error.
 //   tier 2  FP64 with the CUDA double-precision exp/log1p, for the candidates
 //           whose df score intervals still overlap.  GB300 runs FP64 at about
 //           1/75 of its FP32 rate, so this tier only sees genuine near-ties.
@@ -25,89 +26,99 @@
 
 namespace lg {
 
-// ln2/128 split as L1 + L2 + L3: L1 = 709 * 2^-17 has 10 significant bits, so
-// N * L1 is exact for |N| < 2^14; L2 and L3 are the next FP32 pieces
-// (remainder below 5e-21).
-constexpr float EXP_L1 = 0x1.628p-8f;
-constexpr float EXP_L2 = 0x1.90bfbep-18f;
-constexpr float EXP_L3 = 0x1.1cf79ap-43f;
-constexpr float EXP_INV_L = 0x1.715476p+7f;   // 128 / ln2
-constexpr int EXP_TAB = 128;                  // 2^(j/128), j < 128
-constexpr int LOG_TAB = 257;                  // c_k = 1 + k/256, k <= 256
+// Double-float moment terms by table and Taylor series.  With a = |u|,
+//   t1 = log cosh u + ln 2 = a + phi(a),   phi(a) = log(1 + exp(-2a)),
+//   t2 = u exp(-u^2/2)     = sign(u) psi(a),   psi(a) = a exp(-a^2/2).
+// The tables hold phi, psi and their first two derivatives (double-float) at
+// the nodes c_k = k/128, k <= 1152 (a <= 9).  At an FP32 point a = c_k + h
+// (|h| <= 1/256, h exact by Sterbenz's lemma) each function is its Taylor
+// polynomial to h^5: the h and h^2 terms in double-float, h^3 .. h^5 in FP32
+// from derivatives written in tanh c (phi) or as Hermite polynomials times
+// exp(-c^2/2) (psi); the h^6 remainder is below 1e-16.  The low part of the
+// residual enters to second order through the derivative of that
+// polynomial.  Beyond a = 9, phi(a) = exp(-2a) to 1e-16 and psi(a) < 3e-17
+// come from the FP32 exponential.  A host emulation of these steps in FP32
+// against 40-digit values shows at most 1e-14 absolute error per term, with
+// no bias (the route through exp and log1p by Tang's table methods, used
+// before, showed 3e-14).
+constexpr int TT_STEP = 128;                  // nodes per unit of a
+constexpr int TT_ROWS = 9 * TT_STEP + 1;      // c_k = k / 128, k <= 1152
 
-__device__ float2 g_exp_tab[EXP_TAB];         // hi, lo of 2^(j/128)
-__device__ float4 g_log_tab[LOG_TAB];         // hi, lo of 1/c_k; hi, lo of log c_k
+__device__ float4 g_tt_pa[TT_ROWS];   // phi hi, lo; phi' hi, lo
+__device__ float4 g_tt_pb[TT_ROWS];   // phi''/2 hi, lo; psi''/2 hi, lo
+__device__ float4 g_tt_qa[TT_ROWS];   // psi hi, lo; psi' hi, lo
+__device__ float g_tt_qe[TT_ROWS];    // exp(-c^2/2)
 
-// exp(x) for x <= 0 by the table-driven method of P. T. P. Tang (ACM TOMS
-// 15(2), 1989), in double-float: x = (128 m + j) ln2/128 + r with
-// |r| <= ln2/256, exp(x) = 2^m 2^(j/128) exp(r), exp(r) by its Taylor series
-// to r^5 (the r^6 term is below 6e-19).  Returns 0 for x < -87 (exp(x) below
-// the smallest normal FP32 number).
-__device__ __forceinline__ dfl df_exp_nonpos(dfl x, const float2 *tab)
+// The block's shared-memory copies of the tables.
+struct TtTab {
+    const float4 *pa, *pb, *qa;
+    const float *qe;
+};
+constexpr size_t TT_SMEM = (size_t)TT_ROWS * (3 * sizeof(float4) + sizeof(float));
+
+// The moment terms of one residual value u: t1 = (a + al) + f, t2 = g.
+__device__ __forceinline__ void tt_terms(dfl u, const TtTab &T, float &a, float &al, dfl &f,
+                                         dfl &g)
 {
-    if (!(x.hi > -87.0f)) return {0.0f, 0.0f};
-    const float N = rintf(__fmul_rn(x.hi, EXP_INV_L));      // -16066 <= N <= 0
-    const int Ni = __float2int_rn(N);
-    const int j = Ni & (EXP_TAB - 1), m = Ni >> 7;          // Ni = 128 m + j
-    const float t0 = __fmaf_rn(-N, EXP_L1, x.hi);           // exact (Sterbenz)
-    const dfl pq = df_two_prod(N, EXP_L2);
-    const dfl s = df_two_sum(t0, -pq.hi);
-    const float low = __fadd_rn(__fsub_rn(s.lo, pq.lo), __fsub_rn(x.lo, __fmul_rn(N, EXP_L3)));
-    const dfl r = df_two_sum(s.hi, low);
-    dfl r2 = df_two_prod(r.hi, r.hi);
-    r2.lo = __fmaf_rn(__fmul_rn(2.0f, r.hi), r.lo, r2.lo);
-    const float rh = r.hi;
-    const float q = rh * rh * rh * (1.0f / 6.0f + rh * (1.0f / 24.0f + rh * (1.0f / 120.0f)));
-    const dfl a = df_fast_two_sum(1.0f, r.hi);
-    const dfl b = df_fast_two_sum(a.hi, __fmul_rn(0.5f, r2.hi));
-    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo),
-                               __fadd_rn(r.lo, __fmaf_rn(0.5f, r2.lo, q)));
-    const dfl e = df_fast_two_sum(b.hi, lo);
-    const float2 T = tab[j];
-    const dfl v = df_mul(e, dfl{T.x, T.y});
-    const float sc = __int_as_float((m + 127) << 23);       // 2^m, m >= -126
-    return {__fmul_rn(v.hi, sc), __fmul_rn(v.lo, sc)};
-}
-
-// log(1 + v) for 0 <= v <= 1 by table-driven reduction (P. T. P. Tang, ACM
-// TOMS 16(4), 1990): 1 + v = c_k (1 + d) with c_k = 1 + k/256, |d| <= 1/512,
-// log(1 + v) = log c_k + log(1 + d), the latter by its Taylor series to d^5
-// (the d^6 term is below 1e-17).
-__device__ __forceinline__ dfl df_log1p_unit(dfl v, const float4 *tab)
-{
-    const dfl w = df_fast_two_sum(1.0f, v.hi);
-    const float wlo = __fadd_rn(w.lo, v.lo);
-    const int k = min(max(__float2int_rn(__fmul_rn(__fsub_rn(w.hi, 1.0f), 256.0f)), 0),
-                      LOG_TAB - 1);
-    const float4 T = tab[k];
-    const float dh = __fsub_rn(w.hi, __fmaf_rn((float)k, 0x1p-8f, 1.0f));   // exact
-    const float p = __fmul_rn(dh, T.x);
-    float e = __fmaf_rn(dh, T.x, -p);
-    e = __fmaf_rn(dh, T.y, e);
-    e = __fmaf_rn(wlo, T.x, e);
-    const dfl d = df_two_sum(p, e);
-    dfl d2 = df_two_prod(d.hi, d.hi);
-    d2.lo = __fmaf_rn(__fmul_rn(2.0f, d.hi), d.lo, d2.lo);
-    const float dd = d.hi;
-    const float q = dd * dd * dd * (1.0f / 3.0f + dd * (-0.25f + dd * 0.2f));
-    const dfl s1 = df_two_sum(T.z, d.hi);
-    const dfl s2 = df_two_sum(s1.hi, __fmul_rn(-0.5f, d2.hi));
-    const float lo = __fadd_rn(__fadd_rn(s1.lo, s2.lo),
-                               __fadd_rn(T.w, __fadd_rn(d.lo, __fmaf_rn(-0.5f, d2.lo, q))));
-    return df_fast_two_sum(s2.hi, lo);
-}
-
-// The two moment terms of one residual value u:
-//   t1 = log cosh u + ln 2 = |u| + log(1 + exp(-2|u|)),   t2 = u exp(-u^2/2).
-__device__ __forceinline__ void df_terms(dfl u, dfl &t1, dfl &t2, const float2 *et,
-                                         const float4 *lt)
-{
-    const dfl a = u.hi < 0.0f ? dfl{-u.hi, -u.lo} : u;
-    const dfl v = df_exp_nonpos(dfl{-2.0f * a.hi, -2.0f * a.lo}, et);
-    t1 = df_add(a, df_log1p_unit(v, lt));
-    dfl u2 = df_two_prod(u.hi, u.hi);
-    u2.lo = __fmaf_rn(__fmul_rn(2.0f, u.hi), u.lo, u2.lo);
-    t2 = df_mul(u, df_exp_nonpos(dfl{-0.5f * u2.hi, -0.5f * u2.lo}, et));
+    const float sg = u.hi < 0.0f ? -1.0f : 1.0f;
+    a = fabsf(u.hi);
+    al = sg * u.lo;   // |u| = a + al
+    const float kf = rintf(__fmul_rn(a, (float)TT_STEP));
+    if (kf < (float)TT_ROWS) {
+        const int k = (int)kf;
+        const float c = __fmul_rn(kf, 1.0f / TT_STEP);
+        const float h = __fsub_rn(a, c);                               // exact
+        const float qh = __fmul_rn(h, h), ql = __fmaf_rn(h, h, -qh);   // h^2
+        const float4 A = T.pa[k], B = T.pb[k], Q = T.qa[k];
+        const float E = T.qe[k];
+        {
+            // phi' = tanh c - 1, phi'' = s = 1 - tanh^2 c, phi''' = -2 tanh c s,
+            // phi'''' = s (6 tanh^2 c - 2), phi^(5) = 8 tanh c s (2 - 3 tanh^2 c)
+            float p1h = __fmul_rn(A.z, h), p1l = __fmaf_rn(A.z, h, -p1h);
+            p1l = __fmaf_rn(A.w, h, p1l);
+            float p2h = __fmul_rn(B.x, qh), p2l = __fmaf_rn(B.x, qh, -p2h);
+            p2l = __fmaf_rn(B.x, ql, p2l);
+            p2l = __fmaf_rn(B.y, qh, p2l);
+            const float th = A.z + 1.0f, sc = B.x + B.x, t2 = th * th;
+            const float c3 = -th * sc * (1.0f / 3.0f);
+            const float c4 = sc * (6.0f * t2 - 2.0f) * (1.0f / 24.0f);
+            const float c5 = th * sc * (2.0f - 3.0f * t2) * (1.0f / 15.0f);
+            const float r = qh * h * (c3 + h * (c4 + h * c5));
+            const float corr =
+                (A.z + h * (2.0f * B.x + h * (3.0f * c3 + h * 4.0f * c4)) + B.x * al) * al;
+            const dfl s1 = df_two_sum(A.x, p1h);
+            const dfl s2 = df_fast_two_sum(s1.hi, p2h);
+            const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(A.y, p1l)),
+                                       __fadd_rn(p2l, __fadd_rn(r, corr)));
+            f = df_fast_two_sum(s2.hi, lo);
+        }
+        {
+            // psi^(m) = (-1)^m He_(m+1)(c) exp(-c^2/2)
+            const float cc = c * c;
+            float p1h = __fmul_rn(Q.z, h), p1l = __fmaf_rn(Q.z, h, -p1h);
+            p1l = __fmaf_rn(Q.w, h, p1l);
+            float p2h = __fmul_rn(B.z, qh), p2l = __fmaf_rn(B.z, qh, -p2h);
+            p2l = __fmaf_rn(B.z, ql, p2l);
+            p2l = __fmaf_rn(B.w, qh, p2l);
+            const float d3 = (6.0f * cc - cc * cc - 3.0f) * E;
+            const float d4 = c * (cc * cc - 10.0f * cc + 15.0f) * E;
+            const float d5 = -(((cc - 15.0f) * cc + 45.0f) * cc - 15.0f) * E;
+            const float r =
+                qh * h * (d3 * (1.0f / 6.0f) + h * (d4 * (1.0f / 24.0f) + h * d5 * (1.0f / 120.0f)));
+            const float corr =
+                (Q.z + h * (2.0f * B.z + h * (0.5f * d3 + h * d4 * (1.0f / 6.0f))) + B.z * al) * al;
+            const dfl s1 = df_two_sum(Q.x, p1h);
+            const dfl s2 = df_two_sum(s1.hi, p2h);
+            const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(Q.y, p1l)),
+                                       __fadd_rn(p2l, __fadd_rn(r, corr)));
+            const dfl v = df_fast_two_sum(s2.hi, lo);
+            g = dfl{sg * v.hi, sg * v.lo};
+        }
+    } else {
+        const float e = expf(-2.0f * a);
+        f = dfl{e, -2.0f * e * al};
+        g = dfl{sg * a * expf(-0.5f * a * a), 0.0f};
+    }
 }
 
 // alpha * za - beta * zb in double-float.
@@ -134,6 +145,14 @@ struct DfAcc {
     dfl s{0.0f, 0.0f};
     double d = 0.0;
     __device__ __forceinline__ void add(dfl t) { s = df_add(s, t); }
+    // adds (a + al) + f, the three parts of t1 from tt_terms
+    __device__ __forceinline__ void add3(float a, float al, dfl f)
+    {
+        const dfl x = df_two_sum(s.hi, a);
+        const dfl y = df_two_sum(x.hi, f.hi);
+        s = df_fast_two_sum(y.hi, __fadd_rn(__fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)),
+                                            __fadd_rn(al, f.lo)));
+    }
     __device__ __forceinline__ void fold()
     {
         d += (double)s.hi + (double)s.lo;
@@ -154,8 +173,8 @@ __device__ __forceinline__ void f64_terms(double u, double &t1, double &t2)
 // position); TIER 2: FP64 from the residual data R by original index.
 // The work of one instance, for the global warp index w0 of nw warps.
 template <int TIER>
-__device__ __forceinline__ void hp_instance(const HpParams &P, const float2 *s_exp,
-                                            const float4 *s_log, int64_t w0, int64_t nw)
+__device__ __forceinline__ void hp_instance(const HpParams &P, const TtTab &T, int64_t w0,
+                                            int64_t nw)
 {
     const int lane = threadIdx.x & 31;
     int cbeg = 0;
@@ -194,10 +213,11 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const float2 *s_e
                 DfAcc A1, A2;
                 int cnt = 0;
                 for (int s = s0 + lane; s < n; s += 32) {
-                    dfl t1, t2;
-                    df_terms(dfl{zh[s], zl[s]}, t1, t2, s_exp, s_log);
-                    A1.add(t1);
-                    A2.add(t2);
+                    float ua, ual;
+                    dfl f, g;
+                    tt_terms(dfl{zh[s], zl[s]}, T, ua, ual, f, g);
+                    A1.add3(ua, ual, f);
+                    A2.add(g);
                     if (++cnt == HP_FOLD) {
                         A1.fold();
                         A2.fold();
@@ -281,13 +301,14 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const float2 *s_e
             int cnt = 0;
             for (int s = s0 + lane; s < n; s += 32) {
                 const dfl za{zah[s], zal[s]}, zb{zbh[s], zbl[s]};
-                dfl t1, t2;
-                df_terms(df_resid(al, be, za, zb), t1, t2, s_exp, s_log);
-                A1.add(t1);
-                A2.add(t2);
-                df_terms(df_resid(al, be, zb, za), t1, t2, s_exp, s_log);
-                B1.add(t1);
-                B2.add(t2);
+                float ua, ual;
+                dfl f, g;
+                tt_terms(df_resid(al, be, za, zb), T, ua, ual, f, g);
+                A1.add3(ua, ual, f);
+                A2.add(g);
+                tt_terms(df_resid(al, be, zb, za), T, ua, ual, f, g);
+                B1.add3(ua, ual, f);
+                B2.add(g);
                 if (++cnt == HP_FOLD) {
                     A1.fold();
                     A2.fold();
@@ -346,54 +367,79 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const float2 *s_e
 }
 
 // Every warp of the grid works on every instance in turn, so the whole GPU
-// serves whichever instances have work (in a batch usually a few).
+// serves whichever instances have work (in a batch usually a few).  The
+// double-float tier copies the Taylor tables into the block's shared memory
+// first, unless no instance has work in this pass.
 template <int TIER>
 __global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__restrict__ Ps,
                                                              int count)
 {
-    __shared__ float2 s_exp[TIER == 1 ? EXP_TAB : 1];
-    __shared__ float4 s_log[TIER == 1 ? LOG_TAB : 1];
+    extern __shared__ float4 tt_smem[];
+    TtTab T{};
     if (TIER == 1) {
-        for (int k = threadIdx.x; k < EXP_TAB; k += blockDim.x) s_exp[k] = g_exp_tab[k];
-        for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) s_log[k] = g_log_tab[k];
+        bool any = false;
+        for (int inst = 0; inst < count && !any; ++inst) {
+            const HpParams &P = Ps[inst];
+            const DevState *st = P.state;
+            any = P.mode == 0 ||
+                  (!st->resolved && st->tier == TIER && st->pass_end > st->pass_begin);
+        }
+        if (!any) return;
+        float4 *pa = tt_smem, *pb = pa + TT_ROWS, *qa = pb + TT_ROWS;
+        float *qe = reinterpret_cast<float *>(qa + TT_ROWS);
+        for (int k = threadIdx.x; k < TT_ROWS; k += blockDim.x) {
+            pa[k] = g_tt_pa[k];
+            pb[k] = g_tt_pb[k];
+            qa[k] = g_tt_qa[k];
+            qe[k] = g_tt_qe[k];
+        }
         __syncthreads();
+        T = TtTab{pa, pb, qa, qe};
     }
     constexpr int WPB = HP_THREADS / 32;
     const int64_t w0 = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * WPB;
-    for (int inst = 0; inst < count; ++inst) hp_instance<TIER>(Ps[inst], s_exp, s_log, w0, nw);
+    for (int inst = 0; inst < count; ++inst) hp_instance<TIER>(Ps[inst], T, w0, nw);
 }
 
 cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     if (tier == 1)
-        k_pairs_hp_b<1><<<blocks, HP_THREADS, 0, s>>>(P, count);
+        k_pairs_hp_b<1><<<blocks, HP_THREADS, TT_SMEM, s>>>(P, count);
     else
         k_pairs_hp_b<2><<<blocks, HP_THREADS, 0, s>>>(P, count);
     return cudaGetLastError();
 }
 
-// Tables of the double-float exp and log: 2^(j/128), 1/c_k and log c_k from
-// the host's FP64 libm (about 1 ulp of FP64), split into FP32 hi + lo.
+// Tables of the double-float tier from the host's FP64 libm (about 1 ulp of
+// FP64, well inside the 48 bits of a double-float), written without
+// cancellation: with e = exp(-2c), tanh c - 1 = -2e / (1 + e) and
+// (1 - tanh^2 c) / 2 = 2e / (1 + e)^2.
 cudaError_t df_tables_setup()
 {
-    float2 et[EXP_TAB];
-    float4 lt[LOG_TAB];
-    for (int j = 0; j < EXP_TAB; ++j) {
-        const double v = exp2((double)j / EXP_TAB);
-        const float h = (float)v;
-        et[j] = make_float2(h, (float)(v - (double)h));
+    static float4 pa[TT_ROWS], pb[TT_ROWS], qa[TT_ROWS];
+    static float qe[TT_ROWS];
+    auto hi = [](double v) { return (float)v; };
+    auto lo = [](double v) { return (float)(v - (double)(float)v); };
+    for (int k = 0; k < TT_ROWS; ++k) {
+        const double c = (double)k / TT_STEP;
+        const double e = exp(-2.0 * c);
+        const double phi = log1p(e), d1 = -2.0 * e / (1.0 + e), d2 = 2.0 * e / ((1.0 + e) * (1.0 + e));
+        const double E = exp(-0.5 * c * c);
+        const double psi = c * E, q1 = (1.0 - c * c) * E, q2 = 0.5 * (c * c * c - 3.0 * c) * E;
+        pa[k] = make_float4(hi(phi), lo(phi), hi(d1), lo(d1));
+        pb[k] = make_float4(hi(d2), lo(d2), hi(q2), lo(q2));
+        qa[k] = make_float4(hi(psi), lo(psi), hi(q1), lo(q1));
+        qe[k] = (float)E;
     }
-    for (int k = 0; k < LOG_TAB; ++k) {
-        const double c = 1.0 + (double)k / 256.0;
-        const double inv = 1.0 / c, lg = log(c);
-        const float ih = (float)inv, lh = (float)lg;
-        lt[k] = make_float4(ih, (float)(inv - (double)ih), lh, (float)(lg - (double)lh));
-    }
-    cudaError_t e = cudaMemcpyToSymbol(g_exp_tab, et, sizeof(et));
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(g_log_tab, lt, sizeof(lt));
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(g_tt_pa, pa, sizeof(pa))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_tt_pb, pb, sizeof(pb))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_tt_qa, qa, sizeof(qa))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_tt_qe, qe, sizeof(qe))) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pairs_hp_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TT_SMEM);
 }
 
 // ------------------------------------------------------- refine + decide --

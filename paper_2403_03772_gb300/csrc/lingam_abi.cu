@@ -1841,6 +1841,17 @@ lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam
     return LINGAM_OK;
 }
 
+static_assert(PAIR_NCFG == LINGAM_PAIR_TILES, "the C ABI announces every configuration");
+
+lingam_status lingam_pair_tile_info(int32_t tile, int32_t *out)
+{
+    if (!out || tile < 0 || tile >= PAIR_NCFG) return LINGAM_ERR_ARG;
+    const PairCfg &G = PAIR_CFGS[tile];
+    const int32_t v[8] = {G.wi, G.wj, G.wgi, G.wgj, G.stages, G.groups, G.fold, G.packed};
+    for (int k = 0; k < 8; ++k) out[k] = v[k];
+    return LINGAM_OK;
+}
+
 // Times one pair-kernel launch of configuration cfg on the synthetic columns
 // (minimum of three runs after a warm-up).
 // `copies` identical instances in one launch (a batch of that many problems),

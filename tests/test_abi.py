@@ -104,3 +104,18 @@ def test_library_has_no_undefined_internal_symbols(lib):
                          check=True).stdout
     missing = [line.split()[-1] for line in out.splitlines() if "_ZN2lg" in line]
     assert not missing, missing
+
+
+def test_pair_tile_info_describes_every_tile(lib):
+    import paper_2403_03772_gb300 as pkg
+    txt = open(HEADER).read()
+    n = int(re.search(r"#define LINGAM_PAIR_TILES (\d+)", txt).group(1))
+    assert n == pkg.PAIR_TILES
+    for t in range(n):
+        g = pkg.lingam_pair_tile_info(t)
+        assert 32 * g["wgi"] * g["wgj"] <= 1024
+        assert g["groups"] in (1, 2) and g["packed"] in (0, 1) and g["fold"] >= 1
+        assert g["stages"] >= 2 and g["wi"] >= 1 and g["wj"] >= 1
+    for bad in (-1, n):
+        with pytest.raises(pkg.LingamError):
+            pkg.lingam_pair_tile_info(bad)
