@@ -224,12 +224,16 @@ def run_one_order(args):
         ctx.causal_order(X)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
         order = ctx.causal_order(X)
+        b.record()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         st = ctx.stats()
         print(json.dumps({"one_order": prec, "workload": args.workload,
-                          "graph_nodes": st["graph_nodes"],
+                          "ms": a.elapsed_time(b), "graph_nodes": st["graph_nodes"],
                           **{k: st[k] for k in ("refined_steps", "df_candidates",
                                                 "fp64_candidates", "genuine_ties")},
                           "order_head": [int(v) for v in order[:8]]}), flush=True)

@@ -47,14 +47,38 @@ constexpr int TT_ROWS = 9 * TT_STEP + 1;      // c_k = k / 128, k <= 1152
 __device__ float4 g_tt_pa[TT_ROWS];   // phi hi, lo; phi' hi, lo
 __device__ float4 g_tt_pb[TT_ROWS];   // phi''/2 hi, lo; psi''/2 hi, lo
 __device__ float4 g_tt_qa[TT_ROWS];   // psi hi, lo; psi' hi, lo
-__device__ float g_tt_qe[TT_ROWS];    // exp(-c^2/2)
+__device__ float4 g_tt_pc[TT_ROWS];   // phi'''/6, phi''''/24, phi^(5)/120, psi'''/6
+__device__ float2 g_tt_qc[TT_ROWS];   // psi''''/24, psi^(5)/120
 
 // The block's shared-memory copies of the tables.
 struct TtTab {
-    const float4 *pa, *pb, *qa;
-    const float *qe;
+    const float4 *pa, *pb, *qa, *pc;
+    const float2 *qc;
 };
-constexpr size_t TT_SMEM = (size_t)TT_ROWS * (3 * sizeof(float4) + sizeof(float));
+constexpr size_t TT_SMEM = (size_t)TT_ROWS * (4 * sizeof(float4) + sizeof(float2));
+
+// One function's value at c + h from its row: v0 (double-float value), v1
+// (double-float first derivative), v2 (double-float half second derivative)
+// and c3, c4, c5 (FP32 Taylor coefficients of h^3 .. h^5); al is the low
+// part of the argument, entered to second order through the derivative of
+// the polynomial.
+__device__ __forceinline__ dfl tt_eval(float v0h, float v0l, float v1h, float v1l, float v2h,
+                                       float v2l, float c3, float c4, float c5, float h,
+                                       float qh, float ql, float al)
+{
+    float p1h = __fmul_rn(v1h, h), p1l = __fmaf_rn(v1h, h, -p1h);
+    p1l = __fmaf_rn(v1l, h, p1l);
+    float p2h = __fmul_rn(v2h, qh), p2l = __fmaf_rn(v2h, qh, -p2h);
+    p2l = __fmaf_rn(v2h, ql, p2l);
+    p2l = __fmaf_rn(v2l, qh, p2l);
+    const float r = qh * h * (c3 + h * (c4 + h * c5));
+    const float corr = (v1h + h * (2.0f * v2h + h * (3.0f * c3 + h * 4.0f * c4)) + v2h * al) * al;
+    const dfl s1 = df_two_sum(v0h, p1h);
+    const dfl s2 = df_two_sum(s1.hi, p2h);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(v0l, p1l)),
+                               __fadd_rn(p2l, __fadd_rn(r, corr)));
+    return df_fast_two_sum(s2.hi, lo);
+}
 
 // The moment terms of one residual value u: t1 = (a + al) + f, t2 = g.
 __device__ __forceinline__ void tt_terms(dfl u, const TtTab &T, float &a, float &al, dfl &f,
@@ -66,54 +90,13 @@ __device__ __forceinline__ void tt_terms(dfl u, const TtTab &T, float &a, float 
     const float kf = rintf(__fmul_rn(a, (float)TT_STEP));
     if (kf < (float)TT_ROWS) {
         const int k = (int)kf;
-        const float c = __fmul_rn(kf, 1.0f / TT_STEP);
-        const float h = __fsub_rn(a, c);                               // exact
+        const float h = __fsub_rn(a, __fmul_rn(kf, 1.0f / TT_STEP));   // exact
         const float qh = __fmul_rn(h, h), ql = __fmaf_rn(h, h, -qh);   // h^2
-        const float4 A = T.pa[k], B = T.pb[k], Q = T.qa[k];
-        const float E = T.qe[k];
-        {
-            // phi' = tanh c - 1, phi'' = s = 1 - tanh^2 c, phi''' = -2 tanh c s,
-            // phi'''' = s (6 tanh^2 c - 2), phi^(5) = 8 tanh c s (2 - 3 tanh^2 c)
-            float p1h = __fmul_rn(A.z, h), p1l = __fmaf_rn(A.z, h, -p1h);
-            p1l = __fmaf_rn(A.w, h, p1l);
-            float p2h = __fmul_rn(B.x, qh), p2l = __fmaf_rn(B.x, qh, -p2h);
-            p2l = __fmaf_rn(B.x, ql, p2l);
-            p2l = __fmaf_rn(B.y, qh, p2l);
-            const float th = A.z + 1.0f, sc = B.x + B.x, t2 = th * th;
-            const float c3 = -th * sc * (1.0f / 3.0f);
-            const float c4 = sc * (6.0f * t2 - 2.0f) * (1.0f / 24.0f);
-            const float c5 = th * sc * (2.0f - 3.0f * t2) * (1.0f / 15.0f);
-            const float r = qh * h * (c3 + h * (c4 + h * c5));
-            const float corr =
-                (A.z + h * (2.0f * B.x + h * (3.0f * c3 + h * 4.0f * c4)) + B.x * al) * al;
-            const dfl s1 = df_two_sum(A.x, p1h);
-            const dfl s2 = df_fast_two_sum(s1.hi, p2h);
-            const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(A.y, p1l)),
-                                       __fadd_rn(p2l, __fadd_rn(r, corr)));
-            f = df_fast_two_sum(s2.hi, lo);
-        }
-        {
-            // psi^(m) = (-1)^m He_(m+1)(c) exp(-c^2/2)
-            const float cc = c * c;
-            float p1h = __fmul_rn(Q.z, h), p1l = __fmaf_rn(Q.z, h, -p1h);
-            p1l = __fmaf_rn(Q.w, h, p1l);
-            float p2h = __fmul_rn(B.z, qh), p2l = __fmaf_rn(B.z, qh, -p2h);
-            p2l = __fmaf_rn(B.z, ql, p2l);
-            p2l = __fmaf_rn(B.w, qh, p2l);
-            const float d3 = (6.0f * cc - cc * cc - 3.0f) * E;
-            const float d4 = c * (cc * cc - 10.0f * cc + 15.0f) * E;
-            const float d5 = -(((cc - 15.0f) * cc + 45.0f) * cc - 15.0f) * E;
-            const float r =
-                qh * h * (d3 * (1.0f / 6.0f) + h * (d4 * (1.0f / 24.0f) + h * d5 * (1.0f / 120.0f)));
-            const float corr =
-                (Q.z + h * (2.0f * B.z + h * (0.5f * d3 + h * d4 * (1.0f / 6.0f))) + B.z * al) * al;
-            const dfl s1 = df_two_sum(Q.x, p1h);
-            const dfl s2 = df_two_sum(s1.hi, p2h);
-            const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(Q.y, p1l)),
-                                       __fadd_rn(p2l, __fadd_rn(r, corr)));
-            const dfl v = df_fast_two_sum(s2.hi, lo);
-            g = dfl{sg * v.hi, sg * v.lo};
-        }
+        const float4 A = T.pa[k], B = T.pb[k], Q = T.qa[k], C = T.pc[k];
+        const float2 D = T.qc[k];
+        f = tt_eval(A.x, A.y, A.z, A.w, B.x, B.y, C.x, C.y, C.z, h, qh, ql, al);
+        const dfl v = tt_eval(Q.x, Q.y, Q.z, Q.w, B.z, B.w, C.w, D.x, D.y, h, qh, ql, al);
+        g = dfl{sg * v.hi, sg * v.lo};
     } else {
         const float e = expf(-2.0f * a);
         f = dfl{e, -2.0f * e * al};
@@ -212,10 +195,16 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const TtTab &T, i
                 const float *zh = P.zhi + (int64_t)a * P.ldz, *zl = P.zlo + (int64_t)a * P.ldz;
                 DfAcc A1, A2;
                 int cnt = 0;
-                for (int s = s0 + lane; s < n; s += 32) {
+                // the next iteration's sample is loaded before this one's work
+                int s = s0 + lane;
+                dfl zn{0.0f, 0.0f};
+                if (s < n) zn = dfl{__ldg(zh + s), __ldg(zl + s)};
+                for (; s < n; s += 32) {
+                    const dfl z = zn;
+                    if (s + 32 < n) zn = dfl{__ldg(zh + s + 32), __ldg(zl + s + 32)};
                     float ua, ual;
                     dfl f, g;
-                    tt_terms(dfl{zh[s], zl[s]}, T, ua, ual, f, g);
+                    tt_terms(z, T, ua, ual, f, g);
                     A1.add3(ua, ual, f);
                     A2.add(g);
                     if (++cnt == HP_FOLD) {
@@ -299,8 +288,19 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const TtTab &T, i
             const float *zbh = P.zhi + (int64_t)b * P.ldz, *zbl = P.zlo + (int64_t)b * P.ldz;
             DfAcc A1, A2, B1, B2;
             int cnt = 0;
-            for (int s = s0 + lane; s < n; s += 32) {
-                const dfl za{zah[s], zal[s]}, zb{zbh[s], zbl[s]};
+            // the next iteration's samples are loaded before this one's work
+            int s = s0 + lane;
+            dfl zan{0.0f, 0.0f}, zbn{0.0f, 0.0f};
+            if (s < n) {
+                zan = dfl{__ldg(zah + s), __ldg(zal + s)};
+                zbn = dfl{__ldg(zbh + s), __ldg(zbl + s)};
+            }
+            for (; s < n; s += 32) {
+                const dfl za = zan, zb = zbn;
+                if (s + 32 < n) {
+                    zan = dfl{__ldg(zah + s + 32), __ldg(zal + s + 32)};
+                    zbn = dfl{__ldg(zbh + s + 32), __ldg(zbl + s + 32)};
+                }
                 float ua, ual;
                 dfl f, g;
                 tt_terms(df_resid(al, be, za, zb), T, ua, ual, f, g);
@@ -371,7 +371,7 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const TtTab &T, i
 // double-float tier copies the Taylor tables into the block's shared memory
 // first, unless no instance has work in this pass.
 template <int TIER>
-__global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__restrict__ Ps,
+__global__ void __launch_bounds__(HP_THREADS, TIER == 1 ? 2 : 3) k_pairs_hp_b(const HpParams *__restrict__ Ps,
                                                              int count)
 {
     extern __shared__ float4 tt_smem[];
@@ -385,16 +385,17 @@ __global__ void __launch_bounds__(HP_THREADS, 3) k_pairs_hp_b(const HpParams *__
                   (!st->resolved && st->tier == TIER && st->pass_end > st->pass_begin);
         }
         if (!any) return;
-        float4 *pa = tt_smem, *pb = pa + TT_ROWS, *qa = pb + TT_ROWS;
-        float *qe = reinterpret_cast<float *>(qa + TT_ROWS);
+        float4 *pa = tt_smem, *pb = pa + TT_ROWS, *qa = pb + TT_ROWS, *pc = qa + TT_ROWS;
+        float2 *qc = reinterpret_cast<float2 *>(pc + TT_ROWS);
         for (int k = threadIdx.x; k < TT_ROWS; k += blockDim.x) {
             pa[k] = g_tt_pa[k];
             pb[k] = g_tt_pb[k];
             qa[k] = g_tt_qa[k];
-            qe[k] = g_tt_qe[k];
+            pc[k] = g_tt_pc[k];
+            qc[k] = g_tt_qc[k];
         }
         __syncthreads();
-        T = TtTab{pa, pb, qa, qe};
+        T = TtTab{pa, pb, qa, pc, qc};
     }
     constexpr int WPB = HP_THREADS / 32;
     const int64_t w0 = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
@@ -414,30 +415,44 @@ cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks
 
 // Tables of the double-float tier from the host's FP64 libm (about 1 ulp of
 // FP64, well inside the 48 bits of a double-float), written without
-// cancellation: with e = exp(-2c), tanh c - 1 = -2e / (1 + e) and
-// (1 - tanh^2 c) / 2 = 2e / (1 + e)^2.
+// cancellation: with e = exp(-2c), t = tanh c and s = 1 - t^2,
+// t - 1 = -2e / (1 + e) and s = 4e / (1 + e)^2.  Derivatives of phi:
+// phi' = t - 1, phi'' = s, phi''' = -2 t s, phi'''' = s (6 t^2 - 2),
+// phi^(5) = 8 t s (2 - 3 t^2); of psi: psi^(m) = (-1)^m He_(m+1)(c) E with
+// E = exp(-c^2/2) and the Hermite polynomials He_2 = c^2 - 1,
+// He_3 = c^3 - 3c, He_4 = c^4 - 6c^2 + 3, He_5 = c^5 - 10c^3 + 15c,
+// He_6 = c^6 - 15c^4 + 45c^2 - 15.
 cudaError_t df_tables_setup()
 {
-    static float4 pa[TT_ROWS], pb[TT_ROWS], qa[TT_ROWS];
-    static float qe[TT_ROWS];
+    static float4 pa[TT_ROWS], pb[TT_ROWS], qa[TT_ROWS], pc[TT_ROWS];
+    static float2 qc[TT_ROWS];
     auto hi = [](double v) { return (float)v; };
     auto lo = [](double v) { return (float)(v - (double)(float)v); };
     for (int k = 0; k < TT_ROWS; ++k) {
-        const double c = (double)k / TT_STEP;
+        const double c = (double)k / TT_STEP, c2 = c * c;
         const double e = exp(-2.0 * c);
-        const double phi = log1p(e), d1 = -2.0 * e / (1.0 + e), d2 = 2.0 * e / ((1.0 + e) * (1.0 + e));
-        const double E = exp(-0.5 * c * c);
-        const double psi = c * E, q1 = (1.0 - c * c) * E, q2 = 0.5 * (c * c * c - 3.0 * c) * E;
+        const double t = (1.0 - e) / (1.0 + e), s = 4.0 * e / ((1.0 + e) * (1.0 + e));
+        const double phi = log1p(e), d1 = -2.0 * e / (1.0 + e), d2 = 0.5 * s;
+        const double d3 = -2.0 * t * s, d4 = s * (6.0 * t * t - 2.0);
+        const double d5 = 8.0 * t * s * (2.0 - 3.0 * t * t);
+        const double E = exp(-0.5 * c2);
+        const double psi = c * E, q1 = (1.0 - c2) * E, q2 = 0.5 * (c2 * c - 3.0 * c) * E;
+        const double q3 = -(c2 * c2 - 6.0 * c2 + 3.0) * E;
+        const double q4 = (c2 * c2 * c - 10.0 * c2 * c + 15.0 * c) * E;
+        const double q5 = -(((c2 - 15.0) * c2 + 45.0) * c2 - 15.0) * E;
         pa[k] = make_float4(hi(phi), lo(phi), hi(d1), lo(d1));
         pb[k] = make_float4(hi(d2), lo(d2), hi(q2), lo(q2));
         qa[k] = make_float4(hi(psi), lo(psi), hi(q1), lo(q1));
-        qe[k] = (float)E;
+        pc[k] = make_float4((float)(d3 / 6.0), (float)(d4 / 24.0), (float)(d5 / 120.0),
+                            (float)(q3 / 6.0));
+        qc[k] = make_float2((float)(q4 / 24.0), (float)(q5 / 120.0));
     }
-    cudaError_t e;
-    if ((e = cudaMemcpyToSymbol(g_tt_pa, pa, sizeof(pa))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(g_tt_pb, pb, sizeof(pb))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(g_tt_qa, qa, sizeof(qa))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(g_tt_qe, qe, sizeof(qe))) != cudaSuccess) return e;
+    cudaError_t err;
+    if ((err = cudaMemcpyToSymbol(g_tt_pa, pa, sizeof(pa))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(g_tt_pb, pb, sizeof(pb))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(g_tt_qa, qa, sizeof(qa))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(g_tt_pc, pc, sizeof(pc))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(g_tt_qc, qc, sizeof(qc))) != cudaSuccess) return err;
     return cudaFuncSetAttribute(k_pairs_hp_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TT_SMEM);
 }
