@@ -209,6 +209,30 @@ __device__ __forceinline__ int find_instance(const int *prefix, int count, int b
     return lo;
 }
 
+// Instances of a batched launch with work, found by the whole block at once
+// instead of one instance after another in every warp: thread t tests
+// instance base + t; the ones with has(k) true are listed in ascending order
+// in list[] (blockDim.x entries), their number returned to every thread.
+// wcnt holds blockDim.x / 32 ints.  Every thread of the block must call it.
+template <class F>
+__device__ __forceinline__ int block_active_list(int base, int count, F has, int *list, int *wcnt)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int k = base + (int)threadIdx.x;
+    const bool act = k < count && has(k);
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) wcnt[w] = __popc(m);
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int i = 0; i < nwarp; ++i) {
+        off += i < w ? wcnt[i] : 0;
+        total += wcnt[i];
+    }
+    if (act) list[off + __popc(m & ((1u << lane) - 1u))] = k;
+    __syncthreads();
+    return total;
+}
+
 // Block-wide sum in a fixed order (warp xor trees, then warp 0 over the
 // per-warp totals); the result is valid in warp 0.
 __device__ __forceinline__ double block_sum(double v, double *sh)

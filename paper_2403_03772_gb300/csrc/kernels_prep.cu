@@ -412,19 +412,31 @@ cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStrea
 // z_lo = fl32(R_i / sigma_i - z_hi) with the same FP64 product the regress
 // kernel rounded to z_hi; only for steps that re-score (state routed to the
 // double-float tier) or score every pair in double-float (`always`).
-__global__ void k_zlo_b(const ZloParams *__restrict__ Ps, int count)
+__global__ void __launch_bounds__(256) k_zlo_b(const ZloParams *__restrict__ Ps, int count)
 {
-    for (int inst = 0; inst < count; ++inst) {
-        const ZloParams &P = Ps[inst];
-        if (!P.always && (P.state->resolved || P.state->tier != 1)) continue;
-        const int64_t total = (int64_t)P.p * P.n;
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-             e += (int64_t)gridDim.x * blockDim.x) {
-            const int a = (int)(e / P.n), s = (int)(e % P.n);
-            const double zx = P.R[(int64_t)P.U[a] * P.ldr + s] * P.isd[a];
-            const int64_t q = (int64_t)a * P.ldz + s;
-            P.zlo[q] = (float)(zx - (double)P.zhi[q]);
+    __shared__ int s_act[256];
+    __shared__ int s_wcnt[8];
+    for (int base = 0; base < count; base += 256) {
+        // the instances of this chunk that need the low parts, found at once
+        const int nact = block_active_list(
+            base, count,
+            [&](int k) {
+                const ZloParams &P = Ps[k];
+                return P.always || (!P.state->resolved && P.state->tier == 1);
+            },
+            s_act, s_wcnt);
+        for (int i = 0; i < nact; ++i) {
+            const ZloParams &P = Ps[s_act[i]];
+            const int64_t total = (int64_t)P.p * P.n;
+            for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+                 e += (int64_t)gridDim.x * blockDim.x) {
+                const int a = (int)(e / P.n), s = (int)(e % P.n);
+                const double zx = P.R[(int64_t)P.U[a] * P.ldr + s] * P.isd[a];
+                const int64_t q = (int64_t)a * P.ldz + s;
+                P.zlo[q] = (float)(zx - (double)P.zhi[q]);
+            }
         }
+        __syncthreads();   // s_act is rewritten by the next chunk
     }
 }
 

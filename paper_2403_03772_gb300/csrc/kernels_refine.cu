@@ -366,41 +366,52 @@ __device__ __forceinline__ void hp_instance(const HpParams &P, const TtTab &T, i
     }
 }
 
-// Every warp of the grid works on every instance in turn, so the whole GPU
-// serves whichever instances have work (in a batch usually a few).  The
-// double-float tier copies the Taylor tables into the block's shared memory
-// first, unless no instance has work in this pass.
+// Every warp of the grid works on every instance with work in turn, so the
+// whole GPU serves whichever instances have work (in a batch usually a few).
+// Each block first lists those instances (256 at a time, all threads testing
+// at once); the double-float tier copies the Taylor tables into the block's
+// shared memory before the first one, and not at all when there is none.
 template <int TIER>
-__global__ void __launch_bounds__(HP_THREADS, TIER == 1 ? 2 : 3) k_pairs_hp_b(const HpParams *__restrict__ Ps,
-                                                             int count)
+__device__ __forceinline__ bool hp_has_work(const HpParams &P)
+{
+    if (P.mode == 0) return true;
+    const DevState *st = P.state;
+    return !st->resolved && st->tier == TIER && st->pass_end > st->pass_begin;
+}
+
+template <int TIER>
+__global__ void __launch_bounds__(HP_THREADS, TIER == 1 ? 2 : 3)
+    k_pairs_hp_b(const HpParams *__restrict__ Ps, int count)
 {
     extern __shared__ float4 tt_smem[];
+    __shared__ int s_act[HP_THREADS];
+    __shared__ int s_wcnt[HP_THREADS / 32];
     TtTab T{};
-    if (TIER == 1) {
-        bool any = false;
-        for (int inst = 0; inst < count && !any; ++inst) {
-            const HpParams &P = Ps[inst];
-            const DevState *st = P.state;
-            any = P.mode == 0 ||
-                  (!st->resolved && st->tier == TIER && st->pass_end > st->pass_begin);
-        }
-        if (!any) return;
-        float4 *pa = tt_smem, *pb = pa + TT_ROWS, *qa = pb + TT_ROWS, *pc = qa + TT_ROWS;
-        float2 *qc = reinterpret_cast<float2 *>(pc + TT_ROWS);
-        for (int k = threadIdx.x; k < TT_ROWS; k += blockDim.x) {
-            pa[k] = g_tt_pa[k];
-            pb[k] = g_tt_pb[k];
-            qa[k] = g_tt_qa[k];
-            pc[k] = g_tt_pc[k];
-            qc[k] = g_tt_qc[k];
-        }
-        __syncthreads();
-        T = TtTab{pa, pb, qa, pc, qc};
-    }
+    bool tables = false;
     constexpr int WPB = HP_THREADS / 32;
     const int64_t w0 = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * WPB;
-    for (int inst = 0; inst < count; ++inst) hp_instance<TIER>(Ps[inst], T, w0, nw);
+    for (int base = 0; base < count; base += HP_THREADS) {
+        const int nact = block_active_list(
+            base, count, [&](int k) { return hp_has_work<TIER>(Ps[k]); }, s_act, s_wcnt);
+        if (nact == 0) continue;
+        if (TIER == 1 && !tables) {
+            float4 *pa = tt_smem, *pb = pa + TT_ROWS, *qa = pb + TT_ROWS, *pc = qa + TT_ROWS;
+            float2 *qc = reinterpret_cast<float2 *>(pc + TT_ROWS);
+            for (int k = threadIdx.x; k < TT_ROWS; k += blockDim.x) {
+                pa[k] = g_tt_pa[k];
+                pb[k] = g_tt_pb[k];
+                qa[k] = g_tt_qa[k];
+                pc[k] = g_tt_pc[k];
+                qc[k] = g_tt_qc[k];
+            }
+            __syncthreads();
+            T = TtTab{pa, pb, qa, pc, qc};
+            tables = true;
+        }
+        for (int i = 0; i < nact; ++i) hp_instance<TIER>(Ps[s_act[i]], T, w0, nw);
+        __syncthreads();   // s_act is rewritten by the next chunk
+    }
 }
 
 cudaError_t launch_pairs_hp_b(int tier, const HpParams *P, int count, int blocks, cudaStream_t s)
