@@ -373,3 +373,28 @@ def is_topological(order, B: np.ndarray, min_abs: float = 0.0) -> bool:
     pos[np.asarray(order)] = np.arange(len(order))
     child, parent = np.nonzero(np.abs(B) > min_abs)
     return bool(np.all(pos[parent] < pos[child]))
+
+
+def ancestors(B: np.ndarray) -> np.ndarray:
+    """anc[i, j] = True when x_j is an ancestor of x_i in the DAG of B
+    (B[child, parent] != 0), by repeated composition of the parent relation."""
+    par = np.asarray(B) != 0
+    anc = par.copy()
+    while True:
+        nxt = anc | ((anc.astype(np.int64) @ par.astype(np.int64)) > 0)
+        if (nxt == anc).all():
+            return anc
+        anc = nxt
+
+
+def prior_from_dag(st: Stream, B: np.ndarray, reveal: float = 0.3) -> np.ndarray:
+    """Ancestry knowledge consistent with the DAG of B: each ordered pair
+    (i, j), i != j, is revealed with probability ``reveal`` as 1 (x_j is an
+    ancestor of x_i) or 0 (it is not); the rest are -1 (unknown)."""
+    d = B.shape[0]
+    anc = ancestors(B)
+    pk = np.where(anc, 1, 0).astype(np.int8)
+    hide = st.random((d, d)) >= reveal
+    pk[hide] = -1
+    np.fill_diagonal(pk, -1)
+    return pk

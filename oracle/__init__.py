@@ -72,6 +72,8 @@ def _load():
                                            ctypes.POINTER(I32)]
         lib.oracle_row_scores.argtypes = [PD, I64, I64, PI32, I64, PI32, I64, I32, PD]
         lib.oracle_causal_order.argtypes = [PD, I64, I64, I32, I32, PI32, PD, I64]
+        lib.oracle_causal_order_prior.argtypes = [PD, I64, I64, I32, I32,
+                                                  ctypes.POINTER(ctypes.c_int8), PI32, PD, I64]
         lib.oracle_moments.argtypes = [PD, I64, PD, PD, PD, PD]
         lib.oracle_entropy.argtypes = [PD, I64, PD, PD]
         lib.oracle_entropy_from_moments.argtypes = [D, D]
@@ -202,17 +204,32 @@ def row_scores(R, rows, U=None, threads: int | None = None) -> np.ndarray:
 
 
 def causal_order(X, literal: bool = False, threads: int | None = None,
-                 scores: bool = False, max_steps: int = 0):
+                 scores: bool = False, max_steps: int = 0, prior=None):
     """DirectLiNGAM causal order of X ([n, d]); optionally the per-step scores
-    (row t = k_list of step t at the original indices, NaN once removed)."""
+    (row t = k_list of step t at the original indices, NaN once removed).
+
+    prior: optional [d, d] ancestry knowledge, prior[i, j] = 1 if x_j is known
+    to be an ancestor of x_i, 0 if known not to be, -1 unknown (a reading:
+    the paper has none).  A variable is chosen only when no remaining
+    variable is a known ancestor of it, and only among the known-exogenous
+    remaining variables when there are any; the scores are unchanged."""
     X = _f64(X)
     n, d = X.shape
     order = np.empty(d, dtype=np.int32)
     sc = np.empty((d, d)) if scores else None
-    code = _load().oracle_causal_order(
-        _pd(X), n, d, int(bool(literal)), int(threads or default_threads()),
-        order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-        _pd(sc) if sc is not None else None, int(max_steps))
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    if prior is None:
+        code = _load().oracle_causal_order(
+            _pd(X), n, d, int(bool(literal)), int(threads or default_threads()),
+            order.ctypes.data_as(P32), _pd(sc) if sc is not None else None, int(max_steps))
+    else:
+        pk = np.ascontiguousarray(prior, dtype=np.int8)
+        if pk.shape != (d, d) or not np.isin(pk, (-1, 0, 1)).all():
+            raise OracleError(1, "causal_order: prior must be [d, d] with entries -1, 0, 1")
+        code = _load().oracle_causal_order_prior(
+            _pd(X), n, d, int(bool(literal)), int(threads or default_threads()),
+            pk.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), order.ctypes.data_as(P32),
+            _pd(sc) if sc is not None else None, int(max_steps))
     _check(code, "causal_order")
     return (order, sc) if scores else order
 

@@ -423,8 +423,51 @@ int oracle_row_scores(const double *R, int64_t n, int64_t ldr, const int32_t *U,
  *   max_steps  if > 0, stop after that many search steps (order entries past
  *          them are -1); used to time a bounded sample of a run.
  */
+/*
+ * Prior knowledge of ancestry (not in the paper; the DirectLiNGAM literature
+ * lets a user state known causal relations, and this is the reading used
+ * here).  prior[i * d + j] = 1: x_j is known to be an ancestor of x_i (a
+ * directed path j -> i); 0: x_j is known not to be an ancestor of x_i; -1:
+ * unknown; the diagonal is ignored.  At each step, among the remaining
+ * variables U:
+ *   - i may be chosen only if no other remaining j is a known ancestor of it;
+ *   - if some remaining i has every other remaining j known not to be an
+ *     ancestor (known exogenous among U), the choice is restricted to those.
+ * The scores k_list are computed as without prior knowledge; the argmax
+ * (ties to the first position) runs over the allowed positions only.  No
+ * allowed position (contradictory knowledge) is ORACLE_ERR_ARG.
+ */
+static int prior_allowed(const int8_t *prior, int64_t d, const int32_t *U, int64_t p,
+                         unsigned char *allow)
+{
+    int any_exo = 0, any = 0;
+    for (int64_t a = 0; a < p; ++a) {
+        int anc = 0, exo = 1;
+        for (int64_t b = 0; b < p; ++b) {
+            if (b == a) continue;
+            const int8_t v = prior[(int64_t)U[a] * d + U[b]];
+            anc |= v == 1;
+            exo &= v == 0;
+        }
+        allow[a] = (unsigned char)((anc ? 0 : 1) | (exo && !anc ? 2 : 0));
+        any_exo |= (allow[a] & 2) != 0;
+    }
+    for (int64_t a = 0; a < p; ++a) {
+        allow[a] = any_exo ? (allow[a] & 2) != 0 : (allow[a] & 1) != 0;
+        any |= allow[a];
+    }
+    return any ? ORACLE_OK : ORACLE_ERR_ARG;
+}
+
 int oracle_causal_order(const double *X, int64_t n, int64_t d, int literal, int nthreads,
                         int32_t *order, double *scores, int64_t max_steps)
+{
+    return oracle_causal_order_prior(X, n, d, literal, nthreads, NULL, order, scores, max_steps);
+}
+
+int oracle_causal_order_prior(const double *X, int64_t n, int64_t d, int literal, int nthreads,
+                              const int8_t *prior, int32_t *order, double *scores,
+                              int64_t max_steps)
 {
     if (!X || !order || n < 2 || d < 1) return ORACLE_ERR_ARG;
     for (int64_t k = 0; k < n * d; ++k)
@@ -435,8 +478,9 @@ int oracle_causal_order(const double *X, int64_t n, int64_t d, int literal, int 
     double *kl = (double *)malloc(sizeof(double) * (size_t)d);
     double *ref = (double *)malloc(sizeof(double) * (size_t)d);
     double *tmp = (double *)malloc(sizeof(double) * (size_t)n * 2);
-    if (!R || !U || !kl || !ref || !tmp) {
-        free(R); free(U); free(kl); free(ref); free(tmp);
+    unsigned char *allow = (unsigned char *)malloc((size_t)d);
+    if (!R || !U || !kl || !ref || !tmp || !allow) {
+        free(R); free(U); free(kl); free(ref); free(tmp); free(allow);
         return ORACLE_ERR_NOMEM;
     }
     for (int64_t i = 0; i < d; ++i) {
@@ -455,6 +499,13 @@ int oracle_causal_order(const double *X, int64_t n, int64_t d, int literal, int 
         int mpos = 0;
         status = oracle_search_step(R, n, n, U, p, ref, literal, nthreads, kl, NULL, NULL, &mpos);
         if (status) break;
+        if (prior) {
+            status = prior_allowed(prior, d, U, p, allow);
+            if (status) break;
+            mpos = -1;
+            for (int64_t a = 0; a < p; ++a)
+                if (allow[a] && (mpos < 0 || kl[a] > kl[mpos])) mpos = (int)a;
+        }
         if (scores)
             for (int64_t a = 0; a < p; ++a) scores[t * d + U[a]] = kl[a];
         int32_t m = U[mpos];
@@ -475,7 +526,7 @@ int oracle_causal_order(const double *X, int64_t n, int64_t d, int literal, int 
         order[t] = U[0];
         if (scores) scores[t * d + U[0]] = 0.0;
     }
-    free(R); free(U); free(kl); free(ref); free(tmp);
+    free(R); free(U); free(kl); free(ref); free(tmp); free(allow);
     return status;
 }
 
