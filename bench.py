@@ -119,6 +119,77 @@ def oracle_sample_step(X, p_sample: int, threads: int):
     return units, dt
 
 
+def run_readouts(pkg, torch, dev, X3, order3, batch):
+    """The read-outs of the estimated graph (total effects, influence, bootstrap
+    edge statistics, adaptive-lasso pruning) through the public API, each
+    against the oracle on the same input (a bounded sample where the oracle is
+    slow).  Host-API timings: the copies are inside."""
+    import oracle
+
+    def wall(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t) / reps * 1e3
+
+    def cpu(fn):
+        t = time.perf_counter()
+        out = fn()
+        return out, (time.perf_counter() - t) * 1e3
+
+    res = {}
+    with pkg.Context(dev, "mixed") as ctx:
+        # total effects and influence at d = 1000
+        B = ctx.fit_adjacency(X3, order3)
+        T, ms = wall(lambda: ctx.total_effects(B, order3), 5)
+        Tref, oms = cpu(lambda: oracle.total_effects(B))
+        (ex, rc, _, _), ims = wall(lambda: ctx.influence(T), 5)
+        (oex, orc), oims = cpu(lambda: oracle.influence(Tref))
+        res["total_effects"] = {"workload": "T = (I - B)^-1, d=1000 (adjacency of the headline order)",
+                                "ms": ms, "oracle_ms": oms,
+                                "max_abs_diff": float(np.max(np.abs(T - Tref)))}
+        res["influence"] = {"workload": "exerted / received influence and ranks, d=1000",
+                            "ms": ims, "oracle_ms": oims,
+                            "max_abs_diff": float(max(np.max(np.abs(ex - oex)),
+                                                      np.max(np.abs(rc - orc))))}
+        # bootstrap edge statistics over the 128 resamples of the batch
+        _, Bs = ctx.causal_order_batch(batch[:128], adjacency=True)
+        (pr, mean), ems = wall(lambda: ctx.bootstrap_edge_stats(Bs), 5)
+        (opr, omean), oems = cpu(lambda: oracle.bootstrap_edge_stats(Bs))
+        res["bootstrap_edge_stats"] = {"workload": "128 resamples of d=200, n=4000",
+                                       "ms": ems, "oracle_ms": oems,
+                                       "max_abs_diff": float(max(np.max(np.abs(pr - opr)),
+                                                                 np.max(np.abs(mean - omean))))}
+        # adaptive-lasso + BIC pruning at d = 100, n = 5000: every row on the
+        # GPU; the oracle (pure-Python coordinate descent) on three rows
+        ds2 = gen.cfg2()
+        X2 = torch.from_numpy(ds2.X).to(f"cuda:{dev}")
+        o2 = ctx.causal_order(X2)
+        Bp, pms = wall(lambda: ctx.prune_adjacency(X2, o2), 3)
+        Xd = ds2.X.astype(np.float64)
+        Xc = Xd - Xd.mean(axis=0)
+        C = Xc.T @ Xc / ds2.n
+        pos = {int(v): i for i, v in enumerate(o2)}
+        rows = [int(o2[k]) for k in (25, 50, 75)]
+        t = time.perf_counter()
+        diffs = []
+        for k in rows:
+            pred = np.asarray(o2[:pos[k]], dtype=np.int64)
+            b = oracle.adaptive_lasso_row(C, k, pred, ds2.n)
+            diffs.append(float(np.max(np.abs(Bp[k, pred] - b))))
+        orow = (time.perf_counter() - t) / len(rows)
+        res["prune"] = {"workload": "adaptive lasso + BIC of every variable on its predecessors, "
+                                    "cfg2 d=100 n=5000",
+                        "ms": pms, "rows_per_s": ds2.d / (pms * 1e-3),
+                        "oracle_rows_per_s": 1.0 / orow,
+                        "oracle_sample": "rows at order positions 25, 50, 75",
+                        "max_abs_diff_sample_rows": max(diffs)}
+    return res
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -181,9 +252,9 @@ def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float)
 # the roofline reports traffic null until the capture is repeated.
 PAIR_TRAFFIC = {"bytes_per_launch": 23.08e6, "launches": 968, "tile": 10,
                 "sources": ["paper_2403_03772_gb300/csrc/kernels_pair.cu",
-                            "paper_2403_03772_gb300/csrc/kernels.cuh",
+                            "paper_2403_03772_gb300/csrc/pair.cuh",
                             "paper_2403_03772_gb300/csrc/common.cuh"],
-                "sha256": "067664f69b9f6b65a32c577f7f119d1b6303a5d0278aa717281a82c196e96250"}
+                "sha256": "5c5f043fa48c5ebcbbcc1326907d825be0425aeeb42c12fbfd19baedb30160ae"}
 
 
 def pair_traffic(tiles):
@@ -332,12 +403,14 @@ def run_ours(args, rank, world):
                            "genuine_ties": stats[-1]["genuine_ties"],
                            "graph_nodes": stats[-1]["graph_nodes"],
                            "order_head": [int(v) for v in order[:8]],
+                           "order": order,
                            "tuning": ({k: tunings[prec][k] for k in ("p_max", "tile", "ctas_per_sm")}
                                       if prec in tunings else None)}
     # batched form: the bootstrap workload (128 resamples of d=200, n=4000 plus
     # 64 uneven instances) in one call, against the same instances ordered one
     # call at a time with the plain FP32 form
     batch_info = None
+    batch = None
     if args.batched:
         insts = gen.cfg5(seed=rank_seed(gen.SEEDS[5], rank))
         batch = [(torch.from_numpy(np.ascontiguousarray(b.X)).to(f"cuda:{dev}"), b.rows)
@@ -506,6 +579,13 @@ def run_ours(args, rank, world):
                "sample": f"first ordering step of Algorithm 1 over the first {args.cpu_p} of the "
                          f"1000 variables, n=10000 ({units:.3e} residual-samples, {dt:.1f} s)"}
 
+    readouts = None
+    if world == 1 and args.readouts:
+        if batch is None:
+            batch = [(torch.from_numpy(np.ascontiguousarray(b.X)).to(f"cuda:{dev}"), b.rows)
+                     for b in gen.cfg5()]
+        readouts = run_readouts(pkg, torch, dev, X, forms[head]["order"], batch)
+
     ms_per_step = tot_ms[head] / args.steps
     value = job_throughput(W, world, args.steps, tot_ms[head])
     launches_per_step = f["graph_nodes"] + 2
@@ -531,6 +611,7 @@ def run_ours(args, rank, world):
                       "order_head": forms[p]["order_head"]} for p in args.forms},
         "batched": batch_info,
         "long_n": long_info,
+        "readouts": readouts,
         "timed_region_s": region_s,
     }
     print(json.dumps(line), flush=True)
@@ -551,6 +632,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-long-n", dest="long_n", action="store_false")
+    ap.add_argument("--no-readouts", dest="readouts", action="store_false",
+                    help="skip the timings of total effects, influence, edge statistics, pruning")
     ap.add_argument("--one-order", action="store_true",
                     help="run one profiler-bracketed order of the headline workload and exit")
     ap.add_argument("--workload", choices=["cfg3", "long_n", "cfg2", "batch"], default="cfg3",

@@ -295,6 +295,24 @@ lingam_status lingam_set_tuning(lingam_ctx *ctx, const lingam_tuning *t);
  * tile 0, 4 CTAs per SM). */
 lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam_tuning *out);
 
+/*
+ * Prior knowledge of ancestry for the following ordering calls on ctx
+ * (lingam_causal_order, lingam_causal_order_batch, varlingam_fit on the
+ * innovations).  prior: host int8 [d][d] row-major, copied; prior[i*d + j] =
+ * 1 if x_j is known to be an ancestor of x_i (a directed path j -> i), 0 if
+ * known not to be, -1 if unknown; the diagonal is ignored.  NULL or d = 0
+ * clears it.  The paper has no prior knowledge; the rule follows the
+ * DirectLiNGAM literature's use of such a matrix: at each step a variable may
+ * be chosen only if no remaining variable is a known ancestor of it, and
+ * only among the known-exogenous remaining variables (every other remaining
+ * one known not to be an ancestor) when there are any; the scores M(i) are
+ * unchanged.  Every input of a later ordering call must have this d
+ * (LINGAM_ERR_ARG otherwise), and knowledge that leaves no variable to choose
+ * makes that call return LINGAM_ERR_ARG.  LINGAM_ERR_ARG here for entries
+ * outside {-1, 0, 1} or d outside 1..6000.
+ */
+lingam_status lingam_set_prior_knowledge(lingam_ctx *ctx, const int8_t *prior, int64_t d);
+
 /* Number of pair-kernel tile configurations. */
 #define LINGAM_PAIR_TILES 13
 

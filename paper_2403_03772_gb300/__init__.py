@@ -106,6 +106,7 @@ SIGNATURES = {
     "lingam_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "lingam_get_tuning": (_I32, [_P, _I32, ctypes.POINTER(Tuning)]),
     "lingam_pair_tile_info": (_I32, [_I32, ctypes.POINTER(_I32)]),
+    "lingam_set_prior_knowledge": (_I32, [_P, ctypes.POINTER(ctypes.c_int8), _I64]),
 }
 
 
@@ -426,6 +427,19 @@ class Context:
     def set_tuning(self, table: dict):
         t = Tuning.from_dict(table)
         self._check(self._lib.lingam_set_tuning(self._h, ctypes.byref(t)))
+
+    def set_prior_knowledge(self, prior=None):
+        """Ancestry knowledge for later orderings: [d, d] with prior[i, j] = 1
+        if x_j is known to be an ancestor of x_i, 0 if known not to be, -1
+        unknown; None clears it."""
+        if prior is None:
+            self._check(self._lib.lingam_set_prior_knowledge(self._h, None, 0))
+            return
+        pk = np.ascontiguousarray(np.asarray(prior), dtype=np.int8)
+        if pk.ndim != 2 or pk.shape[0] != pk.shape[1]:
+            raise LingamError(1, "prior knowledge must be a square [d, d] matrix")
+        self._check(self._lib.lingam_set_prior_knowledge(
+            self._h, pk.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), pk.shape[0]))
 
     def peak_probe(self, which: int):
         """(ops per second, SM MHz) of unit `which`: 0 FP32 FMA flop/s,

@@ -21,8 +21,8 @@ OBJDIR = os.path.join(ROOT, "_build", "obj")
 LIBNAME = "liblingam_gb300.so"
 LIBPATH = os.path.join(LIBDIR, LIBNAME)
 
-SOURCES = ["kernels_pair.cu", "kernels_prep.cu", "kernels_refine.cu", "kernels_gram_tc.cu",
-           "kernels_effects.cu",
+SOURCES = ["kernels_pair.cu", "kernels_score.cu", "kernels_prep.cu", "kernels_refine.cu",
+           "kernels_gram_tc.cu", "kernels_effects.cu",
            "lingam_abi.cu", "lingam_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -104,6 +104,7 @@ struct InstDev {
     double *fhz = nullptr, *lcoef = nullptr, *isd0 = nullptr, *isd1 = nullptr;
     float *I32 = nullptr;
     int32_t *U0 = nullptr, *U1 = nullptr, *order = nullptr, *scratch = nullptr, *rows = nullptr;
+    uint8_t *allow = nullptr;   // positions the prior knowledge allows at the step
     DevState *state = nullptr;
     int zrow = 0;
     int ksplit = 1;
@@ -153,6 +154,8 @@ struct lingam_ctx {
     Buf eIn, eIn2, eL, eW, eT, ePos, eOrd, ePtr, eOut, eStatus;
     lingam_stats stats{};
     lingam_tuning tune[2]{};   // pair-kernel choices: [0] accurate (FP32), [1] fast (MIXED)
+    Buf prior;                 // prior ancestry knowledge [prior_d][prior_d] int8, or none
+    int64_t prior_d = 0;
 };
 
 static std::string g_create_error;
@@ -397,7 +400,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     };
     struct Off {
         size_t R, C, Cpart, mom, hz, M, E, hist, ref, fmom, fhz, lcoef, U, order, scratch, rows,
-            state, isd, I32, S, expo, cand, cdbl;
+            state, isd, I32, S, expo, cand, cdbl, allow;
     };
     std::vector<Off> o(K);
     for (int k = 0; k < K; ++k) {
@@ -427,6 +430,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].I32 = take((size_t)d * d * 4);
         o[k].cand = take((size_t)d * 4);
         o[k].cdbl = take((size_t)3 * d * 8);
+        o[k].allow = take((size_t)d);
 
     }
     CK(ensure(pl.arena, off));
@@ -464,6 +468,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         I.isd0 = reinterpret_cast<double *>(base + o[k].isd);
         I.isd1 = I.isd0 + d;
         I.I32 = reinterpret_cast<float *>(base + o[k].I32);
+        I.allow = reinterpret_cast<uint8_t *>(base + o[k].allow);
 
         {   // candidate arrays of the device state
             DevState h{};
@@ -781,7 +786,9 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             sc.push_back(S);
             // candidates of an FP32-scored step go to double-float first; a
             // step scored in double-float sends its near-ties to FP64
-            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 1});
+            se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 1,
+                                      ctx->prior_d > 0 ? (const int8_t *)ctx->prior.p : nullptr,
+                                      ctx->prior_d, I.allow});
             fd1.push_back(hpp(1, 1, I.fmom));
             fd2.push_back(hpp(1, 0, I.fmom));
             f64.push_back(hpp(1, 1, I.fmom));
@@ -1021,6 +1028,12 @@ static lingam_status ensure_plan(lingam_ctx *ctx, const std::vector<InstSpec> &s
 {
     Plan &pl = ctx->plan;
     const int prec = ctx->opts.precision;
+    if (ctx->prior_d > 0 && !stop_after_score0)
+        for (const InstSpec &sp : spec)
+            if (sp.d != ctx->prior_d)
+                return fail(ctx, LINGAM_ERR_ARG,
+                            "prior knowledge is set for d = " + std::to_string(ctx->prior_d) +
+                                " but an input has d = " + std::to_string(sp.d));
     const bool same_layout = pl.arena.p && pl.spec == spec && pl.prec == prec &&
                              pl.scores == (int)scores && pl.lcoef == (int)lcoef &&
                              pl.rows == (int)rows;
@@ -1263,7 +1276,7 @@ lingam_status lingam_destroy(lingam_ctx *ctx)
                   &ctx->aW,     &ctx->aPiv, &ctx->aM,   &ctx->aBt,     &ctx->aRef,
                   &ctx->aStatus, &ctx->eIn, &ctx->eIn2, &ctx->eL,      &ctx->eW,
                   &ctx->eT,     &ctx->ePos, &ctx->eOrd, &ctx->ePtr,    &ctx->eOut,
-                  &ctx->eStatus};
+                  &ctx->eStatus, &ctx->prior};
     for (Buf *b : aux) release(*b);
     cudaEvent_t evs[] = {ctx->e0, ctx->e1, ctx->g0, ctx->g1};
     for (cudaEvent_t ev : evs)
@@ -1838,6 +1851,28 @@ lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam
     if (!ctx || !out) return LINGAM_ERR_ARG;
     if (precision != LINGAM_PREC_FP32 && precision != LINGAM_PREC_MIXED) return LINGAM_ERR_ARG;
     *out = ctx->tune[precision == LINGAM_PREC_MIXED ? 1 : 0];
+    return LINGAM_OK;
+}
+
+lingam_status lingam_set_prior_knowledge(lingam_ctx *ctx, const int8_t *prior, int64_t d)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    if (!prior || d == 0) {
+        ctx->prior_d = 0;
+    } else {
+        if (d < 1 || d > 6000) return fail(ctx, LINGAM_ERR_ARG, "prior knowledge: need 1 <= d <= 6000");
+        for (int64_t k = 0; k < d * d; ++k)
+            if (prior[k] < -1 || prior[k] > 1)
+                return fail(ctx, LINGAM_ERR_ARG, "prior knowledge entries must be -1, 0 or 1");
+        CK(cudaSetDevice(ctx->device));
+        CK(ensure(ctx->prior, (size_t)(d * d)));
+        CK(cudaMemcpyAsync(ctx->prior.p, prior, (size_t)(d * d), cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        ctx->prior_d = d;
+    }
+    // the step graph holds the selection's parameters: capture it again
+    if (ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
+    ctx->plan.exec = nullptr;
     return LINGAM_OK;
 }
 

@@ -1,0 +1,68 @@
+// pair.cuh -- tile configurations and parameters of the FP32 pair-moment
+// kernel (kernels_pair.cu); shared with the host planner and the autotuner.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lg {
+
+// Tile configurations of the FP32 pair-moment kernel.  A warp owns wi x wj
+// ordered pairs (i, j) and its 32 lanes split the samples; wgi x wgj warps
+// form the CTA tile (wi wgi) x (wj wgj); `stages` chunk buffers of PAIR_S
+// samples sit in shared memory, filled by TMA (thread 0 issues the copies).
+// The register caps set how many CTAs share an SM in each form.  The
+// autotuner picks a configuration and a split schedule per range of p.
+struct PairCfg {
+    int wi, wj, wgi, wgj, stages;
+    int reg_fast, reg_acc;   // register cap per thread (fast / accurate form)
+    int groups;              // groups of 4 samples per lane and iteration (1 or 2)
+    int fold;                // chunks between compensated folds of the FP32 partial sums
+    int packed;              // fast form: two samples per paired-FP32 instruction
+    constexpr int ti() const { return wi * wgi; }
+    constexpr int tj() const { return wj * wgj; }
+    constexpr int warps() const { return wgi * wgj; }
+    constexpr int threads() const { return 32 * wgi * wgj; }
+};
+constexpr PairCfg PAIR_CFGS[] = {
+    {4, 4, 2, 4, 4, 248, 128, 1, 4},   // 0: 256 threads, 8 x 16 tile
+    {4, 4, 1, 4, 3, 168, 128, 1, 4},   // 1: 128 threads, 4 x 16 tile
+    {4, 2, 2, 4, 4, 128, 96, 1, 4},    // 2: 256 threads, 8 x 8 tile
+    {2, 4, 2, 4, 4, 128, 96, 1, 4},    // 3: 256 threads, 4 x 16 tile
+    {4, 4, 2, 2, 4, 168, 128, 1, 4},   // 4: 128 threads, 8 x 8 tile
+    {4, 4, 1, 4, 3, 168, 168, 2, 4},   // 5: as 1, 8 samples per lane and iteration
+    {4, 2, 1, 4, 3, 128, 96, 2, 4},    // 6: 128 threads, 4 x 8 tile, 8 samples per lane
+    {4, 2, 2, 4, 4, 128, 96, 2, 4},    // 7: as 2, 8 samples per lane
+    {2, 4, 2, 4, 4, 128, 96, 2, 4},    // 8: as 3, 8 samples per lane
+    {4, 2, 1, 4, 3, 128, 96, 2, 8},    // 9: as 6, folds every 8 chunks
+    {4, 2, 1, 4, 3, 128, 96, 2, 8, 1}, // 10: as 9, paired FP32 (f32x2) arithmetic
+    {4, 4, 1, 4, 3, 168, 168, 2, 8, 1},// 11: as 5, paired, folds every 8 chunks
+    {4, 2, 2, 4, 4, 128, 96, 2, 8, 1}, // 12: as 7, paired, folds every 8 chunks
+};
+constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
+constexpr int PAIR_S = 256;                  // samples per TMA chunk
+
+// Scale folded into the fast-form residual: u~ = KSC * u makes
+// 2^(-u~^2) = exp(-u^2/2).
+constexpr double KSC = 0.84932180028801904272;   // sqrt(log2(e) / 2)
+
+enum PairMode { PAIR_ACCURATE = 0, PAIR_FAST = 1 };
+
+struct PairParams {
+    const double *C;      // FP64 covariance of the residual data, [d][ldc]
+    int64_t ldc;
+    const int32_t *U;     // position -> original variable, p entries
+    int p, n;
+    int tiles_i, tiles_j;
+    int nchunks;          // ceil(n / PAIR_S)
+    int cps;              // chunks per sample split
+    int nsplit;
+    float2 *mom;          // out [nsplit][p][p][2] moment sums of entry (i, j), each as a
+                          // double-float (hi, lo)
+    uint32_t *status;
+    int row0;             // first row of this instance in the z tensor
+    const double *isd;    // [p] 1 / sqrt(C_ii) by position
+};
+
+}  // namespace lg
