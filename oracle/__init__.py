@@ -347,7 +347,7 @@ def bootstrap_edge_stats(Bs, threshold: float = 0.0) -> tuple[np.ndarray, np.nda
 # ------------------------------------------------------- sparse adjacency ---
 
 def adaptive_lasso_path(C, k, pred, n: int, gamma: float = 1.0, n_lambda: int = 60,
-                        eps: float = 1e-6, tol: float = 1e-10, max_sweeps: int = 100000):
+                        eps: float = 1e-6, max_events: int | None = None):
     """Sparse regression of variable k on its predecessors ``pred`` (the paper
     only says "regressing"; this is the reading for pruned output): the
     adaptive lasso of Zou (2006) in covariance form,
@@ -355,14 +355,22 @@ def adaptive_lasso_path(C, k, pred, n: int, gamma: float = 1.0, n_lambda: int = 
         min_b  1/2 b' C_PP b - b' C_Pk + lam sum_j w_j |b_j|,
         w_j = |b_ols_j|^-gamma,  b_ols = C_PP^-1 C_Pk,
 
-    on C = Xc'Xc / n.  Cyclic coordinate descent over ``pred`` in the given
-    order, b_j <- S(C_jk - sum_{l != j} C_jl b_l, lam w_j) / C_jj with S the
-    soft threshold, warm-started along lam_i = lam_max eps^(i / (L - 1)),
-    lam_max = (1 + 1e-9) max_j |C_jk| / w_j, i = 0 .. L-1; a lam's descent stops after
-    the first sweep whose largest change |db_j| sqrt(C_jj) is at most
-    tol sqrt(C_kk).  Each path point carries BIC = n log(RSS/n) + df log n
-    with RSS/n = C_kk - 2 b'C_Pk + b'C_PP b and df the nonzeros.
-    Returns [(lam, b, bic)] over the grid (empty when b = 0 for every lam)."""
+    on C = Xc'Xc / n, at lam_i = lam_max eps^(i / (L - 1)), i = 0 .. L-1,
+    lam_max = (1 + 1e-9) max_j |C_jk| / w_j.  With beta_j = w_j b_j it is a
+    plain lasso on Ct = D C_PP D, ct = D C_Pk, D = diag(1 / w), whose
+    minimiser (unique: C_PP is positive definite) is piecewise linear in lam.
+    The path is followed exactly by the homotopy of Osborne, Presnell and
+    Turlach (2000) / the lasso form of LARS (Efron et al. 2004): with the
+    active set A and signs s_A, beta_A = Ct_AA^-1 (ct_A - lam s_A) and the
+    correlations rho = ct - Ct beta satisfy rho_A = lam s_A, |rho_j| <= lam
+    off A; lam decreases to the next of: an inactive |rho_j| reaching lam
+    (j joins with the sign of rho_j), an active beta_j reaching 0 (j leaves),
+    or the next grid value (a path point).  A variable is not dropped in the
+    event right after it joined nor re-joined right after it left (rounding
+    puts it a hair off the boundary).  Variables with b_ols_j = 0 stay 0.
+    Each path point carries BIC = n log(RSS/n) + df log n with
+    RSS/n = C_kk - 2 b'C_Pk + b'C_PP b and df the nonzeros.
+    Returns [(lam, b, bic)] over the grid (empty when lam_max is 0)."""
     C = _f64(C)
     pred = np.asarray(pred, dtype=np.int64)
     q = pred.size
@@ -372,49 +380,90 @@ def adaptive_lasso_path(C, k, pred, n: int, gamma: float = 1.0, n_lambda: int = 
     cpk = C[pred, k]
     ckk = C[k, k]
     b_ols = np.linalg.solve(Cpp, cpk)
-    with np.errstate(divide="ignore"):
-        w = np.where(b_ols != 0.0, np.abs(b_ols) ** -gamma, np.inf)
-    # 1e-9 above the exact boundary, so that rounding cannot leave a 1e-19
-    # coefficient (counted as an edge by BIC) at the first grid point
-    lam_max = np.max(np.where(np.isfinite(w), np.abs(cpk) / w, 0.0)) * (1.0 + 1e-9)
+    use = b_ols != 0.0
+    D = np.where(use, np.abs(np.where(use, b_ols, 1.0)) ** gamma, 0.0)   # 1 / w
+    Ct = Cpp * np.outer(D, D)
+    ct = cpk * D
+    lam_top = float(np.max(np.abs(ct)))
+    lam_max = lam_top * (1.0 + 1e-9)
     if not lam_max > 0.0:
         return []
-    b = np.zeros(q)
+    grid = lam_max * eps ** (np.arange(n_lambda) / (n_lambda - 1))
     path = []
-    stop = tol * np.sqrt(ckk)
-    for i in range(n_lambda):
-        lam = lam_max * eps ** (i / (n_lambda - 1))
-        for _ in range(max_sweeps):
-            big = 0.0
-            for j in range(q):
-                if not np.isfinite(w[j]):
-                    continue
-                r = cpk[j] - (Cpp[j] @ b - Cpp[j, j] * b[j])
-                t = lam * w[j]
-                nb = (np.sign(r) * (abs(r) - t) if abs(r) > t else 0.0) / Cpp[j, j]
-                big = max(big, abs(nb - b[j]) * np.sqrt(Cpp[j, j]))
-                b[j] = nb
-            if big <= stop:
-                break
+
+    def record(lam, beta):
+        b = beta * D
         rss = ckk - 2.0 * (b @ cpk) + b @ Cpp @ b
         bic = n * np.log(max(rss, 1e-300)) + np.count_nonzero(b) * np.log(n)
-        path.append((lam, b.copy(), bic))
+        path.append((lam, b, bic))
+
+    beta = np.zeros(q)
+    gi = 0
+    while gi < n_lambda and grid[gi] >= lam_top:      # above the first join: b = 0
+        record(grid[gi], beta)
+        gi += 1
+    first = int(np.argmax(np.abs(ct)))
+    A, sign = [first], {first: 1.0 if ct[first] > 0.0 else -1.0}
+    lam, left, fresh = lam_top, -1, first
+    for _ in range(max_events or 20 * q + 100):
+        if gi >= n_lambda:
+            break
+        Ai = np.array(A)
+        sA = np.array([sign[j] for j in A])
+        G = Ct[np.ix_(Ai, Ai)]
+        bA = np.linalg.solve(G, ct[Ai] - lam * sA)
+        dA = np.linalg.solve(G, sA)            # d beta_A / d(-lam)
+        rho = ct - Ct[:, Ai] @ bA
+        a = Ct[:, Ai] @ dA                     # d rho / d lam
+        active = np.zeros(q, dtype=bool)
+        active[Ai] = True
+        step, kind, who = lam - grid[gi], "grid", -1
+        for j in range(q):
+            if active[j] or not use[j] or j == left:
+                continue
+            if abs(rho[j]) >= lam:             # on or past the boundary: joins now
+                step, kind, who = 0.0, "join", j
+                break
+            for num, den in ((lam - rho[j], 1.0 - a[j]), (lam + rho[j], 1.0 + a[j])):
+                if den > 0.0 and num / den < step:
+                    step, kind, who = num / den, "join", j
+        for t, j in enumerate(A):
+            if j != fresh and dA[t] != 0.0:
+                dl = -bA[t] / dA[t]
+                if 1e-12 * lam < dl < step:
+                    step, kind, who = dl, "drop", j
+        left = fresh = -1
+        if kind == "grid":
+            lam = grid[gi]
+            beta[:] = 0.0
+            beta[Ai] = np.linalg.solve(G, ct[Ai] - lam * sA)
+            record(lam, beta)
+            gi += 1
+        elif kind == "join":
+            lam -= step
+            sign[who] = 1.0 if rho[who] - step * a[who] > 0.0 else -1.0
+            A.append(who)
+            fresh = who
+        else:
+            lam -= step
+            A.remove(who)
+            left = who
     return path
 
 
 def adaptive_lasso_row(C, k, pred, n: int, gamma: float = 1.0, n_lambda: int = 60,
-                       eps: float = 1e-6, tol: float = 1e-10) -> np.ndarray:
+                       eps: float = 1e-6) -> np.ndarray:
     """The path point of ``adaptive_lasso_path`` with the smallest BIC (the
     first one on ties); zeros when the path is empty."""
-    path = adaptive_lasso_path(C, k, pred, n, gamma, n_lambda, eps, tol)
+    path = adaptive_lasso_path(C, k, pred, n, gamma, n_lambda, eps)
     if not path:
         return np.zeros(np.asarray(pred).size)
     best = min(range(len(path)), key=lambda i: (path[i][2], i))
     return path[best][1]
 
 
-def prune_adjacency(X, order, gamma: float = 1.0, n_lambda: int = 60, eps: float = 1e-6,
-                    tol: float = 1e-10) -> np.ndarray:
+def prune_adjacency(X, order, gamma: float = 1.0, n_lambda: int = 60,
+                    eps: float = 1e-6) -> np.ndarray:
     """Sparse weighted adjacency: ``adaptive_lasso_row`` for every variable on
     the variables before it in ``order``; B[k, pred(k)] = its coefficients."""
     X = _f64(X)
@@ -425,5 +474,5 @@ def prune_adjacency(X, order, gamma: float = 1.0, n_lambda: int = 60, eps: float
     B = np.zeros((d, d))
     for pos_k, k in enumerate(order):
         pred = order[:pos_k]
-        B[k, pred] = adaptive_lasso_row(C, k, pred, n, gamma, n_lambda, eps, tol)
+        B[k, pred] = adaptive_lasso_row(C, k, pred, n, gamma, n_lambda, eps)
     return B

@@ -32,7 +32,7 @@ def test_vanishing_penalty_gives_least_squares():
     C = Xc.T @ Xc / X.shape[0]
     k = int(ds.order[-1])
     pred = ds.order[:-1]
-    path = oracle.adaptive_lasso_path(C, k, pred, X.shape[0], eps=1e-13, n_lambda=30, tol=1e-13)
+    path = oracle.adaptive_lasso_path(C, k, pred, X.shape[0], eps=1e-13, n_lambda=30)
     ols, *_ = np.linalg.lstsq(Xc[:, pred], Xc[:, k], rcond=None)
     assert np.max(np.abs(path[-1][1] - ols)) < 1e-8
 
@@ -47,7 +47,7 @@ def test_path_point_matches_sklearn_lasso():
     X = np.column_stack([Z, y])
     Xc = X - X.mean(axis=0)
     C = Xc.T @ Xc / n
-    path = oracle.adaptive_lasso_path(C, q, np.arange(q), n, n_lambda=12, eps=1e-2, tol=1e-14)
+    path = oracle.adaptive_lasso_path(C, q, np.arange(q), n, n_lambda=12, eps=1e-2)
     b_ols = np.linalg.solve(C[:q, :q], C[:q, q])
     w = 1.0 / np.abs(b_ols)
     for lam, b, _ in path[3::3]:
@@ -81,3 +81,25 @@ def test_recovers_the_true_support_at_large_n():
         assert np.all((B != 0) | (ds.B == 0))          # no true edge is lost
         assert np.max(np.abs(B - ds.B)) < 0.05
     assert exact >= 8
+
+
+def test_every_path_point_satisfies_the_lasso_optimality_conditions():
+    # KKT of the weighted lasso at each grid lam: C_Pk - C_PP b = lam w sign(b)
+    # on the support, |C_jk - (C_PP b)_j| <= lam w_j off it
+    ds = gen.cfg2(seed=1002, n=5000, d=40)
+    X = ds.X.astype(np.float64)
+    Xc = X - X.mean(axis=0)
+    n = X.shape[0]
+    C = Xc.T @ Xc / n
+    worst = 0.0
+    for pos in range(1, ds.d):
+        k, pred = int(ds.order[pos]), ds.order[:pos]
+        cpp, cpk = C[np.ix_(pred, pred)], C[pred, k]
+        w = 1.0 / np.abs(np.linalg.solve(cpp, cpk))
+        for lam, b, _ in oracle.adaptive_lasso_path(C, k, pred, n):
+            g = cpk - cpp @ b
+            on = b != 0
+            worst = max(worst,
+                        np.max(np.abs(g[on] - lam * w[on] * np.sign(b[on])), initial=0.0) / lam,
+                        np.max(np.abs(g[~on]) - lam * w[~on], initial=0.0) / lam)
+    assert worst < 1e-6
