@@ -361,9 +361,10 @@ cudaError_t launch_var_window(const double *B0, const double *Bt, int d, int lag
                               const int32_t *order0, double *A, int32_t *order, cudaStream_t s);
 cudaError_t launch_influence(const double *T, int d, double *exert, double *receive,
                              int32_t *rank_exert, int32_t *rank_receive, cudaStream_t s);
+void prune_workspace(int d, int num_sms, int *blocks, size_t *dbl, size_t *ints);
 cudaError_t launch_prune(const double *C, const double *Bols, const int32_t *order, int d, int n,
-                         double gamma, int L, double eps, double tol, double *Cp, double *ws,
-                         double *B, cudaStream_t s);
+                         double gamma, int L, double eps, int blocks, double *Cp, double *ws,
+                         int *iws, double *B, uint32_t *status, cudaStream_t s);
 cudaError_t launch_edge_stats(const double *const *Bs, int count, int d, double threshold,
                               double *prob, double *mean, uint32_t *status, cudaStream_t s);
 

@@ -1435,12 +1435,17 @@ lingam_status lingam_prune_adjacency(lingam_ctx *ctx, const void *X, int64_t n, 
     if ((st = begin_call(ctx, user))) return st;
     uint32_t *status = nullptr;
     if ((st = adjacency_core(ctx, X, n, d, ld, layout, order, true, &status))) return st;
+    int hblocks = 1;
+    size_t wdbl = 0, wint = 0;
+    prune_workspace((int)d, ctx->num_sms, &hblocks, &wdbl, &wint);
     CK(ensure(ctx->eL, (size_t)d * d * 8));
-    CK(ensure(ctx->eW, (size_t)4 * d * d * 8));
+    CK(ensure(ctx->eW, wdbl * 8));
+    CK(ensure(ctx->ePos, wint * 4));
     CK(ensure(ctx->eT, (size_t)d * d * 8));
     CK(launch_prune(ptr<double>(ctx->eIn), ptr<double>(ctx->aW), ptr<int32_t>(ctx->aPiv), (int)d,
-                    (int)n, gamma, n_lambda, eps, 1e-10, ptr<double>(ctx->eL), ptr<double>(ctx->eW),
-                    ptr<double>(ctx->eT), ctx->s));
+                    (int)n, gamma, n_lambda, eps, hblocks, ptr<double>(ctx->eL),
+                    ptr<double>(ctx->eW), ptr<int>(ctx->ePos), ptr<double>(ctx->eT), status,
+                    ctx->s));
     CK(cudaMemcpyAsync(B_out, ctx->eT.p, (size_t)d * d * 8,
                        B_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
     uint32_t hst = 0;
