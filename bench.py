@@ -245,16 +245,16 @@ def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float)
 
 # DRAM traffic of the pair-moment kernel per launch, from one ncu capture of
 # one order of the d=1000, n=10000 workload (dram__bytes_read.sum +
-# dram__bytes_write.sum summed over its 968 k_pair_fast_b launches, tuned
-# tile 10, divided by the launches; the launch-list summary of that workload
+# dram__bytes_write.sum summed over its 968 k_pair_fast_b launches, tile 15
+# at the largest p, divided by the launches; the launch-list summary of that workload
 # under profiles/ gives the command).  It describes only the kernel source it
 # was taken on, identified by the SHA-256 of these files; after any change
 # the roofline reports traffic null until the capture is repeated.
-PAIR_TRAFFIC = {"bytes_per_launch": 23.08e6, "launches": 968, "tile": 10,
+PAIR_TRAFFIC = {"bytes_per_launch": 23.10e6, "launches": 968, "tile": 15,
                 "sources": ["paper_2403_03772_gb300/csrc/kernels_pair.cu",
                             "paper_2403_03772_gb300/csrc/pair.cuh",
                             "paper_2403_03772_gb300/csrc/common.cuh"],
-                "sha256": "5c5f043fa48c5ebcbbcc1326907d825be0425aeeb42c12fbfd19baedb30160ae"}
+                "sha256": "5ebd9a53eb6cb91f6ce3c17f98dd19c947515c59626e57d943906414fc5eff4e"}
 
 
 def pair_traffic(tiles):

@@ -314,7 +314,7 @@ lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam
 lingam_status lingam_set_prior_knowledge(lingam_ctx *ctx, const int8_t *prior, int64_t d);
 
 /* Number of pair-kernel tile configurations. */
-#define LINGAM_PAIR_TILES 13
+#define LINGAM_PAIR_TILES 16
 
 /*
  * Shape of tile configuration `tile` (no context or GPU needed): out[8] =

@@ -480,7 +480,7 @@ def lingam_step_measures(ctx: Context, X):
     return ctx.step_measures(X)
 
 
-PAIR_TILES = 13
+PAIR_TILES = 16
 _TILE_KEYS = ("wi", "wj", "wgi", "wgj", "stages", "groups", "fold", "packed")
 
 

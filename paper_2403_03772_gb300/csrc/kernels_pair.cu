@@ -423,8 +423,8 @@ struct PairTable {
     static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
-using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12>;
-static_assert(PAIR_NCFG == 13, "PairKernels lists every configuration");
+using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
+static_assert(PAIR_NCFG == 16, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {

@@ -39,6 +39,9 @@ constexpr PairCfg PAIR_CFGS[] = {
     {4, 2, 1, 4, 3, 128, 96, 2, 8, 1}, // 10: as 9, paired FP32 (f32x2) arithmetic
     {4, 4, 1, 4, 3, 168, 168, 2, 8, 1},// 11: as 5, paired, folds every 8 chunks
     {4, 2, 2, 4, 4, 128, 96, 2, 8, 1}, // 12: as 7, paired, folds every 8 chunks
+    {2, 2, 1, 4, 3, 80, 80, 2, 8, 1},  // 13: 128 threads, 2 x 8 tile, paired, 6 CTAs per SM
+    {2, 2, 2, 4, 4, 80, 80, 2, 8, 1},  // 14: 256 threads, 4 x 8 tile, paired, 3 CTAs per SM
+    {4, 2, 1, 4, 3, 96, 96, 2, 8, 1},  // 15: as 10 with 96 registers, 5 CTAs per SM
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk

@@ -52,7 +52,7 @@ def test_error_bounds_hold_with_margin(datasets, name):
     # the default tiles, the configuration with the longest plain-FP32
     # partial sums (folds every 8 chunks) and two paired-FP32 (f32x2) ones
     for prec, tile in [("fp32", None), ("mixed", None), ("mixed", 9), ("fp32", 9),
-                       ("mixed", 10), ("fp32", 12)]:
+                       ("mixed", 10), ("fp32", 12), ("mixed", 13)]:
         with pkg.Context(0, prec) as c:
             if tile is not None:
                 c.set_tuning({"count": 1, "precision": pkg.PREC[prec], "p_max": [2 ** 31 - 1],

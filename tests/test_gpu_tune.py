@@ -9,7 +9,7 @@ from gpu_util import read_golden_order, scores_close
 
 pytestmark = pytest.mark.gpu
 
-N_CFG = 13
+N_CFG = 16
 
 
 @pytest.fixture(scope="module")
