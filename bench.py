@@ -570,6 +570,23 @@ def run_ours(args, rank, world):
                                       "median SM clock of the timed region"},
                 "kernel_share": f["pair_ms"] / sum(f["ms"])}
 
+    # the streaming step (column stats + regress-out + downdate, fused in
+    # k_regress_b / k_downdate_b): algorithmic HBM bytes per (variable, sample)
+    # of a step = read R_i (8) + write R_i (8) + write z (4); R_m is read once
+    # per step and shared through L2.  Against the measured copy bandwidth.
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    reg_bytes = 20.0 * sum((p - 1) * n for p in range(2, d + 1))
+    reg_ms = f["phase_ms_per_step"]["regress_ms"]
+    secondary = {"regress_downdate": {
+        "kernels": "k_regress_b + k_downdate_b", "bound": "hbm",
+        "achieved": reg_bytes / (reg_ms * 1e-3) / 1e9 if reg_ms else None,
+        "peak": hbm, "unit": "GB/s",
+        "frac": (reg_bytes / (reg_ms * 1e-3) / 1e9 / hbm) if reg_ms and hbm else None,
+        "algorithmic_bytes_per_order": reg_bytes,
+        "note": "20 B per (variable, sample) per step; FP64 regress-out and standardisation, "
+                "of measured copy bandwidth"}}
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -612,6 +629,7 @@ def run_ours(args, rank, world):
         "batched": batch_info,
         "long_n": long_info,
         "readouts": readouts,
+        "secondary_rooflines": secondary,
         "timed_region_s": region_s,
     }
     print(json.dumps(line), flush=True)
