@@ -164,7 +164,7 @@ def run_readouts(pkg, torch, dev, X3, order3, batch):
                                        "max_abs_diff": float(max(np.max(np.abs(pr - opr)),
                                                                  np.max(np.abs(mean - omean))))}
         # adaptive-lasso + BIC pruning at d = 100, n = 5000: every row on the
-        # GPU; the oracle (pure-Python coordinate descent) on three rows
+        # GPU; the oracle (numpy homotopy) on three rows
         ds2 = gen.cfg2()
         X2 = torch.from_numpy(ds2.X).to(f"cuda:{dev}")
         o2 = ctx.causal_order(X2)

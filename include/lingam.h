@@ -188,11 +188,15 @@ lingam_status lingam_step_measures(lingam_ctx *ctx, const void *X, int64_t n, in
  * (Sec. 1); this is the pruned reading: for every variable k with
  * predecessors P, the adaptive lasso of Zou (2006) in covariance form,
  *     min_b 1/2 b'C_PP b - b'C_Pk + lam sum_j w_j |b_j|,  w_j = |b_ols_j|^-gamma,
- * on the centred FP64 covariance C = Xc'Xc/n, by cyclic coordinate descent
- * over P in order, warm-started along lam_i = lam_max eps^(i/(n_lambda-1)),
- * i = 0..n_lambda-1 (lam_max = (1 + 1e-9) max_j |C_jk| / w_j), each lam's sweeps ending
- * once the largest change |db_j| sqrt(C_jj) <= 1e-10 sqrt(C_kk); the lam with
- * the smallest BIC = n log(RSS/n) + df log n (first minimum) gives row k.
+ * on the centred FP64 covariance C = Xc'Xc/n, at lam_i = lam_max
+ * eps^(i/(n_lambda-1)), i = 0..n_lambda-1 (lam_max = (1 + 1e-9) max_j
+ * |C_jk| / w_j).  Each point is the exact minimiser, the path being followed
+ * by homotopy (the lasso form of LARS: joins and drops of the active set,
+ * the active Gram's inverse updated in place); the lam with the smallest
+ * BIC = n log(RSS/n) + df log n (first minimum) gives row k.  Variables with
+ * b_ols_j = 0 keep b_j = 0.  LINGAM_ERR_DEGENERATE if the active Gram stops
+ * being positive definite or a row's path does not end within 20 q + 100
+ * events (q predecessors).
  *   X, n, d, ld, layout, order: as lingam_fit_adjacency.
  *   gamma > 0 (1 is usual), 2 <= n_lambda <= 1000, 0 < eps < 1 (60, 1e-6
  *   are the library's test settings).

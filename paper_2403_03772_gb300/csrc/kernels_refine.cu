@@ -39,8 +39,8 @@ namespace lg {
 // polynomial.  Beyond a = 9, phi(a) = exp(-2a) to 1e-16 and psi(a) < 3e-17
 // come from the FP32 exponential.  A host emulation of these steps in FP32
 // against 40-digit values shows at most 1e-14 absolute error per term, with
-// no bias (the route through exp and log1p by Tang's table methods, used
-// before, showed 3e-14).
+// no bias (an earlier route through exp and log1p by P. T. P. Tang's
+// table-driven methods showed 3e-14).
 constexpr int TT_STEP = 128;                  // nodes per unit of a
 constexpr int TT_ROWS = 9 * TT_STEP + 1;      // c_k = k / 128, k <= 1152
 
