@@ -499,11 +499,14 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
         h64[j] = neg_entropy_part(s1 * invn - LN2_D, s2 * invn);
     }
     __syncthreads();
+    // one candidate at a time over the whole block (its entries split over
+    // all threads, fixed-order block sums): a pass often has only two
+    __shared__ double s_acc[8], s_err[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = cb + w; c < ce; c += nw) {
+    for (int c = cb; c < ce; ++c) {
         const int pc = st->cand[c];
         double acc = 0.0, err = 0.0;
-        for (int j = lane; j < P.p; j += 32) {
+        for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
             if (j == pc) continue;
             const size_t rec = ((size_t)c * P.p + j) * 4;
             if (P.mom[rec] < 0.0) continue;     // skipped entry (marker in range 0)
@@ -521,11 +524,21 @@ __global__ void __launch_bounds__(256) k_refine_select_b(const RefineSelectParam
         acc = warp_sum_xor(acc);
         err = warp_sum_xor(err);
         if (lane == 0) {
-            st->mhp[c] = -acc;
-            st->ehp[c] = err;
+            s_acc[w] = acc;
+            s_err[w] = err;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ta = 0.0, te = 0.0;
+            for (int k = 0; k < nw; ++k) {
+                ta += s_acc[k];
+                te += s_err[k];
+            }
+            st->mhp[c] = -ta;
+            st->ehp[c] = te;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (threadIdx.x != 0) return;
     int best = 0;
     for (int c = 1; c < ce; ++c)
