@@ -412,6 +412,8 @@ cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStrea
 // z_lo = fl32(R_i / sigma_i - z_hi) with the same FP64 product the regress
 // kernel rounded to z_hi; only for steps that re-score (state routed to the
 // double-float tier) or score every pair in double-float (`always`).
+constexpr int ZLO_CHUNK = 2048;   // samples per work item of k_zlo_b
+
 __global__ void __launch_bounds__(256) k_zlo_b(const ZloParams *__restrict__ Ps, int count)
 {
     __shared__ int s_act[256];
@@ -426,14 +428,21 @@ __global__ void __launch_bounds__(256) k_zlo_b(const ZloParams *__restrict__ Ps,
             },
             s_act, s_wcnt);
         for (int i = 0; i < nact; ++i) {
+            // work items of (column, range of ZLO_CHUNK samples), one per block
+            // at a time: no 64-bit division per element, and every block busy
+            // whether p is large or n is
             const ZloParams &P = Ps[s_act[i]];
-            const int64_t total = (int64_t)P.p * P.n;
-            for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-                 e += (int64_t)gridDim.x * blockDim.x) {
-                const int a = (int)(e / P.n), s = (int)(e % P.n);
-                const double zx = P.R[(int64_t)P.U[a] * P.ldr + s] * P.isd[a];
-                const int64_t q = (int64_t)a * P.ldz + s;
-                P.zlo[q] = (float)(zx - (double)P.zhi[q]);
+            const int chunks = (P.n + ZLO_CHUNK - 1) / ZLO_CHUNK;
+            const int64_t items = (int64_t)P.p * chunks;
+            for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+                const int a = (int)(it / chunks), c = (int)(it % chunks);
+                const double *r = P.R + (int64_t)P.U[a] * P.ldr;
+                const double isd = P.isd[a];
+                const float *zh = P.zhi + (int64_t)a * P.ldz;
+                float *zl = P.zlo + (int64_t)a * P.ldz;
+                const int s1 = min(P.n, (c + 1) * ZLO_CHUNK);
+                for (int s = c * ZLO_CHUNK + threadIdx.x; s < s1; s += blockDim.x)
+                    zl[s] = (float)__dsub_rn(__dmul_rn(r[s], isd), (double)zh[s]);
             }
         }
         __syncthreads();   // s_act is rewritten by the next chunk
