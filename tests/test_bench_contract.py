@@ -1,0 +1,29 @@
+"""bench.py's host-side contract pieces that need no GPU: the recorded DRAM
+traffic of the pair kernel is reported only for the sources and tile it was
+measured on, and the work count matches its closed form."""
+import copy
+
+import bench
+import gen
+
+
+def test_traffic_is_reported_only_for_the_measured_sources_and_tile():
+    rec = bench.PAIR_TRAFFIC
+    assert bench.pair_traffic([13, 13, 13, 15, rec["tile"]]) == rec["bytes_per_launch"]
+    other = (rec["tile"] + 1) % 16
+    assert bench.pair_traffic([rec["tile"], other]) is None
+    assert bench.pair_traffic([]) is None
+    saved = copy.deepcopy(rec)
+    try:
+        rec["sha256"] = "0" * 64            # the kernel source changed since the capture
+        assert bench.pair_traffic([rec["tile"]]) is None
+        rec["sources"] = rec["sources"] + ["no/such/file.cu"]
+        assert bench.pair_traffic([rec["tile"]]) is None
+    finally:
+        bench.PAIR_TRAFFIC.clear()
+        bench.PAIR_TRAFFIC.update(saved)
+
+
+def test_work_count_is_the_sum_over_steps():
+    for d, n in [(10, 1000), (100, 5000), (1000, 10000)]:
+        assert gen.residual_samples(d, n) == n * sum(p * (p - 1) for p in range(2, d + 1))
