@@ -383,11 +383,17 @@ lingam_status lingam_peak_probe(lingam_ctx *ctx, int32_t which, double *ops_per_
  * Limits: 2 <= d <= 64 (the scratch array's size), 2 <= n <= 2^30; anything
  * else returns LINGAM_ERR_ARG without touching the GPU.  NaN/Inf input gives
  * LINGAM_ERR_NONFINITE, a zero variance or |rho| = 1 LINGAM_ERR_DEGENERATE.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
- * on one GPU share the array (the call clears what must start at zero), so
- * calls that overlap in time on the same GPU race and must be serialised by
- * the caller.
+ * Each call looks up the array's device address with the caller's device
+ * current.  Under CUDA's lazy module loading the first call on a device loads
+ * the library's device code there, and that load can allocate device memory
+ * (for the code and the array): make one call on each device before entering
+ * a region where allocation is forbidden, and before any stream capture.
+ * Later calls allocate nothing.  All calls on one GPU share the array (the
+ * call clears what must start at zero), so calls that overlap in time on the
+ * same GPU race and must be serialised by the caller.  Cost: each unordered
+ * pair re-reads its two columns three times from row-major X, one row per
+ * lane, so a call makes about 3 d^2 strided passes over n samples; it is
+ * meant for small d, not for throughput.
  */
 lingam_status lingam_step_scores_noalloc(const double *X, int64_t n, int64_t d, int64_t ld,
                                          double *M_out, lingam_stream_t stream);

@@ -16,13 +16,20 @@
 //
 // The scratch array lives in device memory of every GPU that loads this
 // library, for as long as the process runs (~66 KB).  Host code cannot use
-// the array's name as a device address; the address is looked up once per
-// device with cudaGetSymbolAddress while that device is current.
+// the array's name as a device address; every call looks the address up with
+// cudaGetSymbolAddress while the caller's device is current.  The lookup is
+// repeated on each call rather than cached: a device reset (cudaDeviceReset,
+// or a reset of the primary context) unloads the module, and the next load
+// may place the array elsewhere, so a cached address could go stale.  Once
+// the module is loaded on a device the lookup allocates nothing.  Under
+// CUDA's lazy module loading the module is loaded by the first call on each
+// device, and that load can allocate device memory for the code and the
+// array: a caller that must not allocate makes one call on each device before
+// entering its no-allocation region.
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "../../include/lingam.h"
 #include "common.cuh"
@@ -42,9 +49,6 @@ constexpr int NA_DOUBLES = NA_DONE + 1;
 
 // One copy per GPU that loads the library; every call on that GPU shares it.
 static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
-
-std::mutex g_addr_mutex;
-void *g_addr[128] = {};           // device address of the array, per device ordinal
 
 __device__ __forceinline__ void terms64(double u, double &t1, double &t2)
 {
@@ -194,19 +198,13 @@ __global__ void __launch_bounds__(256) k_step_scores_noalloc(const double *__res
     if (threadIdx.x == 0) *reinterpret_cast<unsigned int *>(scratch + NA_DONE) = 0u;
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
-cudaError_t scratch_address(int dev, double **out)
+// Device address of the scratch array on the current device.
+cudaError_t scratch_address(double **out)
 {
-    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = reinterpret_cast<double *>(g_addr[dev]);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = reinterpret_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -223,7 +221,7 @@ lingam_status lingam_step_scores_noalloc(const double *X, int64_t n, int64_t d, 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     double *scratch = nullptr;
-    if (e == cudaSuccess) e = scratch_address(dev, &scratch);
+    if (e == cudaSuccess) e = scratch_address(&scratch);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the status word and the done counter must start at zero
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + NA_STATUS, 0, 2 * sizeof(double), s);
