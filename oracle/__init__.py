@@ -74,6 +74,8 @@ def _load():
         lib.oracle_causal_order.argtypes = [PD, I64, I64, I32, I32, PI32, PD, I64]
         lib.oracle_causal_order_prior.argtypes = [PD, I64, I64, I32, I32,
                                                   ctypes.POINTER(ctypes.c_int8), PI32, PD, I64]
+        lib.oracle_regress_along.argtypes = [PD, I64, I64, PI32, ctypes.POINTER(I64), PI32,
+                                             I64, I64]
         lib.oracle_moments.argtypes = [PD, I64, PD, PD, PD, PD]
         lib.oracle_entropy.argtypes = [PD, I64, PD, PD]
         lib.oracle_entropy_from_moments.argtypes = [D, D]
@@ -232,6 +234,44 @@ def causal_order(X, literal: bool = False, threads: int | None = None,
             _pd(sc) if sc is not None else None, int(max_steps))
     _check(code, "causal_order")
     return (order, sc) if scores else order
+
+
+class Residuals:
+    """Sec. 2.2's residual data along a given order, step by step.
+
+    ``advance(t)`` regresses order[t_now .. t) out of the remaining variables
+    (the oracle's own helper, in its own sequence); ``data`` is then the [n, d]
+    residual matrix (removed variables keep their last values) and ``U`` the
+    remaining variables ascending, i.e. the state at which step t of the
+    oracle's loop scores when ``order`` is the oracle's order."""
+
+    def __init__(self, X, order):
+        X = _f64(X)
+        self.n, self.d = X.shape
+        self._R = np.ascontiguousarray(X.T)
+        self._U = np.arange(self.d, dtype=np.int32)
+        self._p = ctypes.c_int64(self.d)
+        self._order = np.ascontiguousarray(order, dtype=np.int32)
+        self.t = 0
+
+    def advance(self, t: int):
+        if t < self.t or t > self.d:
+            raise OracleError(1, "Residuals.advance: steps only move forward")
+        P32 = ctypes.POINTER(ctypes.c_int32)
+        code = _load().oracle_regress_along(
+            _pd(self._R), self.n, self.d, self._U.ctypes.data_as(P32), ctypes.byref(self._p),
+            self._order.ctypes.data_as(P32), self.t, t)
+        _check(code, "regress_along")
+        self.t = t
+        return self
+
+    @property
+    def U(self) -> np.ndarray:
+        return self._U[: self._p.value].copy()
+
+    @property
+    def data(self) -> np.ndarray:
+        return self._R.T
 
 
 # ------------------------------------------------------------ adjacency -----

@@ -459,6 +459,10 @@ static int prior_allowed(const int8_t *prior, int64_t d, const int32_t *U, int64
     return any ? ORACLE_OK : ORACLE_ERR_ARG;
 }
 
+int oracle_causal_order_prior(const double *X, int64_t n, int64_t d, int literal, int nthreads,
+                              const int8_t *prior, int32_t *order, double *scores,
+                              int64_t max_steps);
+
 int oracle_causal_order(const double *X, int64_t n, int64_t d, int literal, int nthreads,
                         int32_t *order, double *scores, int64_t max_steps)
 {
@@ -527,6 +531,46 @@ int oracle_causal_order_prior(const double *X, int64_t n, int64_t d, int literal
         if (scores) scores[t * d + U[0]] = 0.0;
     }
     free(R); free(U); free(kl); free(ref); free(tmp); free(allow);
+    return status;
+}
+
+/*
+ * Sec. 2.2's regress-out step applied along a given order: R is column-major
+ * [d][n] (variable i at R + i n), U[0..p) the remaining variables ascending.
+ * For k = t0 .. t1-1 the variable order[k] is regressed out of every other
+ * remaining variable with the same _residual helper and in the same sequence
+ * as oracle_causal_order, then removed from U.  On return *p is the number of
+ * remaining variables.  With `order` the oracle's own order, R and U then
+ * equal its internal state at step t1 bitwise, so sampled scores of a late
+ * step can be checked one row at a time.
+ */
+int oracle_regress_along(double *R, int64_t n, int64_t d, int32_t *U, int64_t *p,
+                         const int32_t *order, int64_t t0, int64_t t1)
+{
+    if (!R || !U || !p || !order || n < 2 || *p < 1 || *p > d || t0 < 0 || t1 < t0)
+        return ORACLE_ERR_ARG;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)n * 2);
+    if (!tmp) return ORACLE_ERR_NOMEM;
+    int status = ORACLE_OK;
+    for (int64_t k = t0; k < t1 && status == ORACLE_OK; ++k) {
+        int64_t mpos = -1;
+        for (int64_t a = 0; a < *p; ++a)
+            if (U[a] == order[k]) mpos = a;
+        if (mpos < 0) {
+            status = ORACLE_ERR_ARG;
+            break;
+        }
+        const double *rm = R + (int64_t)order[k] * n;
+        for (int64_t a = 0; a < *p && !status; ++a) {
+            if (a == mpos) continue;
+            double *ri = R + (int64_t)U[a] * n;
+            status = oracle_residual(ri, rm, n, tmp, tmp + n);
+            if (!status) memcpy(ri, tmp, sizeof(double) * (size_t)n);
+        }
+        for (int64_t a = mpos; a + 1 < *p; ++a) U[a] = U[a + 1];
+        --*p;
+    }
+    free(tmp);
     return status;
 }
 

@@ -22,11 +22,6 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import gen      # noqa: E402
 import oracle   # noqa: E402
 
-# cfg5 instances the oracle orders in full (small uneven ones plus a few resamples)
-CFG5_RESAMPLES = (0, 1, 2, 3)
-CFG5_MAX_D = 120
-
-
 def write_order(name, order, header_lines):
     path = os.path.join(HERE, f"{name}_order.txt")
     with open(path + ".tmp", "w") as f:
@@ -76,33 +71,47 @@ def run_cfg4(threads):
                        f"seed={gen.SEEDS[4]}", vd.digest(), time.time() - t, threads))
 
 
-def cfg5_selected(insts):
-    sel = list(CFG5_RESAMPLES)
-    for k, inst in enumerate(insts):
-        if inst.rows is None and inst.X.shape[1] <= CFG5_MAX_D:
-            sel.append(k)
-    return sel
+def _read_cfg5(path):
+    """Instances already stored: {index: line} (the file is rewritten after each one)."""
+    done = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                done[int(line.split()[0])] = line if line.endswith("\n") else line + "\n"
+    return done
 
 
 def run_cfg5(threads):
+    """Oracle orders of all 192 batch instances, cheapest first.
+
+    The file is rewritten (sorted by instance index) after every instance, so
+    an interrupted run keeps what it finished and a rerun skips it."""
+    import hashlib
     insts = gen.cfg5()
-    sel = cfg5_selected(insts)
     path = os.path.join(HERE, "cfg5_orders.txt")
-    with open(path + ".tmp", "w") as f:
-        f.write("# DirectLiNGAM causal orders from the FP64 oracle for selected cfg5 instances.\n")
-        f.write(f"# workload: cfg5 seed={gen.SEEDS[5]}; one line per instance:\n")
-        f.write("# <instance index> <name> <data-sha256-16> : <order>\n")
-        f.write("# written by tests/golden/make_golden.py\n")
-        for k in sel:
-            X = insts[k].data()
-            dig = __import__("hashlib").sha256(np.ascontiguousarray(X).tobytes()).hexdigest()[:16]
-            t = time.time()
-            order = oracle.causal_order(X, threads=threads)
-            print(f"cfg5[{k}] {insts[k].name} d={X.shape[1]} n={X.shape[0]} "
-                  f"{time.time() - t:.1f}s", flush=True)
-            f.write(f"{k} {insts[k].name} {dig} : " + " ".join(str(int(v)) for v in order) + "\n")
-    os.replace(path + ".tmp", path)
-    print("wrote", path, flush=True)
+    done = _read_cfg5(path)
+    todo = [k for k in range(len(insts)) if k not in done]
+    n_of = [len(i.rows) if i.rows is not None else i.X.shape[0] for i in insts]
+    todo.sort(key=lambda k: (gen.residual_samples(insts[k].X.shape[1], n_of[k]), k))
+    for k in todo:
+        X = insts[k].data()
+        dig = hashlib.sha256(np.ascontiguousarray(X).tobytes()).hexdigest()[:16]
+        t = time.time()
+        order = oracle.causal_order(X, threads=threads)
+        print(f"cfg5[{k}] {insts[k].name} d={X.shape[1]} n={X.shape[0]} "
+              f"{time.time() - t:.1f}s", flush=True)
+        done[k] = f"{k} {insts[k].name} {dig} : " + " ".join(str(int(v)) for v in order) + "\n"
+        with open(path + ".tmp", "w") as f:
+            f.write("# DirectLiNGAM causal orders from the FP64 oracle for the cfg5 instances.\n")
+            f.write(f"# workload: cfg5 seed={gen.SEEDS[5]}; one line per instance:\n")
+            f.write("# <instance index> <name> <data-sha256-16> : <order>\n")
+            f.write("# written by tests/golden/make_golden.py\n")
+            for j in sorted(done):
+                f.write(done[j])
+        os.replace(path + ".tmp", path)
+    print("wrote", path, f"({len(done)} instances)", flush=True)
 
 
 def main():

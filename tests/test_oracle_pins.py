@@ -348,3 +348,40 @@ def test_varlingam_recovers_hand_built_var1():
     assert np.max(np.abs(M[0] - M1)) < 0.03
     assert np.max(np.abs(B0h - B0)) < 0.03
     assert np.max(np.abs(Bt[0] - (np.eye(d) - B0) @ M1)) < 0.04
+
+
+# ------------------------------------------------ residuals along an order ----
+
+def test_residuals_along_order_equal_lstsq_on_removed_variables():
+    """After t steps, each remaining column is x_i minus its least-squares fit
+    (with intercept) on the t removed variables: Sec. 2.2's sequential
+    regressions span the same space as one regression on all of them."""
+    ds = gen.cfg2(seed=71, n=1500, d=9)
+    order = oracle.causal_order(ds.X)
+    res = oracle.Residuals(ds.X, order)
+    X = ds.X.astype(np.float64)
+    for t in (1, 3, 6, 8):
+        res.advance(t)
+        removed = order[:t]
+        assert sorted(res.U) == sorted(set(range(9)) - set(int(v) for v in removed))
+        Z = np.column_stack([np.ones(X.shape[0]), X[:, removed]])
+        for i in res.U:
+            coef, *_ = np.linalg.lstsq(Z, X[:, i], rcond=None)
+            r_ls = X[:, i] - Z @ coef
+            r = res.data[:, i]
+            assert np.max(np.abs((r - r.mean()) - r_ls)) < 1e-10 * X[:, i].std()
+
+
+def test_residuals_reproduce_the_oracle_loop_scores_at_later_steps():
+    """Scoring rows on the residual state of step t gives the k_list the
+    oracle's own loop recorded at step t (bitwise: same helpers, same order)."""
+    ds = gen.cfg2(seed=72, n=900, d=8)
+    order, sc = oracle.causal_order(ds.X, scores=True)
+    res = oracle.Residuals(ds.X, order)
+    for t in (0, 2, 5):
+        res.advance(t)
+        U = res.U
+        rows = np.arange(U.size, dtype=np.int32)
+        k = oracle.row_scores(res.data, rows, U=U)
+        assert np.array_equal(k, sc[t, U])
+        assert int(U[np.argmax(k)]) == int(order[t])
