@@ -5,7 +5,11 @@ inputs of ``gen/``; nothing comes from the CUDA path.  Each file records the
 workload, its seed and the SHA-256 prefix of the generated float32 data, so a
 test can refuse to compare against data that drifted.
 
-    python tests/golden/make_golden.py cfg1 cfg2 cfg4 cfg5 cfg3 long_n [--threads N]
+    python tests/golden/make_golden.py cfg1 cfg2 cfg4 cfg5 cfg3 long_n rows [--threads N]
+
+`rows` (run after the orders) writes oracle_rows.json: first-step scores of
+sampled variables and adjacency rows along the stored orders, which bench.py
+reads to state each GPU form's error against the oracle.
 
 cfg3 (d=1000, n=10000) is ~1e5 core-seconds of FP64 libm work.
 """
@@ -114,6 +118,55 @@ def run_cfg5(threads):
     print("wrote", path, f"({len(done)} instances)", flush=True)
 
 
+ROW_SAMPLES = {"cfg1": None, "cfg2": None, "cfg3": [0, 1, 137, 500, 998, 999],
+               "cfg4": [0, 5, 200, 486], "long_n": [0, 3, 41, 77, 99]}
+B_SAMPLES = {"cfg1": None, "cfg2": [0, 17, 50, 99], "cfg3": [0, 137, 500, 999],
+             "cfg4": [0, 5, 200, 486], "long_n": [0, 41, 99]}
+
+
+def run_rows(threads):
+    """Sampled first-step scores and adjacency rows of the FP64 oracle per
+    workload (None = every variable), along the stored oracle orders."""
+    import json
+    from gpu_util_golden import read_order
+    out = {}
+    for name in ROW_SAMPLES:
+        if name == "cfg4":
+            vd = gen.cfg4()
+            M, X = oracle.var_fit(vd.Xt, 1)
+            digest = vd.digest()
+        else:
+            ds = gen.long_n() if name == "long_n" else getattr(gen, name)()
+            X, digest = ds.X.astype(np.float64), ds.digest()
+        order, gdig = read_order(os.path.join(HERE, f"{name}_order.txt"))
+        if order is None or gdig != digest:
+            print(f"rows: {name} has no stored order for this data; skipped", flush=True)
+            continue
+        t = time.time()
+        d = X.shape[1]
+        sv = ROW_SAMPLES[name]
+        if sv is None:
+            sv = list(range(d))
+            m = oracle.search_step(X, threads=threads)["k_list"]
+        else:
+            m = oracle.row_scores(X, sv, threads=threads)
+        bv = B_SAMPLES[name] or list(range(d))
+        B = oracle.adjacency_rows(X, order, bv)
+        out[name] = {"data_sha256_16": digest, "step0_vars": [int(v) for v in sv],
+                     "step0_M": [float(v) for v in m], "B_vars": [int(v) for v in bv],
+                     "B_rows": [[float(v) for v in row] for row in B]}
+        print(f"rows: {name} {time.time() - t:.1f}s", flush=True)
+    path = os.path.join(HERE, "oracle_rows.json")
+    with open(path + ".tmp", "w") as f:
+        f.write(json.dumps({"written_by": "tests/golden/make_golden.py rows (oracle/ only)",
+                            "what": "FP64 oracle: first-step k_list of sampled variables "
+                                    "(Algorithm 1) and adjacency rows B[v] along the stored "
+                                    "oracle order (least squares on the predecessors)",
+                            "workloads": out}, indent=1))
+    os.replace(path + ".tmp", path)
+    print("wrote", path, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", nargs="+")
@@ -128,6 +181,8 @@ def main():
             run_cfg5(a.threads)
         elif w == "long_n":
             run_long_n(a.threads)
+        elif w == "rows":
+            run_rows(a.threads)
         else:
             raise SystemExit(f"unknown workload {w}")
 
