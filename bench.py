@@ -106,6 +106,229 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------ stored oracle values --
+# Written by tests/golden/make_golden.py from the FP64 oracle; bench.py only
+# reads them (text), to state each GPU form's error against the oracle.
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_order(name):
+    """(order, data digest) stored for a workload, or (None, None)."""
+    try:
+        lines = open(os.path.join(GOLDEN, f"{name}_order.txt")).read().splitlines()
+    except OSError:
+        return None, None
+    digest = order = None
+    for line in lines:
+        if line.startswith("# data-sha256-16:"):
+            digest = line.split(":")[1].strip()
+        elif not line.startswith("#") and line.strip():
+            order = [int(v) for v in line.split()]
+    return order, digest
+
+
+def golden_cfg5():
+    """{instance index: order} of the stored batch instances."""
+    out = {}
+    try:
+        for line in open(os.path.join(GOLDEN, "cfg5_orders.txt")):
+            if line.startswith("#") or not line.strip():
+                continue
+            head, tail = line.split(":")
+            out[int(head.split()[0])] = [int(v) for v in tail.split()]
+    except OSError:
+        pass
+    return out
+
+
+def golden_rows(name, digest):
+    """Stored oracle step-0 scores and adjacency rows of a workload, if they
+    were written for this data."""
+    try:
+        w = json.load(open(os.path.join(GOLDEN, "oracle_rows.json")))["workloads"].get(name)
+    except (OSError, ValueError):
+        return None
+    return w if w and w.get("data_sha256_16") == digest else None
+
+
+def oracle_errors(name, digest, order, M0=None, B=None):
+    """A GPU result against the stored FP64 oracle values: order equality,
+    max |dM(i)| / max_k |M(k)| over the stored first-step variables, max |dB|
+    over the stored adjacency rows (B computed along the oracle's order)."""
+    gold, gdig = golden_order(name)
+    out = {"order_equals_oracle": (list(map(int, order)) == gold) if gold and gdig == digest
+           else None}
+    rows = golden_rows(name, digest)
+    if rows and M0 is not None:
+        v = np.asarray(rows["step0_vars"])
+        scale = float(np.max(np.abs(M0)))
+        out["max_rel_dM_step0"] = float(np.max(np.abs(M0[v] - np.asarray(rows["step0_M"])))
+                                        / scale) if scale > 0 else None
+    if rows and B is not None:
+        v = np.asarray(rows["B_vars"])
+        out["max_abs_dB"] = float(np.max(np.abs(B[v] - np.asarray(rows["B_rows"]))))
+    return out
+
+# -------------------------------------------------------- the other configs --
+def _events_ms(torch, fn, reps, warmup, flush):
+    """Median device time (CUDA events on the current stream) of fn(), L2
+    flushed before each timed call."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms), out
+
+
+def run_configs(pkg, torch, dev, flush, reps):
+    """Every stated workload besides the headline one, per form: time per
+    call, pair-samples per second and the error against the stored FP64
+    oracle values (order equality, first-step scores, adjacency rows)."""
+    out = {}
+    cuda = f"cuda:{dev}"
+    for name, forms in (("cfg1", ("fp64", "fp32", "mixed")), ("cfg2", ("fp32", "mixed"))):
+        ds = getattr(gen, name)()
+        W = gen.residual_samples(ds.d, ds.n)
+        gold, _ = golden_order(name)
+        rec = {"workload": f"{name} d={ds.d} n={ds.n}", "residual_samples": W}
+        for prec in forms:
+            X = torch.from_numpy(ds.X.astype(np.float64 if prec == "fp64" else np.float32)).to(cuda)
+            with pkg.Context(dev, prec) as ctx:
+                if prec in ("fp32", "mixed"):
+                    ctx.autotune(ds.n, ds.d)
+                ms, order = _events_ms(torch, lambda: ctx.causal_order(X), reps, 3, flush)
+                _, M0 = ctx.step_measures(X)
+                B = ctx.fit_adjacency(torch.from_numpy(ds.X).to(cuda), gold) if gold else None
+            rec[prec] = {"ms": ms, "value": W / (ms * 1e-3),
+                         **oracle_errors(name, ds.digest(), order, M0, B)}
+        out[name] = rec
+    # VarLiNGAM at the stock-returns shape: FP64 VAR fit, ordering of the
+    # innovations, B0 and B1, end to end through varlingam_fit
+    vd = gen.cfg4()
+    T, d = vd.Xt.shape
+    W = gen.residual_samples(d, T - 1)
+    Xt = torch.from_numpy(vd.Xt).to(cuda)
+    rec = {"workload": f"cfg4 VarLiNGAM d={d} T={T} lag 1", "residual_samples": W}
+    for prec in ("mixed", "fp32"):
+        with pkg.Context(dev, prec) as ctx:
+            ctx.autotune(T - 1, d)
+            ms, res = _events_ms(torch, lambda: ctx.varlingam_fit(Xt, 1), reps, 3, flush)
+        order, B0, _ = res
+        rows = golden_rows("cfg4", vd.digest())
+        gold, _ = golden_order("cfg4")
+        e = {"order_equals_oracle": list(map(int, order)) == gold if gold else None}
+        if rows and gold and list(map(int, order)) == gold:
+            v = np.asarray(rows["B_vars"])
+            e["max_abs_dB0"] = float(np.max(np.abs(B0[v] - np.asarray(rows["B_rows"]))))
+        rec[prec] = {"ms": ms, "value": W / (ms * 1e-3), **e}
+    out["cfg4"] = rec
+    return out
+
+
+def run_batch_sequential(pkg, torch, dev, batch):
+    """The batch's instances ordered one call at a time (untimed warm-up pass
+    per form, then one timed pass: host wall time around the device work)."""
+    out = {}
+    rows_data = [(X if r is None else X[torch.from_numpy(r).to(X.device).long()].contiguous())
+                 for X, r in batch]
+    for prec in ("mixed", "fp32"):
+        with pkg.Context(dev, prec) as ctx:
+            ctx.autotune(max(int(X.shape[0]) for X in rows_data),
+                         max(int(X.shape[1]) for X in rows_data))
+            for X in rows_data:
+                ctx.causal_order(X)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for X in rows_data:
+                ctx.causal_order(X)
+            torch.cuda.synchronize()
+            out[prec] = (time.perf_counter() - t0) * 1e3
+    return out
+
+def cpu_model():
+    """The host CPU's model name (lscpu on Arm hosts, /proc/cpuinfo else)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def _oracle_partial(X, steps, threads):
+    """The oracle's first ``steps`` ordering steps of X: (residual-samples done, s)."""
+    import oracle
+    n, d = X.shape
+    t = time.perf_counter()
+    oracle.causal_order(X, threads=threads, max_steps=steps)
+    dt = time.perf_counter() - t
+    units = n * sum(p * (p - 1) for p in range(d - steps + 1, d + 1))
+    return units, dt
+
+
+def cpu_baselines(threads, X3, insts):
+    """The FP64 oracle (as it stands) per stated workload on the host cores,
+    each a bounded sample of a few seconds; where the sample is not the whole
+    order, the order time is extrapolated by the exact work p (p - 1) n per
+    step and marked so."""
+    out = {"cpu_model": cpu_model(), "cores": threads}
+
+    def rec(name, units, dt, W, sample, cores=threads):
+        full = units >= W
+        return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": sample, "order_s": W / (units / dt),
+                "order_s_kind": "measured" if full else "extrapolated"}
+
+    ds1 = gen.cfg1()
+    X1 = ds1.X.astype(np.float64)
+    u, dt = _oracle_partial(X1, ds1.d - 1, threads)
+    out["cfg1"] = rec("cfg1", u, dt, gen.residual_samples(ds1.d, ds1.n), "whole order")
+    ds2 = gen.cfg2()
+    X2 = ds2.X.astype(np.float64)
+    W2 = gen.residual_samples(ds2.d, ds2.n)
+    u, dt = _oracle_partial(X2, ds2.d - 1, threads)
+    out["cfg2"] = rec("cfg2", u, dt, W2, "whole order")
+    u, dt = _oracle_partial(X2, 3, 1)
+    out["cfg2_one_core"] = rec("cfg2", u, dt, W2, "first 3 of 99 steps on one core", cores=1)
+    u, dt = oracle_sample_step(X3.astype(np.float64), 400, threads)
+    out["cfg3"] = rec("cfg3", u, dt, gen.residual_samples(X3.shape[1], X3.shape[0]),
+                      "first ordering step over the first 400 of 1000 variables")
+    import oracle
+    vd = gen.cfg4()
+    t = time.perf_counter()
+    _, E = oracle.var_fit(vd.Xt, 1)
+    t_fit = time.perf_counter() - t
+    u, dt = _oracle_partial(E, 4, threads)
+    r4 = rec("cfg4", u, dt, gen.residual_samples(E.shape[1], E.shape[0]),
+             "FP64 VAR fit + first 4 of 486 ordering steps on the innovations")
+    r4["var_fit_s"] = t_fit
+    r4["order_s"] += t_fit
+    out["cfg4"] = r4
+    W5 = sum(gen.residual_samples(b.X.shape[1], b.X.shape[0] if b.rows is None else len(b.rows))
+             for b in insts)
+    u, dt = _oracle_partial(insts[0].data().astype(np.float64), 8, threads)
+    out["cfg5"] = rec("cfg5", u, dt, W5, "first 8 steps of resample 0 (d=200, n=4000); "
+                      "order_s is the whole 192-instance batch")
+    return out
+
 # --------------------------------------------------------------- reference --
 def oracle_sample_step(X, p_sample: int, threads: int):
     """Bounded sample of the workload for the CPU oracle: the first ordering
@@ -390,6 +613,7 @@ def run_ours(args, rank, world):
             if prec in ("mixed", "fp32") and not args.no_autotune:
                 tunings[prec] = ctx.autotune(n, d)
             ms, stats, order = time_form(ctx, X, args.steps, args.warmup, flush, torch, rank, world)
+            _, M0 = ctx.step_measures(X)     # first-step scores, for the oracle comparison
             pair_ms = sum(s["pair_ms"] for s in stats)
             pair_units = sum(s["pair_units"] for s in stats)
             forms[prec] = {"ms": ms, "pair_ms": pair_ms, "pair_units": pair_units,
@@ -403,7 +627,7 @@ def run_ours(args, rank, world):
                            "genuine_ties": stats[-1]["genuine_ties"],
                            "graph_nodes": stats[-1]["graph_nodes"],
                            "order_head": [int(v) for v in order[:8]],
-                           "order": order,
+                           "order": order, "M0": M0,
                            "tuning": ({k: tunings[prec][k] for k in ("p_max", "tile", "ctas_per_sm")}
                                       if prec in tunings else None)}
     # batched form: the bootstrap workload (128 resamples of d=200, n=4000 plus
@@ -433,22 +657,16 @@ def run_ours(args, rank, world):
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record()
-                ctx.causal_order_batch(batch)
+                ctx_batch_orders = ctx.causal_order_batch(batch)
                 b.record()
                 torch.cuda.synchronize()
                 bms.append(a.elapsed_time(b))
             bst = ctx.stats()
-        seq_ms = None
-        if args.batched_sequential:
-            with pkg.Context(dev, "fp32") as ctx:
-                rows_data = [(X if r is None else X[torch.from_numpy(r).to(X.device).long()].contiguous())
-                             for X, r in batch]
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for X in rows_data:
-                    ctx.causal_order(X)
-                torch.cuda.synchronize()
-                seq_ms = (time.perf_counter() - t0) * 1e3
+        # the same instances one call at a time, in both forms
+        seq = run_batch_sequential(pkg, torch, dev, batch) if args.batched_sequential else {}
+        gold5 = golden_cfg5()
+        border = ctx_batch_orders
+        matched = sum(1 for k, o in gold5.items() if k < len(border) and list(border[k]) == o)
         batch_info = {"workload": "bootstrap_128x(d200,n4000)+64x(d50-400,n1000-8000)",
                       "instances": len(insts), "residual_samples": Wb,
                       "ms_per_call": sum(bms) / len(bms), "value": Wb / (sum(bms) / len(bms) * 1e-3),
@@ -458,8 +676,11 @@ def run_ours(args, rank, world):
                       "tuning": ({k: btune[k] for k in ("p_max", "tile", "ctas_per_sm", "ms")}
                                  if btune else None),
                       "df_candidates": bst["df_candidates"],
-                      "sequential_plain_fp32_ms": seq_ms,
-                      "sequential_plain_fp32_value": (Wb / (seq_ms * 1e-3)) if seq_ms else None}
+                      "sequential_plain_fp32_ms": seq.get("fp32"),
+                      "sequential_plain_fp32_value": (Wb / (seq["fp32"] * 1e-3)) if seq else None,
+                      "sequential_mixed_ms": seq.get("mixed"),
+                      "sequential_mixed_value": (Wb / (seq["mixed"] * 1e-3)) if seq else None,
+                      "orders_equal_oracle": f"{matched} of {len(gold5)} stored instances"}
 
     # the paper's long-sample case: n = 1e6, d = 100 (Sec. 2.3), head form
     long_info = None
@@ -473,6 +694,11 @@ def run_ours(args, rank, world):
                 ctx.autotune(dl.n, dl.d)
             lms, lst, lorder = time_form(ctx, Xl, args.steps, args.warmup, flush, torch, rank,
                                          world)
+            _, lM0 = ctx.step_measures(Xl)
+        lgold, _ = golden_order("long_n")
+        with pkg.Context(dev, "fp32") as ctx:
+            lB = ctx.fit_adjacency(Xl, lgold) if lgold else None
+        lerr = oracle_errors("long_n", dl.digest(), lorder, lM0, lB)
         lmax = max_over_ranks(sum(lms), world, f"cuda:{dev}")
         long_info = {"workload": "long_n_d100_n1e6 (cfg2 generator)", "precision": head0,
                      "residual_samples": Wl, "ms_per_order": lmax / args.steps,
@@ -485,7 +711,7 @@ def run_ours(args, rank, world):
                      "fp64_candidates": lst[-1]["fp64_candidates"],
                      "genuine_ties": lst[-1]["genuine_ties"],
                      "refined_steps": lst[-1]["refined_steps"],
-                     "order_head": [int(v) for v in lorder[:8]]}
+                     "order_head": [int(v) for v in lorder[:8]], "oracle_errors": lerr}
         del Xl
 
     region_s = time.perf_counter() - t_region0
@@ -530,7 +756,8 @@ def run_ours(args, rank, world):
                "lg2": lg2 / (sms * l_mhz * 1e6), "fp64_fma": dfma / 2 / (sms * d_mhz * 1e6)}
     run_mhz = clk.get("sm_mhz") or f_mhz
     # fast form per residual-sample: 2 MUFU ex2 (exp(-u^2/2), exp(-2|u|)), one
-    # lg2 per 4 x groups samples (the log of the product of the 1 + y), and
+    # lg2 per 4 x groups samples (x the chunks of a ring stage in the
+    # streamlined tiles: the log of the product of the 1 + y), and
     # 7.25 FP32-pipe lane ops (u: multiply + FMA; u^2; u e accumulate; |u|
     # scale; product chain; |u| sum; lg2 combine), issued as 7.25 scalar
     # instructions or, with paired-FP32 tiles, 4.4 (six of the seven as
@@ -543,7 +770,7 @@ def run_ours(args, rank, world):
         b = next((i for i, pm in enumerate(tune["p_max"]) if p <= pm), len(tune["p_max"]) - 1)
         g = pkg.lingam_pair_tile_info(tune["tile"][b])
         w = p * (p - 1.0)
-        lg2w += w / (4.0 * g["groups"])
+        lg2w += w / (4.0 * g["groups"] * max(1, g.get("sub", 0)))
         issw += w * (4.4 if g["packed"] else 7.25)
         wsum += w
     mix = {"mufu_ex2": 2.0, "mufu_lg2": lg2w / wsum, "fp32_pipe": 7.25,
@@ -596,6 +823,26 @@ def run_ours(args, rank, world):
                "sample": f"first ordering step of Algorithm 1 over the first {args.cpu_p} of the "
                          f"1000 variables, n=10000 ({units:.3e} residual-samples, {dt:.1f} s)"}
 
+    cpu_all = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_all = cpu_baselines(threads, ds.X, insts if args.batched else gen.cfg5())
+        cpu["cpu_model"] = cpu_all["cpu_model"]
+
+    configs = None
+    if world == 1 and args.configs:
+        configs = run_configs(pkg, torch, dev, flush, min(args.steps, 5))
+
+    # each cfg3 form against the stored oracle values (adjacency along the
+    # oracle's order once: it does not depend on the form)
+    gold3, _ = golden_order("cfg3")
+    B3 = None
+    if gold3:
+        with pkg.Context(dev, "fp32") as ctx:
+            B3 = ctx.fit_adjacency(X, gold3)
+    for p in args.forms:
+        forms[p]["oracle_errors"] = oracle_errors("cfg3", ds.digest(), forms[p]["order"],
+                                                  forms[p]["M0"], B3)
+
     readouts = None
     if world == 1 and args.readouts:
         if batch is None:
@@ -625,7 +872,10 @@ def run_ours(args, rank, world):
                       "phase_ms_per_step": forms[p]["phase_ms_per_step"],
                       "genuine_ties": forms[p]["genuine_ties"],
                       "tuning": forms[p]["tuning"],
-                      "order_head": forms[p]["order_head"]} for p in args.forms},
+                      "order_head": forms[p]["order_head"],
+                      "oracle_errors": forms[p]["oracle_errors"]} for p in args.forms},
+        "configs": configs,
+        "cpu_baselines": cpu_all,
         "batched": batch_info,
         "long_n": long_info,
         "readouts": readouts,
@@ -660,7 +910,10 @@ def main():
     ap.add_argument("--tile", type=int, default=None,
                     help="--one-order: one pair-kernel tile configuration instead of the autotuner")
     ap.add_argument("--ctas", type=int, default=4, help="--one-order --tile: CTAs per SM")
-    ap.add_argument("--batched-sequential", action="store_true")
+    ap.add_argument("--no-batched-sequential", dest="batched_sequential", action="store_false",
+                    help="skip the batch's instances as single calls")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the cfg1 / cfg2 / cfg4 timings and their oracle errors")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the untuned pair-kernel tiles (one 8 x 16 configuration)")
     args = ap.parse_args()

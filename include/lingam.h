@@ -317,15 +317,77 @@ lingam_status lingam_get_tuning(const lingam_ctx *ctx, int32_t precision, lingam
  */
 lingam_status lingam_set_prior_knowledge(lingam_ctx *ctx, const int8_t *prior, int64_t d);
 
-/* Number of pair-kernel tile configurations. */
-#define LINGAM_PAIR_TILES 16
+/*
+ * Pair sharding of one ordering over several ranks (one process and GPU per
+ * rank).  Algorithm 1's work per step is the p (p - 1) ordered pairs, which
+ * are independent (Sec. 3.1 parallelises over them); only the p-vector of
+ * scores M(i) joins them.  With a shard set, a context computes the pair
+ * moments and the score terms only for the pairs its rank owns
+ * (lingam_shard_owner), so its M(i) and error bounds E(i) are partial sums;
+ * after each step's scoring the library calls
+ *
+ *     int allreduce(double *buf, int64_t count, void *user)
+ *
+ * with buf = [partial M (p values) | partial E (p values)], count = 2 p, on
+ * the host.  It must replace buf with the element-wise sums over all ranks,
+ * identical bit for bit on every rank (for example gather the partials and
+ * add them in rank order), and return 0; a non-zero return fails the call
+ * with LINGAM_ERR_CUDA.  Every rank then takes the same decisions: the
+ * argmax, the re-score tiers (candidate rows recomputed in full on every
+ * rank) and the regress-out are replicated, so all ranks return the same
+ * order.  One exchange of 2 p doubles per step.
+ *
+ *   rank, nranks  0 <= rank < nranks; nranks = 1 removes the shard.
+ *   allreduce     required when nranks > 1; user is passed through.
+ * Applies to lingam_causal_order (without a score history) and
+ * lingam_step_measures (which returns the rank's partial first-step M, no
+ * exchange, and I(i, j) only for owned entries).  A sharded context refuses
+ * batched calls and score histories with LINGAM_ERR_ARG.
+ */
+typedef int (*lingam_allreduce_fn)(double *buf, int64_t count, void *user);
+lingam_status lingam_set_shard(lingam_ctx *ctx, int32_t rank, int32_t nranks,
+                               lingam_allreduce_fn allreduce, void *user);
+
+/* Owner rank of the ordered pairs (i, j) and (j, i) of positions i, j < p at a
+ * step with p remaining variables over nranks ranks: the positions are cut
+ * into blocks of 16 and the unordered block pairs, taken row by row over the
+ * upper triangle, into nranks contiguous ranges of about p (p - 1) / nranks
+ * ordered pairs each.  No context or GPU needed; -1 for arguments out of
+ * range (p = 1 has no pairs: rank 0). */
+int32_t lingam_shard_owner(int64_t i, int64_t j, int64_t p, int32_t nranks);
 
 /*
- * Shape of tile configuration `tile` (no context or GPU needed): out[8] =
+ * Input gate for the single-instance calls (lingam_causal_order,
+ * lingam_step_measures).  (The paper has no counterpart: a runtime facility.)
+ * With a gate set, each such call first waits on the device until *flag is
+ * non-zero, and only then reads X, so a producer that cannot share a stream
+ * with the caller (another process, a copy engine driven elsewhere, the host
+ * writing mapped memory) can release the input by setting the flag after
+ * its data are written (with release ordering at system scope, e.g. a
+ * __threadfence_system() before the store, or a stream-ordered copy).
+ *
+ *   flag       4-byte aligned uint32 in device, managed or mapped (pinned,
+ *              cudaHostAllocMapped / registered-mapped) host memory, owned by
+ *              the caller and valid while the gate is set; NULL removes the
+ *              gate.  The library only reads it.
+ *   timeout_s  bound on each wait, 0 < timeout_s <= 60.
+ * When a wait runs out, the call returns LINGAM_ERR_TIMEOUT (its outputs are
+ * not valid) and the context stays usable: the next call waits again.  A
+ * flag that is not device-readable memory, a misaligned flag or a timeout
+ * outside the range is LINGAM_ERR_ARG.
+ */
+lingam_status lingam_set_input_gate(lingam_ctx *ctx, const uint32_t *flag, double timeout_s);
+
+/* Number of pair-kernel tile configurations. */
+#define LINGAM_PAIR_TILES 26
+
+/*
+ * Shape of tile configuration `tile` (no context or GPU needed): out[9] =
  * {pairs per warp along i, along j, warps along i, along j, TMA ring stages,
  * groups of 4 samples per lane and iteration (one MUFU lg2 per 4 x groups
  * samples in the fast form), chunks of 256 samples between compensated
- * folds, paired-FP32 (f32x2) arithmetic 0/1}.  LINGAM_ERR_ARG for a tile
+ * folds, paired-FP32 (f32x2) arithmetic 0/1, chunks per TMA ring stage of the
+ * streamlined block (0: the original one-chunk-per-stage block)}.  LINGAM_ERR_ARG for a tile
  * outside 0 .. LINGAM_PAIR_TILES-1 or a null out.
  */
 lingam_status lingam_pair_tile_info(int32_t tile, int32_t *out);

@@ -107,6 +107,9 @@ SIGNATURES = {
     "lingam_get_tuning": (_I32, [_P, _I32, ctypes.POINTER(Tuning)]),
     "lingam_pair_tile_info": (_I32, [_I32, ctypes.POINTER(_I32)]),
     "lingam_set_prior_knowledge": (_I32, [_P, ctypes.POINTER(ctypes.c_int8), _I64]),
+    "lingam_set_input_gate": (_I32, [_P, _P, ctypes.c_double]),
+    "lingam_set_shard": (_I32, [_P, _I32, _I32, _P, _P]),
+    "lingam_shard_owner": (_I32, [_I64, _I64, _I64, _I32]),
 }
 
 
@@ -240,6 +243,44 @@ class Context:
 
     def _dtype(self):
         return np.float64 if self.precision == "fp64" else np.float32
+
+    def set_shard(self, rank: int, nranks: int, allreduce=None):
+        """Compute only this rank's slice of the pair space (lingam_set_shard).
+
+        ``allreduce(buf)`` receives a float64 numpy view of [partial M |
+        partial E] (2 p values) after each step's scoring and must overwrite
+        it with the sums over all ranks, identical on every rank."""
+        if nranks <= 1:
+            self._check(self._lib.lingam_set_shard(self._h, 0, 1, None, None))
+            self._shard_cb = None
+            return
+
+        def trampoline(buf, count, user):
+            try:
+                allreduce(np.ctypeslib.as_array(buf, shape=(int(count),)))
+                return 0
+            except Exception:   # reported to the caller as a failed exchange
+                return 1
+
+        cb = _ALLREDUCE_FN(trampoline)
+        self._check(self._lib.lingam_set_shard(self._h, int(rank), int(nranks),
+                                               ctypes.cast(cb, ctypes.c_void_p), None))
+        self._shard_cb = cb          # the library keeps calling it while set
+
+    def set_input_gate(self, flag, timeout_s: float = 1.0):
+        """Make lingam_causal_order / step_measures wait on the device until
+        the uint32 ``flag`` (a CUDA tensor, or an integer device / mapped
+        host address) is non-zero before reading their input; ``None``
+        removes the gate.  A wait longer than ``timeout_s`` fails the call
+        with ERR_TIMEOUT."""
+        if flag is None:
+            self._check(self._lib.lingam_set_input_gate(self._h, None, 0.0))
+            self._gate = None
+            return
+        addr = flag.data_ptr() if hasattr(flag, "data_ptr") else int(flag)
+        self._check(self._lib.lingam_set_input_gate(self._h, ctypes.c_void_p(addr),
+                                                     float(timeout_s)))
+        self._gate = flag           # keep the caller's buffer alive while set
 
     # -- the ABI ----------------------------------------------------------------
     def causal_order(self, X, scores: bool = False):
@@ -480,16 +521,27 @@ def lingam_step_measures(ctx: Context, X):
     return ctx.step_measures(X)
 
 
-PAIR_TILES = 16
-_TILE_KEYS = ("wi", "wj", "wgi", "wgj", "stages", "groups", "fold", "packed")
+PAIR_TILES = 26
+_TILE_KEYS = ("wi", "wj", "wgi", "wgj", "stages", "groups", "fold", "packed", "sub")
+
+
+_ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                 ctypes.c_void_p)
+
+
+def shard_owner(i: int, j: int, p: int, nranks: int) -> int:
+    """Owner rank of the pairs (i, j) and (j, i) at a step with p remaining
+    variables (lingam_shard_owner; no GPU needed)."""
+    return int(load().lingam_shard_owner(int(i), int(j), int(p), int(nranks)))
 
 
 def lingam_pair_tile_info(tile: int) -> dict:
     """Shape of pair-kernel tile configuration `tile` (no GPU needed): pairs
     per warp (wi x wj), warps (wgi x wgj), TMA stages, groups of 4 samples per
     lane and iteration (one lg2 per 4 x groups samples in the fast form),
-    chunks between compensated folds, paired-FP32 arithmetic."""
-    out = (ctypes.c_int32 * 8)()
+    chunks between compensated folds, paired-FP32 arithmetic, chunks per
+    ring stage of the streamlined block (0: the original block)."""
+    out = (ctypes.c_int32 * 9)()
     st = load().lingam_pair_tile_info(int(tile), out)
     if st != 0:
         raise LingamError(st, f"lingam_pair_tile_info({tile}): no such tile configuration")

@@ -75,6 +75,39 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bit)
     atomicOr(status, bit);
 }
 
+// -------------------------------------------------------- pair sharding ---
+// Rank that owns the entries (i, j) and (j, i) of a step with p remaining
+// variables when the pair space is split over nranks.  The positions are cut
+// into blocks of SHARD_BLOCK; the unordered block pairs (a <= b), taken row
+// by row over the upper triangle, are cut into nranks contiguous ranges of
+// about p (p - 1) / nranks ordered pairs each (a block pair goes to the range
+// holding its midpoint).  Every pair-kernel tile lies inside one block pair
+// (tile sides divide SHARD_BLOCK), and a tile and its transpose have the
+// same owner.
+constexpr int SHARD_BLOCK = 16;
+__host__ __device__ inline int shard_owner(int i, int j, int p, int nranks)
+{
+    constexpr int64_t B = SHARD_BLOCK;
+    if (p < 2 || nranks < 2) return 0;
+    int64_t a = i / SHARD_BLOCK, b = j / SHARD_BLOCK;
+    if (a > b) {
+        const int64_t t = a;
+        a = b;
+        b = t;
+    }
+    const int64_t P = p;
+    const int64_t sa = P - B * a < B ? P - B * a : B;   // size of block a (the last is short)
+    const int64_t sb = P - B * b < B ? P - B * b : B;
+    // ordered pairs before block pair (a, b): the full rows a' < a (each
+    // s(s - 1) + 2 s (p - B a' - s) with s = B), then within row a the
+    // diagonal block and the full blocks a + 1 .. b - 1
+    int64_t cum = a * (2 * B * P - B * B - B) - B * B * a * (a - 1);
+    if (b > a) cum += sa * (sa - 1) + 2 * sa * B * (b - a - 1);
+    const int64_t w = a == b ? sa * (sa - 1) : 2 * sa * sb;
+    const int64_t r = ((int64_t)nranks * (2 * cum + w)) / (2 * P * (P - 1));
+    return (int)(r < nranks - 1 ? r : nranks - 1);
+}
+
 // ------------------------------------------------------------- mbarrier ---
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
@@ -117,9 +150,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait for the phase with the given parity to complete.  Returns
 // false after ~2^22 polls with back-off (well over a second), so a kernel
 // never spins forever; the caller then records ST_TIMEOUT and winds down.
+// (A variant whose polls carried a suspend-time hint was measured slower: it
+// woke the waiting warps late.)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     if (mbar_try_wait(bar, parity)) return true;

@@ -76,6 +76,7 @@ struct ScoreParams {
     float *I32;           // optional [p][p] lower bound of I(i, j) (rounded down), read by
                           // the re-score passes: entries with I32 >= 0 are skipped
     double *epsOut;       // optional [p][p] the entry bounds (step-measure calls)
+    int shard_rank, shard_n;   // shard_n > 1 (FP32-scored steps): only owned entries count
 };
 
 // Bound on the change of h(m1, m2) for moment errors (e1, e2), in FP32 (a
@@ -275,6 +276,8 @@ struct FinishParams {
 
 // ---- launchers (return the launch error) ----
 // Batched launchers take a device array of per-instance parameters.
+cudaError_t launch_gate_wait(const uint32_t *flag, uint64_t limit_ns, uint32_t *status,
+                             cudaStream_t s);
 cudaError_t launch_pack(const void *X, int is_f64, int layout, int64_t ld, int n, int d,
                         double *R, int64_t ldr, uint32_t *status, cudaStream_t s);
 cudaError_t launch_center(double *R, int64_t ldr, int n, int d, cudaStream_t s);

@@ -380,6 +380,343 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
     }
 }
 
+// ------------------------------------------------------------------------
+// Streamlined block (tile configurations with sub >= 1)
+// ------------------------------------------------------------------------
+//
+// The same per-pair arithmetic as pair_block, with less bookkeeping per
+// residual-sample: a ring stage holds `sub` consecutive chunks (fewer barrier
+// waits and arrivals per sample), stage and parity advance incrementally, the
+// fold test uses a power-of-two chunk count, each lane loads the WJ column
+// samples once per chunk and the WI row samples one row at a time (fewer live
+// registers), the paired-FP32 u exp(-u^2/2) sums stay float2 across the
+// chunks of a fold period, and the product of the 1 + y factors starts from
+// (1, 1) so every sample pair takes one f32x2 FMA.
+
+// One full chunk of the paired fast form for the WI x WJ pairs of a warp
+// (groups of four samples g 128 + 4 l .. + 3, g = 0, 1, as in pair_chunk).
+// The product of the 1 + y factors and the |u| sum run on in pr / asum across
+// the chunks of a ring stage (FIRST starts them); the caller takes one lg2 of
+// the product of up to 8 SUB factors (at most 2^16) when the stage ends.
+template <int WI, int WJ, int S, bool FIRST>
+__device__ __forceinline__ void pair_chunk_pk(const float *__restrict__ rows,
+                                              const float *__restrict__ cols,
+                                              const float2 (&A)[WI][WJ],
+                                              const float2 (&NB)[WI][WJ], float2 (&pr)[WI][WJ],
+                                              float (&asum)[WI][WJ], float2 (&acc)[WI][WJ],
+                                              int lane)
+{
+    static_assert(S == 256, "one iteration of 8 samples per lane covers a chunk");
+    const int s0 = lane * 4;
+    float zj[WJ][8];
+#pragma unroll
+    for (int c = 0; c < WJ; ++c) {
+        const float4 t0 = *reinterpret_cast<const float4 *>(cols + c * S + s0);
+        const float4 t1 = *reinterpret_cast<const float4 *>(cols + c * S + s0 + 128);
+        zj[c][0] = t0.x; zj[c][1] = t0.y; zj[c][2] = t0.z; zj[c][3] = t0.w;
+        zj[c][4] = t1.x; zj[c][5] = t1.y; zj[c][6] = t1.z; zj[c][7] = t1.w;
+    }
+    const float2 C2 = make_float2(FAST_C2, FAST_C2);
+    const float2 ONE = make_float2(1.0f, 1.0f);
+#pragma unroll
+    for (int r = 0; r < WI; ++r) {
+        float zi[8];
+        {
+            const float4 t0 = *reinterpret_cast<const float4 *>(rows + r * S + s0);
+            const float4 t1 = *reinterpret_cast<const float4 *>(rows + r * S + s0 + 128);
+            zi[0] = t0.x; zi[1] = t0.y; zi[2] = t0.z; zi[3] = t0.w;
+            zi[4] = t1.x; zi[5] = t1.y; zi[6] = t1.z; zi[7] = t1.w;
+        }
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) {
+            float2 pc = FIRST ? ONE : pr[r][c];
+            float as = asum[r][c];
+            float2 ac = acc[r][c];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float2 zi2 = make_float2(zi[2 * h], zi[2 * h + 1]);
+                const float2 zj2 = make_float2(zj[c][2 * h], zj[c][2 * h + 1]);
+                const float2 u = __ffma2_rn(A[r][c], zi2, __fmul2_rn(NB[r][c], zj2));
+                const float2 sq = __fmul2_rn(u, u);
+                const float2 e = make_float2(ex2_approx(-sq.x), ex2_approx(-sq.y));
+                ac = __ffma2_rn(u, e, ac);
+                const float2 q = __fmul2_rn(u, C2);   // C2 < 0: exp(-2|u|) = ex2(-|q|)
+                const float2 y = make_float2(ex2_approx(-fabsf(q.x)), ex2_approx(-fabsf(q.y)));
+                pc = __ffma2_rn(y, pc, pc);
+                as = (FIRST && h == 0) ? fabsf(u.x) + fabsf(u.y) : as + fabsf(u.x) + fabsf(u.y);
+            }
+            acc[r][c] = ac;
+            pr[r][c] = pc;
+            asum[r][c] = as;
+        }
+    }
+}
+
+template <int MODE, int CFG>
+__device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUtensorMap *tmJ,
+                                              const PairParams &P, const int ti, const int tj,
+                                              const int split)
+{
+    constexpr PairCfg G = PAIR_CFGS[CFG];
+    constexpr int WI = G.wi, WJ = G.wj, WGJ = G.wgj;
+    constexpr int NCW = G.warps();
+    constexpr int TI = G.ti(), TJ = G.tj(), S = PAIR_S, STAGES = G.stages, SUB = G.sub;
+    constexpr uint32_t CHUNK_FLOATS = (TI + TJ) * S;
+    constexpr uint32_t STAGE_FLOATS = CHUNK_FLOATS * SUB;
+    constexpr bool PK = MODE == PAIR_FAST && G.packed != 0;
+    constexpr int FOLD = G.fold;
+    static_assert(SUB >= 1 && (FOLD & (FOLD - 1)) == 0 && FOLD % SUB == 0,
+                  "streamlined block: power-of-two folds, a multiple of the stage");
+    static_assert(!PK || G.groups == 2, "the paired chunk takes 8 samples per lane");
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + STAGES;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 512);
+    float *buf = reinterpret_cast<float *>(smem + 1024);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = split * P.cps;
+    const int c1 = min(c0 + P.cps, P.nchunks);
+    const int nck = c1 - c0;
+    const int nst = (nck + SUB - 1) / SUB;   // ring stages of this sample range
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        *abort_flag = (*(volatile uint32_t *)P.status & ST_TIMEOUT) ? 1 : 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (nck <= 0 || *abort_flag) return;
+
+    // Thread 0 fills stage k with the chunks k SUB .. k SUB + SUB - 1 of the
+    // range that exist (the last stage may hold fewer), once every warp has
+    // released what that ring slot held before.
+    int issued = 0;
+    auto issue = [&](int k) -> bool {
+        const int st = k % STAGES;
+        if (k >= STAGES && !mbar_wait_bounded(&empty[st], ((k / STAGES) - 1) & 1)) return false;
+        float *dst = buf + st * STAGE_FLOATS;
+        const int nb = min(SUB, nck - k * SUB);
+        mbar_arrive_expect_tx(&full[st], (uint32_t)nb * CHUNK_FLOATS * 4u);
+        for (int b = 0; b < nb; ++b) {
+            const int x = (c0 + k * SUB + b) * S;
+            tma_load_2d(dst + b * CHUNK_FLOATS, tmI, x, P.row0 + ti * TI, &full[st]);
+            tma_load_2d(dst + b * CHUNK_FLOATS + TI * S, tmJ, x, P.row0 + tj * TJ, &full[st]);
+        }
+        issued = k + 1;
+        return true;
+    };
+    if (threadIdx.x == 0) {
+        prefetch_tensormap(tmI);
+        prefetch_tensormap(tmJ);
+        for (int k = 0; k < min(STAGES - 1, nst); ++k) (void)issue(k);
+    }
+
+    const int wi = warp / WGJ, wj = warp % WGJ;
+    const int ri0 = wi * WI, cj0 = wj * WJ;
+    const int pi0 = ti * TI + ri0, pj0 = tj * TJ + cj0;
+
+    float ca[WI][WJ], cb[WI][WJ];
+    {
+        // rho and 1 - rho^2 in FP64, the reciprocal square root in FP32
+        float a = 0.0f, b = 0.0f;
+        if (lane < WI * WJ) {
+            const int pi = pi0 + lane / WJ, pj = pj0 + lane % WJ;
+            if (pi < P.p && pj < P.p && pi != pj) {
+                const int oi = P.U[pi], oj = P.U[pj];
+                const int lo = min(oi, oj), hi = max(oi, oj);
+                const double rho = P.C[(int64_t)lo * P.ldc + hi] * P.isd[pi] * P.isd[pj];
+                const double s2 = fma(-rho, rho, 1.0);
+                if (s2 > 1e-12) {
+                    a = rsqrtf((float)s2);
+                    b = (float)rho * a;
+                } else {
+                    set_status(P.status, ST_DEGENERATE);
+                    a = 1.0f;
+                }
+                if (MODE == PAIR_FAST) {
+                    a *= (float)KSC;
+                    b *= (float)KSC;
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < WI * WJ; ++e) {
+            ca[e / WJ][e % WJ] = __shfl_sync(0xffffffffu, a, e);
+            cb[e / WJ][e % WJ] = __shfl_sync(0xffffffffu, b, e);
+        }
+    }
+    float2 A[WI][WJ], NB[WI][WJ];
+#pragma unroll
+    for (int r = 0; r < WI; ++r)
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) {
+            A[r][c] = make_float2(ca[r][c], ca[r][c]);
+            NB[r][c] = make_float2(-cb[r][c], -cb[r][c]);
+        }
+
+    // (hi, lo) folded sums, and the FP32 sums of the current fold period
+    // (S2 as two interleaved float2 halves in the paired form)
+    float s1[WI][WJ], s2[WI][WJ], e1[WI][WJ], e2[WI][WJ], a1[WI][WJ], asum[WI][WJ];
+    float2 acc[WI][WJ], pr[WI][WJ];
+#pragma unroll
+    for (int r = 0; r < WI; ++r)
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) {
+            s1[r][c] = s2[r][c] = e1[r][c] = e2[r][c] = a1[r][c] = asum[r][c] = 0.0f;
+            acc[r][c] = pr[r][c] = make_float2(0.0f, 0.0f);
+        }
+
+    int st = 0;
+    uint32_t ph = 0;
+    for (int k = 0; k < nst; ++k) {
+        if (threadIdx.x == 0 && k + STAGES - 1 < nst && !*abort_flag) {
+            if (!issue(k + STAGES - 1)) {
+                set_status(P.status, ST_TIMEOUT);
+                *abort_flag = 1;
+            }
+        }
+        if (!mbar_wait_bounded(&full[st], ph)) {
+            set_status(P.status, ST_TIMEOUT);
+            *abort_flag = 1;
+            break;
+        }
+        const float *sb = buf + st * STAGE_FLOATS;
+        // a chunk after the first of a stage exists only if the first was
+        // full (a short chunk is the last of the instance)
+        bool pending = false;
+#pragma unroll
+        for (int b = 0; b < SUB; ++b) {
+            const int ch = k * SUB + b;
+            if (ch >= nck) break;
+            const float *rows = sb + b * CHUNK_FLOATS + ri0 * S;
+            const float *cols = sb + b * CHUNK_FLOATS + TI * S + cj0 * S;
+            const int valid = min(S, P.n - (c0 + ch) * S);
+            if (PK && valid == S) {
+                if (b == 0)
+                    pair_chunk_pk<WI, WJ, S, true>(rows, cols, A, NB, pr, asum, acc, lane);
+                else
+                    pair_chunk_pk<WI, WJ, S, false>(rows, cols, A, NB, pr, asum, acc, lane);
+                pending = true;
+            } else {
+                float tca[WI][WJ], tcb[WI][WJ], t2[WI][WJ];
+#pragma unroll
+                for (int r = 0; r < WI; ++r)
+#pragma unroll
+                    for (int c = 0; c < WJ; ++c) {
+                        tca[r][c] = A[r][c].x;
+                        tcb[r][c] = -NB[r][c].x;
+                        t2[r][c] = 0.0f;
+                    }
+                if (valid == S)
+                    pair_chunk<MODE, false, WI, WJ, S, G.groups, false>(rows, cols, tca, tcb, a1,
+                                                                        t2, lane, valid);
+                else
+                    pair_chunk<MODE, true, WI, WJ, S, G.groups, false>(rows, cols, tca, tcb, a1,
+                                                                       t2, lane, valid);
+#pragma unroll
+                for (int r = 0; r < WI; ++r)
+#pragma unroll
+                    for (int c = 0; c < WJ; ++c) acc[r][c].x += t2[r][c];
+            }
+        }
+        if (PK && pending) {
+            // sum log2(2 cosh u) over the stage's full chunks: C3 sum |u~| +
+            // lg2 of the product of their 1 + y factors
+#pragma unroll
+            for (int r = 0; r < WI; ++r)
+#pragma unroll
+                for (int c = 0; c < WJ; ++c)
+                    a1[r][c] += fmaf(asum[r][c], FAST_C3, lg2_approx(pr[r][c].x * pr[r][c].y));
+        }
+        // fold the period's FP32 sums into (hi, lo) pairs every FOLD chunks
+        // (FOLD is a multiple of SUB) and after the last stage
+        if ((((k + 1) * SUB) & (FOLD - 1)) == 0 || k == nst - 1) {
+#pragma unroll
+            for (int r = 0; r < WI; ++r)
+#pragma unroll
+                for (int c = 0; c < WJ; ++c) {
+                    float t, err;
+                    two_sum(s1[r][c], a1[r][c], t, err);
+                    s1[r][c] = t;
+                    e1[r][c] += err;
+                    two_sum(s2[r][c], acc[r][c].x + acc[r][c].y, t, err);
+                    s2[r][c] = t;
+                    e2[r][c] += err;
+                    a1[r][c] = 0.0f;
+                    acc[r][c] = make_float2(0.0f, 0.0f);
+                }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        if (++st == STAGES) {
+            st = 0;
+            ph ^= 1u;
+        }
+        if (*abort_flag) break;
+    }
+
+    // never leave with a copy in flight (bounded waits on the last phases)
+    if (threadIdx.x == 0)
+        for (int k = max(0, issued - STAGES); k < issued; ++k)
+            (void)mbar_wait_bounded(&full[k % STAGES], (k / STAGES) & 1);
+
+    // Cross-lane reduction through shared memory, one moment at a time: each
+    // lane stores its (hi, lo) sums, then lane L adds the sums of 32 / LPC
+    // source lanes for one pair (compensated, fixed order) and LPC lanes
+    // join by xor shuffles.  The ring is free once every warp has passed the
+    // barrier below (thread 0 has waited for the last copies).
+    __syncthreads();
+    constexpr int NP = WI * WJ;
+    constexpr int LPC = 32 / NP;   // lanes per pair
+    constexpr int SRC = 32 / LPC;  // source lanes summed by each lane
+    static_assert(32 % NP == 0, "pairs per warp divide the warp");
+    float *red = buf + warp * (NP * 2 * 33);   // [NP][hi, lo][33], padded rows
+    float2 *mom = P.mom + (size_t)split * P.p * P.p * 2;
+    const int e = lane / LPC, part = lane % LPC;
+    const int pi = pi0 + e / WJ, pj = pj0 + e % WJ;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+#pragma unroll
+        for (int r = 0; r < WI; ++r)
+#pragma unroll
+            for (int c = 0; c < WJ; ++c) {
+                const int q = r * WJ + c;
+                red[(q * 2 + 0) * 33 + lane] = m == 0 ? s1[r][c] : s2[r][c];
+                red[(q * 2 + 1) * 33 + lane] = m == 0 ? e1[r][c] : e2[r][c];
+            }
+        __syncwarp();
+        float h = 0.0f, l = 0.0f;
+#pragma unroll
+        for (int k2 = 0; k2 < SRC; ++k2) {
+            const int src = part * SRC + k2;
+            float t, err;
+            two_sum(h, red[(e * 2 + 0) * 33 + src], t, err);
+            h = t;
+            l = (l + red[(e * 2 + 1) * 33 + src]) + err;
+        }
+#pragma unroll
+        for (int o = LPC / 2; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+            float t, err;
+            two_sum(h, oh, t, err);
+            h = t;
+            l = (l + ol) + err;
+        }
+        if (part == 0 && pi < P.p && pj < P.p && pi != pj) {
+            float t, err;
+            two_sum(h, l, t, err);
+            mom[((size_t)pi * P.p + pj) * 2 + m] = make_float2(t, err);
+        }
+        __syncwarp();
+    }
+}
+
 // One launch covers the tiles of every instance in the batch: prefix[k] is the
 // first CTA of instance k (tiles_i * tiles_j * nsplit CTAs each).
 template <int MODE, int CFG>
@@ -393,7 +730,14 @@ __device__ __forceinline__ void pair_dispatch(const CUtensorMap *tmI, const CUte
     const int local = b - prefix[lo];
     const int tiles = P.tiles_i * P.tiles_j;
     const int split = local / tiles, tile = local % tiles;
-    pair_block<MODE, CFG>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
+    if (P.shard_n > 1 &&
+        shard_owner((tile / P.tiles_j) * PAIR_CFGS[CFG].ti(), (tile % P.tiles_j) * PAIR_CFGS[CFG].tj(),
+                    P.p, P.shard_n) != P.shard_rank)
+        return;   // another rank's tile
+    if constexpr (PAIR_CFGS[CFG].sub > 0)
+        pair_block_v2<MODE, CFG>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
+    else
+        pair_block<MODE, CFG>(tmI, tmJ, P, tile / P.tiles_j, tile % P.tiles_j, split);
 }
 
 // One kernel per form and tile configuration; the register cap of each
@@ -423,8 +767,9 @@ struct PairTable {
     static constexpr PairKernel fast[sizeof...(C)] = {k_pair_fast_b<C>...};
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
-using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
-static_assert(PAIR_NCFG == 16, "PairKernels lists every configuration");
+using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19,
+                              20, 21, 22, 23, 24, 25>;
+static_assert(PAIR_NCFG == 26, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {
@@ -434,7 +779,7 @@ static PairKernel pair_kernel(int mode, int cfg)
 size_t pair_smem_bytes(int cfg)
 {
     const PairCfg &G = PAIR_CFGS[cfg];
-    return 1024 + (size_t)G.stages * (G.ti() + G.tj()) * PAIR_S * 4;
+    return 1024 + (size_t)G.stages * (G.sub > 0 ? G.sub : 1) * (G.ti() + G.tj()) * PAIR_S * 4;
 }
 
 static int g_pair_occ[2][PAIR_NCFG];

@@ -72,6 +72,32 @@ cudaError_t launch_pack(const void *X, int is_f64, int layout, int64_t ld, int n
     return cudaGetLastError();
 }
 
+// Input gate: one thread waits until the 32-bit flag (device memory or
+// host-mapped memory) is non-zero, with acquire ordering at system scope so
+// the data written before the flag is seen by the kernels that follow.  The
+// wait is bounded by limit_ns of global time (and an iteration cap); when it
+// runs out the kernel records ST_TIMEOUT and returns.
+__global__ void k_gate_wait(const uint32_t *flag, uint64_t limit_ns, uint32_t *status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t v;
+        asm volatile("ld.acquire.sys.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0u) return;
+        if (global_ns() - t0 > limit_ns) break;
+        __nanosleep(500);
+    }
+    set_status(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_gate_wait(const uint32_t *flag, uint64_t limit_ns, uint32_t *status,
+                             cudaStream_t s)
+{
+    k_gate_wait<<<1, 32, 0, s>>>(flag, limit_ns, status);
+    return cudaGetLastError();
+}
+
 // Row-major FP32 rows X[rows[s]] (rows == nullptr: X[s]) -> R [d][ldr] FP64
 // (bootstrap resampling gathers the sampled rows while transposing).
 __global__ void k_pack_gather(const float *__restrict__ X, int64_t ld, const int32_t *__restrict__ rows,

@@ -13,7 +13,8 @@ namespace lg {
 // ------------------------------------------------------------------------
 //
 // I(i, j) = (h(z_j) + h(r_i^j)) - (h(z_i) + h(r_j^i)) with h = H - H(nu);
-// M(i) = -sum_{j != i} min(0, I(i, j))^2, summed by each lane over j in
+// M(i) = -sum_{j != i} min(0, I(i, j))^2 (with a shard set, over the entries
+// the rank owns: partial M and E, summed over ranks by the caller), summed by each lane over j in
 // ascending order and across lanes by a fixed xor tree.  E(i) bounds |M(i) -
 // M_exact(i)| given |I - I_exact| <= eps per entry: a fixed epsI for steps
 // scored in double-float, else the moment-error model of ErrModel.
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
         const float wi = wsh[i];
         for (int j = wr * 32 + lane; j < P.p; j += 32 * SCORE_WPR) {
             if (j == i) continue;
+            if (P.shard_n > 1 && shard_owner(i, j, P.p, P.shard_n) != P.shard_rank) continue;
             float mf[4];
             const dfl I = score_entry_df(P, i, j, hd, c1, b1, c2, mf);
             float eps = (float)P.epsI;

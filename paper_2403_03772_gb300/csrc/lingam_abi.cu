@@ -123,6 +123,22 @@ struct StepSplit {
     int cfg = 0;           // pair-kernel tile configuration of the step
 };
 
+enum LaunchKind {
+    K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO
+};
+
+// Timing events per ordering step when profiling: before the pair moments,
+// after them, after score + select, after the FP64 passes, after regress-out.
+constexpr int EV_PER_STEP = 5;
+
+struct Launch {
+    LaunchKind kind;
+    size_t off = 0, off2 = 0;
+    int count = 0, a = 0, b = 0, c = 0;
+    int x = 0;   // K_SCORE of a sharded call: p of the step whose partial M, E are exchanged
+};
+
 struct Plan {
     std::vector<InstSpec> spec;
     int prec = -1, profile = -1, scores = -1, lcoef = -1, rows = -1;
@@ -136,6 +152,8 @@ struct Plan {
     CUtensorMap tmI[PAIR_NCFG]{}, tmJ[PAIR_NCFG]{};   // per tile configuration
     std::vector<cudaEvent_t> pev;
     std::vector<double> punits;
+    std::vector<Launch> eager;   // sharded calls: the launches, run in order with the
+                                 // exchange after each sharded score (no graph)
 };
 
 }  // namespace
@@ -156,6 +174,13 @@ struct lingam_ctx {
     lingam_tuning tune[2]{};   // pair-kernel choices: [0] accurate (FP32), [1] fast (MIXED)
     Buf prior;                 // prior ancestry knowledge [prior_d][prior_d] int8, or none
     int64_t prior_d = 0;
+    const uint32_t *gate = nullptr;   // input gate flag (lingam_set_input_gate), or none
+    uint64_t gate_ns = 0;
+    // pair sharding (lingam_set_shard): this rank's slice of the pair space
+    int shard_rank = 0, shard_n = 1;
+    lingam_allreduce_fn allreduce = nullptr;
+    void *allreduce_user = nullptr;
+    std::vector<double> xbuf;         // host buffer of the exchange
 };
 
 static std::string g_create_error;
@@ -277,6 +302,8 @@ static StepSplit step_splits(const lingam_ctx *ctx, const std::vector<InstSpec> 
         if (p >= 2 && !step_hp(prec, p)) tiles += pair_tiles(p, ss.cfg);
         cols += std::max(1, p - 1);
     }
+    // a sharded rank runs about 1 / shard_n of the tiles: split its samples finer
+    if (ctx->shard_n > 1) tiles = (tiles + ctx->shard_n - 1) / ctx->shard_n;
     const int64_t target_pair = (int64_t)ctx->num_sms * std::max(1, tb.ctas_per_sm[b]);
     const int64_t target = (int64_t)ctx->num_sms * 4;
     const int ns_reg = cols > 0 ? (int)std::max<int64_t>(1, (target + cols - 1) / cols) : 1;
@@ -342,6 +369,7 @@ static void destroy_plan(Plan &pl)
     pl.spec.clear();
     pl.prec = pl.profile = pl.scores = pl.lcoef = pl.rows = -1;
     pl.partial = false;
+    pl.eager.clear();
 }
 
 // Lay out and allocate the arenas of a batch (no graph yet).
@@ -520,20 +548,63 @@ struct ParamBlob {
     }
 };
 
-enum LaunchKind {
-    K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO
-};
-
-// Timing events per ordering step when profiling: before the pair moments,
-// after them, after score + select, after the FP64 passes, after regress-out.
-constexpr int EV_PER_STEP = 5;
-
-struct Launch {
-    LaunchKind kind;
-    size_t off = 0, off2 = 0;
-    int count = 0, a = 0, b = 0, c = 0;
-};
+// Issue one launch of a plan on stream s (captured into the plan's graph, or
+// run directly by a sharded call); *nodes counts the kernel nodes.
+static cudaError_t issue_launch(Plan &pl, const Launch &l, char *pb, cudaStream_t s, bool capture,
+                                int *nodes)
+{
+    void *P = pb + l.off;
+    cudaError_t e = cudaSuccess;
+    switch (l.kind) {
+    case K_GRAM: e = launch_gram_b((const GramParams *)P, l.count, l.a, l.b, s); ++*nodes; break;
+    case K_IOTA: e = launch_iota_b((const IotaParams *)P, l.count, l.a, s); break;
+    case K_REG_INIT:
+        e = launch_regress_b((const RegressParams *)P, (const int *)(pb + l.off2), l.count,
+                             true, l.a, s);
+        break;
+    case K_PAIR:
+        e = launch_pair_b(l.c, l.b, &pl.tmI[l.b], &pl.tmJ[l.b], (const PairParams *)P,
+                          (const int *)(pb + l.off2), l.count, l.a, s);
+        break;
+    case K_HP_ALL: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
+    case K_SCORE:
+        e = launch_score_b((const ScoreParams *)P, (const int *)(pb + l.off2), l.count, l.b,
+                           l.a, s);
+        break;
+    case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
+    case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
+    case K_REFINE:
+        e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
+        break;
+    case K_REGRESS:
+        e = launch_regress_b((const RegressParams *)P, (const int *)(pb + l.off2), l.count,
+                             false, l.a, s);
+        break;
+    case K_DOWNDATE:
+        e = launch_downdate_b((const DowndateParams *)P, (const int *)(pb + l.off2), l.count,
+                              l.a, s);
+        break;
+    case K_FINISH: e = launch_finish_b((const FinishParams *)P, l.count, s); break;
+    case K_EVENT:
+        e = capture ? cudaEventRecordWithFlags(pl.pev[l.a], s, cudaEventRecordExternal)
+                    : cudaEventRecord(pl.pev[l.a], s);
+        --*nodes;
+        break;
+    case K_GRAM_TC: {
+        InstDev &I = pl.inst[l.c];
+        e = launch_gram_tc(&I.tmS, I.R, I.ldr, (int)I.n, (int)I.d, I.S, I.expo, I.Cpart,
+                           I.tc_ksplit, I.C, I.d, I.ref_var, &I.state->status, s);
+        *nodes += 2;
+        break;
+    }
+    case K_ZLO: e = launch_zlo_b((const ZloParams *)P, l.count, l.a, s); break;
+    case K_FILL_NAN:
+        e = launch_fill_nan(pl.inst[l.c].hist, (size_t)pl.inst[l.c].d * pl.inst[l.c].d, s);
+        break;
+    }
+    ++*nodes;
+    return e;
+}
 
 // Capture the covariance + ordering loop of the current plan into one graph.
 // stop_after_score0 captures only the first step up to its scores (and writes
@@ -545,6 +616,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     const int K = (int)pl.inst.size();
     const int prec = pl.prec;
     const bool profile = ctx->opts.profile != 0 && !stop_after_score0;
+    const bool sharded = ctx->shard_n > 1;
     cudaStream_t s = ctx->s;
     const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
     // Moment-error model of the FP32 pair kernels and the regress kernel
@@ -671,6 +743,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         std::vector<RegressParams> rg;
         std::vector<DowndateParams> dd;
         int maxp = 0, maxcols = 0, maxsplit = 1;
+        int xp = 0;   // p of a sharded FP32-scored step (its partial scores are exchanged)
         double units = 0;
         for (int k = 0; k < K; ++k) {
             InstDev &I = pl.inst[k];
@@ -689,7 +762,9 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             auto hpp = [&](int mode, int with_vars, double *mom) {
                 HpParams F{};
                 // entries whose FP32 I clears the FP32 bound need no re-score
-                F.I32 = (mode == 1 && !hp) ? I.I32 : nullptr;
+                // a sharded rank holds only its own entries' bounds, and every rank
+                // must re-score identically: no skipping by the FP32 bounds then
+                F.I32 = (mode == 1 && !hp && !sharded) ? I.I32 : nullptr;
                 F.R = I.R;
                 F.ldr = I.ldr;
                 F.zhi = zbase + (int64_t)I.zrow * pl.ldz;
@@ -755,6 +830,8 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 P.status = &I.state->status;
                 P.row0 = I.zrow;
                 P.isd = isd;
+                P.shard_rank = ctx->shard_rank;
+                P.shard_n = ctx->shard_n;
                 pp.push_back(P);
                 prefix.push_back(prefix.back() + P.tiles_i * P.tiles_j * P.nsplit);
                 S.mom2 = reinterpret_cast<const float2 *>(I.mom);
@@ -770,6 +847,9 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 S.C = I.C;
                 S.ldc = I.d;
                 S.isd = isd;
+                S.shard_rank = ctx->shard_rank;
+                S.shard_n = ctx->shard_n;
+                xp = p;
             }
             S.p = p;
             S.n = n;
@@ -872,6 +952,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         ls.count = cnt;
         ls.a = maxp;
         ls.b = pres.back();
+        ls.x = sharded && !stop_after_score0 ? xp : 0;
         L.push_back(ls);
         if (stop_after_score0) break;
         Launch lse{K_SELECT};
@@ -949,58 +1030,23 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     CK(cudaMemcpy(pl.params.p, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice));
     char *pb = reinterpret_cast<char *>(pl.params.p);
 
+    if (sharded && !stop_after_score0) {
+        // a sharded call runs the launches in order and exchanges the partial
+        // scores after each sharded score launch (run_plan), so no graph
+        if (pl.exec) cudaGraphExecDestroy(pl.exec);
+        pl.exec = nullptr;
+        pl.eager = L;
+        pl.nodes = 0;
+        for (const Launch &l : L) pl.nodes += l.kind == K_EVENT ? 0 : (l.kind == K_GRAM_TC ? 3 : 1);
+        pl.profile = profile ? 1 : 0;
+        pl.partial = false;
+        return LINGAM_OK;
+    }
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int nodes = 0;
     cudaError_t e = cudaSuccess;
     for (const Launch &l : L) {
-        void *P = pb + l.off;
-        switch (l.kind) {
-        case K_GRAM: e = launch_gram_b((const GramParams *)P, l.count, l.a, l.b, s); ++nodes; break;
-        case K_IOTA: e = launch_iota_b((const IotaParams *)P, l.count, l.a, s); break;
-        case K_REG_INIT:
-            e = launch_regress_b((const RegressParams *)P, (const int *)(pb + l.off2), l.count,
-                                 true, l.a, s);
-            break;
-        case K_PAIR:
-            e = launch_pair_b(l.c, l.b, &pl.tmI[l.b], &pl.tmJ[l.b], (const PairParams *)P,
-                              (const int *)(pb + l.off2), l.count, l.a, s);
-            break;
-        case K_HP_ALL: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
-        case K_SCORE:
-            e = launch_score_b((const ScoreParams *)P, (const int *)(pb + l.off2), l.count, l.b,
-                               l.a, s);
-            break;
-        case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
-        case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
-        case K_REFINE:
-            e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
-            break;
-        case K_REGRESS:
-            e = launch_regress_b((const RegressParams *)P, (const int *)(pb + l.off2), l.count,
-                                 false, l.a, s);
-            break;
-        case K_DOWNDATE:
-            e = launch_downdate_b((const DowndateParams *)P, (const int *)(pb + l.off2), l.count,
-                                  l.a, s);
-            break;
-        case K_FINISH: e = launch_finish_b((const FinishParams *)P, l.count, s); break;
-        case K_EVENT:
-            e = cudaEventRecordWithFlags(pl.pev[l.a], s, cudaEventRecordExternal);
-            --nodes;
-            break;
-        case K_GRAM_TC: {
-            InstDev &I = pl.inst[l.c];
-            e = launch_gram_tc(&I.tmS, I.R, I.ldr, (int)I.n, (int)I.d, I.S, I.expo, I.Cpart,
-                               I.tc_ksplit, I.C, I.d, I.ref_var, &I.state->status, s);
-            nodes += 2;
-            break;
-        }
-        case K_ZLO: e = launch_zlo_b((const ZloParams *)P, l.count, l.a, s); break;
-        case K_FILL_NAN:
-            e = launch_fill_nan(pl.inst[l.c].hist, (size_t)pl.inst[l.c].d * pl.inst[l.c].d, s);
-            break;
-        }
-        ++nodes;
+        e = issue_launch(pl, l, pb, s, true, &nodes);
         if (e != cudaSuccess) break;
     }
     cudaGraph_t g = nullptr;
@@ -1026,6 +1072,9 @@ static lingam_status ensure_plan(lingam_ctx *ctx, const std::vector<InstSpec> &s
                                  bool lcoef, bool rows, bool stop_after_score0 = false,
                                  double *Iout = nullptr, double *epsOut = nullptr)
 {
+    if (ctx->shard_n > 1 && (spec.size() != 1 || scores))
+        return fail(ctx, LINGAM_ERR_ARG,
+                    "a sharded context orders one instance per call and records no score history");
     Plan &pl = ctx->plan;
     const int prec = ctx->opts.precision;
     if (ctx->prior_d > 0 && !stop_after_score0)
@@ -1134,13 +1183,49 @@ static lingam_status end_call(lingam_ctx *ctx, cudaStream_t user)
 }
 
 // Launch the plan graph and read back orders, scores and states.
+// A sharded call: the plan's launches in order; after each sharded score
+// launch the rank's partial M and E (p + p doubles) go to the caller's
+// all-reduce, whose sums every rank then uses identically (select, re-score
+// tiers, regress-out and downdate are replicated).  One exchange per step.
+static lingam_status run_eager(lingam_ctx *ctx)
+{
+    Plan &pl = ctx->plan;
+    char *pb = reinterpret_cast<char *>(pl.params.p);
+    InstDev &I = pl.inst[0];
+    int nodes = 0;
+    for (const Launch &l : pl.eager) {
+        CK(issue_launch(pl, l, pb, ctx->s, false, &nodes));
+        if (l.kind != K_SCORE || l.x <= 0) continue;
+        const int p = l.x;
+        ctx->xbuf.resize((size_t)2 * p);
+        CK(cudaMemcpyAsync(ctx->xbuf.data(), I.M, (size_t)p * 8, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaMemcpyAsync(ctx->xbuf.data() + p, I.E, (size_t)p * 8, cudaMemcpyDeviceToHost,
+                           ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        const int rc = ctx->allreduce(ctx->xbuf.data(), (int64_t)2 * p, ctx->allreduce_user);
+        if (rc != 0)
+            return fail(ctx, LINGAM_ERR_CUDA,
+                        "the all-reduce callback of the sharded ordering failed (returned " +
+                            std::to_string(rc) + ")");
+        CK(cudaMemcpyAsync(I.M, ctx->xbuf.data(), (size_t)p * 8, cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaMemcpyAsync(I.E, ctx->xbuf.data() + p, (size_t)p * 8, cudaMemcpyHostToDevice,
+                           ctx->s));
+    }
+    return LINGAM_OK;
+}
+
 static lingam_status run_plan(lingam_ctx *ctx, int32_t *const *orders_out, double *scores_out,
                               std::vector<DevState> &hs)
 {
     Plan &pl = ctx->plan;
     const int K = (int)pl.inst.size();
     CK(cudaEventRecord(ctx->g0, ctx->s));
-    CK(cudaGraphLaunch(pl.exec, ctx->s));
+    if (!pl.eager.empty()) {
+        lingam_status st = run_eager(ctx);
+        if (st) return st;
+    } else {
+        CK(cudaGraphLaunch(pl.exec, ctx->s));
+    }
     CK(cudaEventRecord(ctx->g1, ctx->s));
     for (int k = 0; k < K; ++k)
         if (orders_out && orders_out[k])
@@ -1208,6 +1293,7 @@ static lingam_status load_single(lingam_ctx *ctx, const void *X, int64_t n, int6
     lingam_status st = stage(ctx, X, bytes, &off, &dX);
     if (st) return st;
     CK(cudaMemsetAsync(&I.state->status, 0, sizeof(uint32_t), ctx->s));
+    if (ctx->gate) CK(launch_gate_wait(ctx->gate, ctx->gate_ns, &I.state->status, ctx->s));
     CK(launch_pack(dX, is64, layout, ld, (int)n, (int)d, I.R, I.ldr, &I.state->status, ctx->s));
     CK(launch_center(I.R, I.ldr, (int)n, (int)d, ctx->s));
     return LINGAM_OK;
@@ -1883,12 +1969,62 @@ lingam_status lingam_set_prior_knowledge(lingam_ctx *ctx, const int8_t *prior, i
 
 static_assert(PAIR_NCFG == LINGAM_PAIR_TILES, "the C ABI announces every configuration");
 
+lingam_status lingam_set_shard(lingam_ctx *ctx, int32_t rank, int32_t nranks,
+                               lingam_allreduce_fn allreduce, void *user)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (nranks < 1 || rank < 0 || rank >= nranks)
+        return fail(ctx, LINGAM_ERR_ARG, "need 0 <= rank < nranks");
+    if (nranks > 1 && !allreduce) return fail(ctx, LINGAM_ERR_ARG, "a sharded context needs an all-reduce");
+    ctx->shard_rank = nranks > 1 ? rank : 0;
+    ctx->shard_n = nranks;
+    ctx->allreduce = nranks > 1 ? allreduce : nullptr;
+    ctx->allreduce_user = nranks > 1 ? user : nullptr;
+    destroy_plan(ctx->plan);   // the graphs depend on the slice
+    return LINGAM_OK;
+}
+
+int32_t lingam_shard_owner(int64_t i, int64_t j, int64_t p, int32_t nranks)
+{
+    if (nranks < 1 || p < 1 || p > INT32_MAX || i < 0 || j < 0 || i >= p || j >= p) return -1;
+    return shard_owner((int)i, (int)j, (int)p, nranks);
+}
+
+lingam_status lingam_set_input_gate(lingam_ctx *ctx, const uint32_t *flag, double timeout_s)
+{
+    if (!ctx) return LINGAM_ERR_ARG;
+    ctx->err.clear();
+    if (!flag) {
+        ctx->gate = nullptr;
+        ctx->gate_ns = 0;
+        return LINGAM_OK;
+    }
+    if (!(timeout_s > 0.0 && timeout_s <= 60.0))
+        return fail(ctx, LINGAM_ERR_ARG, "the gate's timeout must be in (0, 60] seconds");
+    if ((reinterpret_cast<uintptr_t>(flag) & 3u) != 0)
+        return fail(ctx, LINGAM_ERR_ARG, "the gate flag must be 4-byte aligned");
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, flag) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LINGAM_ERR_ARG, "the gate flag is not memory the device can read");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged &&
+        !(a.type == cudaMemoryTypeHost && a.devicePointer != nullptr))
+        return fail(ctx, LINGAM_ERR_ARG,
+                    "the gate flag must be device, managed or mapped host memory");
+    ctx->gate = a.type == cudaMemoryTypeHost ? reinterpret_cast<const uint32_t *>(a.devicePointer)
+                                             : flag;
+    ctx->gate_ns = (uint64_t)(timeout_s * 1e9);
+    return LINGAM_OK;
+}
+
 lingam_status lingam_pair_tile_info(int32_t tile, int32_t *out)
 {
     if (!out || tile < 0 || tile >= PAIR_NCFG) return LINGAM_ERR_ARG;
     const PairCfg &G = PAIR_CFGS[tile];
-    const int32_t v[8] = {G.wi, G.wj, G.wgi, G.wgj, G.stages, G.groups, G.fold, G.packed};
-    for (int k = 0; k < 8; ++k) out[k] = v[k];
+    const int32_t v[9] = {G.wi, G.wj, G.wgi, G.wgj, G.stages, G.groups, G.fold, G.packed, G.sub};
+    for (int k = 0; k < 9; ++k) out[k] = v[k];
     return LINGAM_OK;
 }
 

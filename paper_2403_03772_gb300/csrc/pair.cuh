@@ -20,6 +20,8 @@ struct PairCfg {
     int groups;              // groups of 4 samples per lane and iteration (1 or 2)
     int fold;                // chunks between compensated folds of the FP32 partial sums
     int packed;              // fast form: two samples per paired-FP32 instruction
+    int sub;                 // 0: one chunk per ring stage (pair_block); >= 1: the streamlined
+                             // block (pair_block_v2) with `sub` chunks per stage
     constexpr int ti() const { return wi * wgi; }
     constexpr int tj() const { return wj * wgj; }
     constexpr int warps() const { return wgi * wgj; }
@@ -42,9 +44,22 @@ constexpr PairCfg PAIR_CFGS[] = {
     {2, 2, 1, 4, 3, 80, 80, 2, 8, 1},  // 13: 128 threads, 2 x 8 tile, paired, 6 CTAs per SM
     {2, 2, 2, 4, 4, 80, 80, 2, 8, 1},  // 14: 256 threads, 4 x 8 tile, paired, 3 CTAs per SM
     {4, 2, 1, 4, 3, 96, 96, 2, 8, 1},  // 15: as 10 with 96 registers, 5 CTAs per SM
+    // streamlined block: row-by-row loads, float2 S2 sums kept across chunks,
+    // incremental ring bookkeeping, `sub` chunks per ring stage
+    {4, 2, 1, 4, 2, 128, 128, 2, 8, 1, 2},   // 16: 4 x 8 tile, 2 stages of 2 chunks, 4 CTAs per SM
+    {2, 2, 1, 4, 2, 80, 80, 2, 8, 1, 2},     // 17: 2 x 8 tile, 2 stages of 2 chunks, 5 CTAs per SM
+    {4, 2, 2, 4, 2, 128, 128, 2, 8, 1, 2},   // 18: 8 x 8 tile, 256 threads, 2 CTAs per SM
+    {2, 2, 2, 4, 2, 80, 80, 2, 8, 1, 2},     // 19: 4 x 8 tile, 256 threads, 3 CTAs per SM
+    {4, 2, 1, 4, 3, 96, 96, 2, 8, 1, 1},     // 20: as 15, streamlined
+    {2, 2, 1, 4, 3, 80, 80, 2, 8, 1, 1},     // 21: as 13, streamlined, 6 CTAs per SM
+    {2, 2, 2, 4, 3, 80, 80, 2, 8, 1, 2},     // 22: as 19 with 3 stages
+    {2, 2, 2, 4, 2, 80, 80, 2, 8, 1, 4},     // 23: as 19 with stages of 4 chunks, 2 CTAs per SM
+    {2, 2, 2, 4, 3, 80, 80, 2, 16, 1, 2},    // 24: as 22, folds every 16 chunks
+    {4, 2, 1, 4, 2, 128, 128, 2, 16, 1, 2},  // 25: as 16, folds every 16 chunks
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
+static_assert(SHARD_BLOCK % 16 == 0, "tile sides (at most 16) divide the shard block");
 
 // Scale folded into the fast-form residual: u~ = KSC * u makes
 // 2^(-u~^2) = exp(-u^2/2).
@@ -66,6 +81,7 @@ struct PairParams {
     uint32_t *status;
     int row0;             // first row of this instance in the z tensor
     const double *isd;    // [p] 1 / sqrt(C_ii) by position
+    int shard_rank, shard_n;   // shard_n > 1: only tiles this rank owns (shard_owner)
 };
 
 }  // namespace lg

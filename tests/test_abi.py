@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "lingam.h")
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^(?:lingam_status|const char \*)\s*(\w+)\(", txt, re.M)))
+    return sorted(set(re.findall(r"^(?:lingam_status|const char \*|int32_t)\s*(\w+)\(", txt, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -116,6 +116,32 @@ def test_pair_tile_info_describes_every_tile(lib):
         assert 32 * g["wgi"] * g["wgj"] <= 1024
         assert g["groups"] in (1, 2) and g["packed"] in (0, 1) and g["fold"] >= 1
         assert g["stages"] >= 2 and g["wi"] >= 1 and g["wj"] >= 1
+        assert g["sub"] in (0, 1, 2, 4)
+        # the streamlined block folds on power-of-two chunk counts
+        assert g["sub"] == 0 or (g["fold"] & (g["fold"] - 1)) == 0
     for bad in (-1, n):
         with pytest.raises(pkg.LingamError):
             pkg.lingam_pair_tile_info(bad)
+
+
+def test_shard_ownership_partitions_pairs_symmetrically_and_by_tile(lib):
+    """lingam_shard_owner (host, no GPU): every ordered pair has one owner,
+    (i, j) and (j, i) the same one, the ranks' shares are within 1 % of equal
+    at p = 1000, and every pair-kernel tile lies inside one owner's share."""
+    import numpy as np
+    import paper_2403_03772_gb300 as pkg
+    assert pkg.shard_owner(0, 0, 1, 3) == 0 and pkg.shard_owner(5, 0, 4, 2) == -1
+    for p, R in [(40, 2), (100, 3), (257, 5), (1000, 3)]:
+        own = np.array([[pkg.shard_owner(i, j, p, R) for j in range(p)] for i in range(p)])
+        assert own.min() >= 0 and own.max() < R and np.array_equal(own, own.T)
+        if p == 1000:
+            off = ~np.eye(p, dtype=bool)
+            counts = [int(((own == r) & off).sum()) for r in range(R)]
+            assert max(counts) - min(counts) < 0.01 * p * (p - 1) / R
+        for t in range(pkg.PAIR_TILES):
+            g = pkg.lingam_pair_tile_info(t)
+            ti, tj = g["wi"] * g["wgi"], g["wj"] * g["wgj"]
+            for a in range(0, p, ti):
+                for b in range(0, p, tj):
+                    blk = own[a:a + ti, b:b + tj]
+                    assert np.all(blk == blk.flat[0])

@@ -6,7 +6,9 @@ the checks are (a) the stored oracle order written by
 tests/golden/make_golden.py, when present; (b) first-step scores M(i) of
 sampled variables, which the oracle computes one by one (literal Algorithm 1
 rows); (c) properties that hold at any size; (d) adjacency rows along the true
-causal order against the oracle's least squares.
+causal order against the oracle's least squares; (e) scores of sampled
+variables at later steps, on the oracle's residual data replayed along the
+GPU's order (Sec. 2.2), one literal Algorithm 1 row at a time.
 """
 import numpy as np
 import pytest
@@ -73,3 +75,34 @@ def test_adjacency_rows_along_true_order(cfg3):
     rows = [int(cfg3.order[k]) for k in (1, 10, 400, 999)]
     ref = oracle.adjacency_rows(cfg3.X, cfg3.order, rows)
     assert np.max(np.abs(B[rows] - ref)) < B_ABS
+
+
+LATER_STEPS = (1, 200, 500)
+
+
+@pytest.fixture(scope="module")
+def later_rows(cfg3, runs):
+    """Oracle rows at LATER_STEPS on the residual data along the mixed form's
+    order (which the stored-order test pins to the oracle's)."""
+    order = runs["mixed"][0]
+    res = oracle.Residuals(cfg3.X, order)
+    out = {}
+    for t in LATER_STEPS:
+        res.advance(t)
+        U = res.U
+        pos = sorted({0, U.size // 3, U.size // 2, U.size - 1,
+                      int(np.searchsorted(U, order[t]))})
+        out[t] = (U, U[pos], oracle.row_scores(res.data, pos, U=U))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_later_step_rows_match_oracle(runs, later_rows, prec):
+    order, scores, _ = runs[prec]
+    assert list(order[:max(LATER_STEPS) + 1]) == list(runs["mixed"][0][:max(LATER_STEPS) + 1])
+    for t, (U, vars_, ref) in later_rows.items():
+        row = scores[t]
+        assert np.all(np.isfinite(row[U])) and np.all(np.isnan(np.delete(row, U)))
+        scale = np.max(np.abs(row[U]))
+        assert np.all(np.abs(row[vars_] - ref) <= M_REL * scale + M_ABS), t
+        assert int(np.nanargmax(row)) == int(order[t])

@@ -9,7 +9,11 @@ from gpu_util import read_golden_order, scores_close
 
 pytestmark = pytest.mark.gpu
 
-N_CFG = 16
+import os as _os
+import re as _re
+
+N_CFG = int(_re.search(r"#define LINGAM_PAIR_TILES (\d+)", open(_os.path.join(
+    _os.path.dirname(_os.path.dirname(_os.path.abspath(__file__))), "include", "lingam.h")).read()).group(1))
 
 
 @pytest.fixture(scope="module")

@@ -1,7 +1,11 @@
 """Multi-rank host logic on CPU with gloo (world_size 2): the bench's rank
-seeding, max-over-ranks timing and whole-job value, and the exchange a
-pair-sharded ordering step would need (partial scores summed across ranks,
-then a replicated argmax) -- checked against the single-rank result."""
+seeding, max-over-ranks timing and whole-job value, and one step of the
+library's pair sharding as far as it runs without a GPU -- each rank keeps
+the oracle's I(i, j) entries that lingam_shard_owner gives it, forms partial
+M and error sums, and exchanges them the way the sharded ordering's
+all-reduce callback must (gather, add in rank order, identical on every
+rank); the replicated argmax then matches the single-rank step.  The GPU
+form of the same exchange is tests/test_gpu_shard.py."""
 import os
 import socket
 
@@ -29,17 +33,24 @@ def _worker(rank, world, port, I, out):
         seed = bench.rank_seed(1003, rank)
         t = bench.max_over_ranks(100.0 + 50.0 * rank, world)
         val = bench.job_throughput(1e12, world, 3, t)
-        # sharded scoring of one step: rank r owns the pairs (i, j) with
-        # (i * p + j) % world == r and sums min(0, I)^2 over them
+        # sharded scoring of one step: rank r keeps the entries the library's
+        # ownership gives it (a partition of the off-diagonal pairs)
+        import paper_2403_03772_gb300 as pkg
         p = I.shape[0]
-        part = np.zeros(p)
+        part = np.zeros(2 * p)
         for i in range(p):
             for j in range(p):
-                if i != j and (i * p + j) % world == rank:
+                if i != j and pkg.shard_owner(i, j, p, world) == rank:
                     part[i] += min(0.0, I[i, j]) ** 2
-        tm = torch.from_numpy(part)
-        dist.all_reduce(tm, op=dist.ReduceOp.SUM)
-        M = -tm.numpy()
+                    part[p + i] += 1.0                 # stands in for the error sums
+        # the exchange contract: sums identical bit for bit on every rank
+        gathered = [torch.zeros(2 * p, dtype=torch.float64) for _ in range(world)]
+        dist.all_gather(gathered, torch.from_numpy(part))
+        total = np.zeros(2 * p)
+        for g in gathered:
+            total += g.numpy()
+        M = -total[:p]
+        assert np.all(total[p:] == p - 1)               # every entry counted once
         best = max(range(p), key=lambda a: (M[a], -a))
         out.put((rank, seed, t, val, best, M.tolist()))
     finally:
