@@ -473,24 +473,37 @@ def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float)
 # under profiles/ gives the command).  It describes only the kernel source it
 # was taken on, identified by the SHA-256 of these files; after any change
 # the roofline reports traffic null until the capture is repeated.
-PAIR_TRAFFIC = {"bytes_per_launch": 23.10e6, "launches": 968, "tile": 15,
-                "sources": ["paper_2403_03772_gb300/csrc/kernels_pair.cu",
-                            "paper_2403_03772_gb300/csrc/pair.cuh",
-                            "paper_2403_03772_gb300/csrc/common.cuh"],
-                "sha256": "5ebd9a53eb6cb91f6ce3c17f98dd19c947515c59626e57d943906414fc5eff4e"}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# fast pair-kernel launch at p = 1000 of the d = 1000, n = 10000 order (the
+# first step; one ncu capture, profiles/k_pair_fast_b_cfg24_d1000_n10000.md),
+# against the 40 MB of z columns that launch must read.  Reported only while
+# the kernel's sources are the captured ones.
+PAIR_TRAFFIC = {"bytes_per_launch": 45.06e6, "algorithmic_bytes": 40.0e6, "p": 1000, "tile": 24,
+                "sources": ['paper_2403_03772_gb300/csrc/kernels_pair.cu', 'paper_2403_03772_gb300/csrc/pair.cuh', 'paper_2403_03772_gb300/csrc/common.cuh'],
+                "sha256": "f051010d45de21aa341009e6b2bb5c31f3747a8e61388cb9788602d4d400a6dd"}
+
+# Issue slots per residual-sample of the plain FP32 pair kernel (CUDA's
+# accurate expf / log1pf; one ncu capture at p = 1000,
+# profiles/k_pair_accurate_b_cfg14_d1000_n10000.md): its bound is the issue
+# rate, 128 thread instructions per SM and clock.
+ACC_ISSUE = {"instructions_per_residual_sample": 55.04, "tile": 14,
+             "sources": PAIR_TRAFFIC["sources"], "sha256": "f051010d45de21aa341009e6b2bb5c31f3747a8e61388cb9788602d4d400a6dd"}
+
+
+def _sources_current(rec):
+    import hashlib
+    try:
+        blob = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in rec["sources"])
+    except OSError:
+        return False
+    return hashlib.sha256(blob).hexdigest() == rec["sha256"]
 
 
 def pair_traffic(tiles):
     """The recorded per-launch traffic if the pair kernel's sources are the
     ones it was measured on and the tile of the largest p (where nearly all
     the traffic is) is the recorded one."""
-    import hashlib
-    root = os.path.dirname(os.path.abspath(__file__))
-    try:
-        blob = b"".join(open(os.path.join(root, f), "rb").read() for f in PAIR_TRAFFIC["sources"])
-    except OSError:
-        return None
-    if hashlib.sha256(blob).hexdigest() != PAIR_TRAFFIC["sha256"]:
+    if not _sources_current(PAIR_TRAFFIC):
         return None
     if not tiles or tiles[-1] != PAIR_TRAFFIC["tile"]:
         return None
@@ -787,7 +800,8 @@ def run_ours(args, rank, world):
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gres/s",
                 "frac": achieved / peak if peak else None,
                 "traffic": pair_traffic(tune["tile"]) if head == "mixed" else None,
-                "traffic_unit": "bytes per launch (DRAM read + write, one ncu capture)",
+                "traffic_unit": "bytes per launch at p = 1000 (DRAM read + write, one ncu capture; "
+                                "the launch reads 40 MB of z columns)",
                 "peak_from": {"sm_mhz": run_mhz, "sms": sms, "per_clock_per_sm": per_clk,
                               "mufu_bound_gres": mufu_rate / 1e9,
                               "fp32_bound_gres": fp32_rate / 1e9,
@@ -796,6 +810,25 @@ def run_ours(args, rank, world):
                               "note": "of measured unit rates (lingam_peak_probe) at the "
                                       "median SM clock of the timed region"},
                 "kernel_share": f["pair_ms"] / sum(f["ms"])}
+
+    # each form's pair kernel against its own bound: the MUFU-bound fast
+    # kernel as above; the plain FP32 kernel bound by instruction issue at its
+    # captured instruction count
+    pair_rooflines = {}
+    for p in args.forms:
+        fp = forms[p]
+        ach = fp["pair_units"] / (fp["pair_ms"] * 1e-3) if fp["pair_ms"] > 0 else 0.0
+        if p == "mixed":
+            pair_rooflines[p] = {"kernel": "k_pair_fast_b", "bound": "alu (MUFU)",
+                                 "achieved": ach / 1e9, "peak": mufu_rate / 1e9,
+                                 "unit": "Gres/s", "frac": ach / mufu_rate if mufu_rate else None}
+        elif p == "fp32" and _sources_current(ACC_ISSUE):
+            ipk = 128.0 * hz / ACC_ISSUE["instructions_per_residual_sample"]
+            pair_rooflines[p] = {"kernel": "k_pair_accurate_b", "bound": "issue",
+                                 "achieved": ach / 1e9, "peak": ipk / 1e9, "unit": "Gres/s",
+                                 "frac": ach / ipk,
+                                 "note": "128 thread instructions per SM and clock over the "
+                                         "captured 55.0 instructions per residual-sample"}
 
     # the streaming step (column stats + regress-out + downdate, fused in
     # k_regress_b / k_downdate_b): algorithmic HBM bytes per (variable, sample)
@@ -873,7 +906,8 @@ def run_ours(args, rank, world):
                       "genuine_ties": forms[p]["genuine_ties"],
                       "tuning": forms[p]["tuning"],
                       "order_head": forms[p]["order_head"],
-                      "oracle_errors": forms[p]["oracle_errors"]} for p in args.forms},
+                      "oracle_errors": forms[p]["oracle_errors"],
+                      "pair_roofline": pair_rooflines.get(p)} for p in args.forms},
         "configs": configs,
         "cpu_baselines": cpu_all,
         "batched": batch_info,

@@ -77,6 +77,8 @@ struct ScoreParams {
                           // the re-score passes: entries with I32 >= 0 are skipped
     double *epsOut;       // optional [p][p] the entry bounds (step-measure calls)
     int shard_rank, shard_n;   // shard_n > 1 (FP32-scored steps): only owned entries count
+    const float *ra;      // FP32-scored steps: [p][p] 1 / sqrt(1 - rho^2) from the pair kernel
+    float4 *hvar;         // FP32-scored steps: [p] h(z_j) as (hi, lo) and its bound (k_hvar_b)
 };
 
 // Bound on the change of h(m1, m2) for moment errors (e1, e2), in FP32 (a

@@ -248,6 +248,9 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
                 const int lo = min(oi, oj), hi = max(oi, oj);
                 const double rho = P.C[(int64_t)lo * P.ldc + hi] * P.isd[pi] * P.isd[pj];
                 const double s2 = fma(-rho, rho, 1.0);
+                // the score kernel's error model reads this entry's factor
+                if (P.ra && split == 0)
+                    P.ra[(size_t)pi * P.p + pj] = rsqrtf(fmaxf((float)s2, 1e-12f));
                 if (s2 > 1e-12) {
                     a = rsqrtf((float)s2);
                     b = (float)rho * a;
@@ -398,7 +401,7 @@ __device__ __forceinline__ void pair_block(const CUtensorMap *tmI, const CUtenso
 // The product of the 1 + y factors and the |u| sum run on in pr / asum across
 // the chunks of a ring stage (FIRST starts them); the caller takes one lg2 of
 // the product of up to 8 SUB factors (at most 2^16) when the stage ends.
-template <int WI, int WJ, int S, bool FIRST>
+template <int WI, int WJ, int S, bool FIRST, bool ABS2>
 __device__ __forceinline__ void pair_chunk_pk(const float *__restrict__ rows,
                                               const float *__restrict__ cols,
                                               const float2 (&A)[WI][WJ],
@@ -431,6 +434,7 @@ __device__ __forceinline__ void pair_chunk_pk(const float *__restrict__ rows,
         for (int c = 0; c < WJ; ++c) {
             float2 pc = FIRST ? ONE : pr[r][c];
             float as = asum[r][c];
+            float2 as2 = make_float2(FIRST ? 0.0f : as, 0.0f);
             float2 ac = acc[r][c];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -443,11 +447,14 @@ __device__ __forceinline__ void pair_chunk_pk(const float *__restrict__ rows,
                 const float2 q = __fmul2_rn(u, C2);   // C2 < 0: exp(-2|u|) = ex2(-|q|)
                 const float2 y = make_float2(ex2_approx(-fabsf(q.x)), ex2_approx(-fabsf(q.y)));
                 pc = __ffma2_rn(y, pc, pc);
-                as = (FIRST && h == 0) ? fabsf(u.x) + fabsf(u.y) : as + fabsf(u.x) + fabsf(u.y);
+                if (ABS2)
+                    as2 = __fadd2_rn(as2, make_float2(fabsf(u.x), fabsf(u.y)));
+                else
+                    as = (FIRST && h == 0) ? fabsf(u.x) + fabsf(u.y) : as + fabsf(u.x) + fabsf(u.y);
             }
             acc[r][c] = ac;
             pr[r][c] = pc;
-            asum[r][c] = as;
+            asum[r][c] = ABS2 ? as2.x + as2.y : as;
         }
     }
 }
@@ -531,6 +538,9 @@ __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUte
                 const int lo = min(oi, oj), hi = max(oi, oj);
                 const double rho = P.C[(int64_t)lo * P.ldc + hi] * P.isd[pi] * P.isd[pj];
                 const double s2 = fma(-rho, rho, 1.0);
+                // the score kernel's error model reads this entry's factor
+                if (P.ra && split == 0)
+                    P.ra[(size_t)pi * P.p + pj] = rsqrtf(fmaxf((float)s2, 1e-12f));
                 if (s2 > 1e-12) {
                     a = rsqrtf((float)s2);
                     b = (float)rho * a;
@@ -571,6 +581,10 @@ __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUte
             acc[r][c] = pr[r][c] = make_float2(0.0f, 0.0f);
         }
 
+    // leading stages whose chunks are all full (the instance's last chunk may
+    // be short)
+    const int nfull_chunks = max(0, min(nck, P.n / S - c0));
+    const int nfs = nfull_chunks / SUB;
     int st = 0;
     uint32_t ph = 0;
     for (int k = 0; k < nst; ++k) {
@@ -589,6 +603,17 @@ __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUte
         // a chunk after the first of a stage exists only if the first was
         // full (a short chunk is the last of the instance)
         bool pending = false;
+        if (PK && k < nfs) {
+            // every chunk of the stage is full: no per-chunk checks
+            pair_chunk_pk<WI, WJ, S, true, G.absadd != 0>(sb + ri0 * S, sb + TI * S + cj0 * S, A,
+                                                          NB, pr, asum, acc, lane);
+#pragma unroll
+            for (int b = 1; b < SUB; ++b)
+                pair_chunk_pk<WI, WJ, S, false, G.absadd != 0>(
+                    sb + b * CHUNK_FLOATS + ri0 * S, sb + b * CHUNK_FLOATS + TI * S + cj0 * S, A,
+                    NB, pr, asum, acc, lane);
+            pending = true;
+        } else
 #pragma unroll
         for (int b = 0; b < SUB; ++b) {
             const int ch = k * SUB + b;
@@ -598,9 +623,11 @@ __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUte
             const int valid = min(S, P.n - (c0 + ch) * S);
             if (PK && valid == S) {
                 if (b == 0)
-                    pair_chunk_pk<WI, WJ, S, true>(rows, cols, A, NB, pr, asum, acc, lane);
+                    pair_chunk_pk<WI, WJ, S, true, G.absadd != 0>(rows, cols, A, NB, pr, asum, acc,
+                                                                  lane);
                 else
-                    pair_chunk_pk<WI, WJ, S, false>(rows, cols, A, NB, pr, asum, acc, lane);
+                    pair_chunk_pk<WI, WJ, S, false, G.absadd != 0>(rows, cols, A, NB, pr, asum, acc,
+                                                                   lane);
                 pending = true;
             } else {
                 float tca[WI][WJ], tcb[WI][WJ], t2[WI][WJ];
@@ -768,8 +795,8 @@ struct PairTable {
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
 using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19,
-                              20, 21, 22, 23, 24, 25>;
-static_assert(PAIR_NCFG == 26, "PairKernels lists every configuration");
+                              20, 21, 22, 23, 24, 25, 26, 27, 28>;
+static_assert(PAIR_NCFG == 29, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {

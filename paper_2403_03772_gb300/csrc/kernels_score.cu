@@ -34,8 +34,15 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     const bool df = P.mom2 != nullptr;
     dfl *hd = reinterpret_cast<dfl *>(wsh + P.p + (P.p & 1));   // h(z_j) as double-floats
     for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
-        score_var(P, j, invn, hsh[j], wsh[j]);
-        if (df) hd[j] = df_split(hsh[j]);
+        if (df && P.hvar) {
+            // computed once for the step by k_hvar_b (no FP64 work per block)
+            const float4 v = P.hvar[j];
+            hd[j] = dfl{v.x, v.y};
+            wsh[j] = v.z;
+        } else {
+            score_var(P, j, invn, hsh[j], wsh[j]);
+            if (df) hd[j] = df_split(hsh[j]);
+        }
     }
     __syncthreads();
     // SCORE_WPR warps per row i: warp wr of the row takes j = 32 wr + lane +
@@ -52,19 +59,27 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
         float errf = 0.0f;
         const int oi = P.U[i];
         const float wi = wsh[i];
+        // the model's FP32 constants, converted once (not per entry)
+        const float epsI = (float)P.epsI, md1 = (float)P.model.d1, md2 = (float)P.model.d2,
+                    mda = (float)P.model.da;
         for (int j = wr * 32 + lane; j < P.p; j += 32 * SCORE_WPR) {
             if (j == i) continue;
             if (P.shard_n > 1 && shard_owner(i, j, P.p, P.shard_n) != P.shard_rank) continue;
             float mf[4];
             const dfl I = score_entry_df(P, i, j, hd, c1, b1, c2, mf);
-            float eps = (float)P.epsI;
+            float eps = epsI;
             if (P.use_model) {
-                const int oj = P.U[j];
-                const double rho =
-                    P.C[(int64_t)min(oi, oj) * P.ldc + max(oi, oj)] * P.isd[i] * P.isd[j];
-                const float ra = rsqrtf(fmaxf((float)fma(-rho, rho, 1.0), 1e-12f)) * 1.01f;
-                const float e1 = (float)P.model.d1 + (float)P.model.da * ra;
-                const float e2 = (float)P.model.d2 + (float)P.model.da * ra;
+                float ra;
+                if (P.ra) {
+                    ra = P.ra[(size_t)i * P.p + j] * 1.01f;   // from the pair kernel
+                } else {
+                    const int oj = P.U[j];
+                    const double rho =
+                        P.C[(int64_t)min(oi, oj) * P.ldc + max(oi, oj)] * P.isd[i] * P.isd[j];
+                    ra = rsqrtf(fmaxf((float)fma(-rho, rho, 1.0), 1e-12f)) * 1.01f;
+                }
+                const float e1 = md1 + mda * ra;
+                const float e2 = md2 + mda * ra;
                 eps = h_err(mf[0], mf[1], e1, e2) + h_err(mf[2], mf[3], e1, e2) + wi + wsh[j];
             }
             const bool neg = I.hi < 0.0f;
@@ -112,12 +127,31 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     }
 }
 
+// The variable terms of an FP32-scored step, once per step: h(z_j) (from the
+// regress kernel's split sums, FP64) as a double-float and its error bound,
+// read by every block of k_score_b.
+__global__ void __launch_bounds__(256) k_hvar_b(const ScoreParams *__restrict__ Ps, int count)
+{
+    const int inst = blockIdx.y;
+    if (inst >= count) return;
+    const ScoreParams &P = Ps[inst];
+    if (!P.mom2 || !P.hvar) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.p) return;
+    double h;
+    float w;
+    score_var(P, j, 1.0 / (double)P.n, h, w);
+    const dfl d = df_split(h);
+    P.hvar[j] = make_float4(d.hi, d.lo, w, 0.0f);
+}
+
 int score_blocks(int p) { return (p + SCORE_RPB - 1) / SCORE_RPB; }
 
 cudaError_t launch_score_b(const ScoreParams *P, const int *prefix, int count, int total_blocks,
                            int maxp, cudaStream_t s)
 {
     if (count <= 0 || total_blocks <= 0) return cudaSuccess;
+    k_hvar_b<<<dim3((maxp + 255) / 256, count), 256, 0, s>>>(P, count);
     k_score_b<<<total_blocks, 32 * SCORE_RPB * SCORE_WPR,
                 (sizeof(double) + sizeof(float) + sizeof(dfl)) * maxp + 32, s>>>(P, prefix, count);
     return cudaGetLastError();

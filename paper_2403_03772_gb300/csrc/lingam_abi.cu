@@ -103,6 +103,8 @@ struct InstDev {
     double *M = nullptr, *E = nullptr, *hist = nullptr, *ref_var = nullptr, *fmom = nullptr;
     double *fhz = nullptr, *lcoef = nullptr, *isd0 = nullptr, *isd1 = nullptr;
     float *I32 = nullptr;
+    float *ra = nullptr;      // [d][d] 1 / sqrt(1 - rho^2) of the step's pairs (pair kernel)
+    float4 *hvar = nullptr;   // [d] variable entropy terms of the step (k_hvar_b)
     int32_t *U0 = nullptr, *U1 = nullptr, *order = nullptr, *scratch = nullptr, *rows = nullptr;
     uint8_t *allow = nullptr;   // positions the prior knowledge allows at the step
     DevState *state = nullptr;
@@ -428,7 +430,7 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     };
     struct Off {
         size_t R, C, Cpart, mom, hz, M, E, hist, ref, fmom, fhz, lcoef, U, order, scratch, rows,
-            state, isd, I32, S, expo, cand, cdbl, allow;
+            state, isd, I32, ra, hvar, S, expo, cand, cdbl, allow;
     };
     std::vector<Off> o(K);
     for (int k = 0; k < K; ++k) {
@@ -456,6 +458,8 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].state = take(sizeof(DevState));
         o[k].isd = take((size_t)2 * d * 8);
         o[k].I32 = take((size_t)d * d * 4);
+        o[k].ra = take((size_t)d * d * 4);
+        o[k].hvar = take((size_t)d * 16);
         o[k].cand = take((size_t)d * 4);
         o[k].cdbl = take((size_t)3 * d * 8);
         o[k].allow = take((size_t)d);
@@ -496,6 +500,8 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         I.isd0 = reinterpret_cast<double *>(base + o[k].isd);
         I.isd1 = I.isd0 + d;
         I.I32 = reinterpret_cast<float *>(base + o[k].I32);
+        I.ra = reinterpret_cast<float *>(base + o[k].ra);
+        I.hvar = reinterpret_cast<float4 *>(base + o[k].hvar);
         I.allow = reinterpret_cast<uint8_t *>(base + o[k].allow);
 
         {   // candidate arrays of the device state
@@ -570,6 +576,7 @@ static cudaError_t issue_launch(Plan &pl, const Launch &l, char *pb, cudaStream_
     case K_SCORE:
         e = launch_score_b((const ScoreParams *)P, (const int *)(pb + l.off2), l.count, l.b,
                            l.a, s);
+        ++*nodes;   // k_hvar_b + k_score_b
         break;
     case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
     case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
@@ -832,6 +839,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 P.isd = isd;
                 P.shard_rank = ctx->shard_rank;
                 P.shard_n = ctx->shard_n;
+                P.ra = I.ra;
                 pp.push_back(P);
                 prefix.push_back(prefix.back() + P.tiles_i * P.tiles_j * P.nsplit);
                 S.mom2 = reinterpret_cast<const float2 *>(I.mom);
@@ -849,6 +857,8 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
                 S.isd = isd;
                 S.shard_rank = ctx->shard_rank;
                 S.shard_n = ctx->shard_n;
+                S.ra = I.ra;
+                S.hvar = I.hvar;
                 xp = p;
             }
             S.p = p;

@@ -22,6 +22,7 @@ struct PairCfg {
     int packed;              // fast form: two samples per paired-FP32 instruction
     int sub;                 // 0: one chunk per ring stage (pair_block); >= 1: the streamlined
                              // block (pair_block_v2) with `sub` chunks per stage
+    int absadd;              // streamlined paired form: 1 sums |u| as f32x2 pairs
     constexpr int ti() const { return wi * wgi; }
     constexpr int tj() const { return wj * wgj; }
     constexpr int warps() const { return wgi * wgj; }
@@ -56,6 +57,9 @@ constexpr PairCfg PAIR_CFGS[] = {
     {2, 2, 2, 4, 2, 80, 80, 2, 8, 1, 4},     // 23: as 19 with stages of 4 chunks, 2 CTAs per SM
     {2, 2, 2, 4, 3, 80, 80, 2, 16, 1, 2},    // 24: as 22, folds every 16 chunks
     {4, 2, 1, 4, 2, 128, 128, 2, 16, 1, 2},  // 25: as 16, folds every 16 chunks
+    {2, 2, 2, 4, 3, 80, 80, 2, 16, 1, 2, 1}, // 26: as 24, |u| sums as f32x2 pairs
+    {4, 2, 1, 4, 2, 128, 128, 2, 16, 1, 2, 1}, // 27: as 25, |u| sums as f32x2 pairs
+    {2, 4, 2, 2, 3, 128, 128, 2, 16, 1, 2, 1}, // 28: 2 x 4 pairs per warp, 4 x 8 tile, 3 CTAs per SM
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
@@ -82,6 +86,8 @@ struct PairParams {
     int row0;             // first row of this instance in the z tensor
     const double *isd;    // [p] 1 / sqrt(C_ii) by position
     int shard_rank, shard_n;   // shard_n > 1: only tiles this rank owns (shard_owner)
+    float *ra;            // out [p][p] 1 / sqrt(1 - rho_ij^2) (FP32, as the score kernel's
+                          // error model takes it), written by the first sample split
 };
 
 }  // namespace lg
