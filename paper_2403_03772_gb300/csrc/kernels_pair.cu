@@ -577,14 +577,31 @@ __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUte
     for (int r = 0; r < WI; ++r)
 #pragma unroll
         for (int c = 0; c < WJ; ++c) {
-            s1[r][c] = s2[r][c] = e1[r][c] = e2[r][c] = a1[r][c] = asum[r][c] = 0.0f;
+            s1[r][c] = s2[r][c] = e1[r][c] = e2[r][c] = asum[r][c] = 0.0f;
             acc[r][c] = pr[r][c] = make_float2(0.0f, 0.0f);
         }
 
-    // leading stages whose chunks are all full (the instance's last chunk may
-    // be short)
-    const int nfull_chunks = max(0, min(nck, P.n / S - c0));
-    const int nfs = nfull_chunks / SUB;
+    // Stages whose SUB chunks all exist take the straight-line path, the
+    // instance's last chunk included when it is short: its samples past n
+    // read as zeros (the z rows are zero-padded, the TMA fills past the
+    // tensor with zeros), so each gives u = 0, adds 0 to the u exp(-u^2/2)
+    // sum and exactly 1 to the log2(2 cosh u) sum (a factor 1 + 1 in the
+    // product, |u| = 0).  Each lane starts its log2 sums at minus its count
+    // of such slots.  A last stage with fewer than SUB chunks takes the
+    // general path (masked tail).
+    const int nfs = PK ? nck / SUB : 0;
+    int ninv = 0;
+    if (PK && nck % SUB == 0 && (int64_t)c1 * S > P.n) {
+        const int64_t base = (int64_t)(c1 - 1) * S + lane * 4;
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ninv += base + g * 128 + v >= P.n;
+    }
+#pragma unroll
+    for (int r = 0; r < WI; ++r)
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) a1[r][c] = -(float)ninv;
     int st = 0;
     uint32_t ph = 0;
     for (int k = 0; k < nst; ++k) {

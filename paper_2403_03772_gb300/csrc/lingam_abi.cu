@@ -474,6 +474,10 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         pl.zrows += spec[k].d;
     }
     CK(ensure(pl.zarena, (size_t)pl.zrows * pl.ldz * 4, true));
+    // the padding of every z row (samples n .. ldz) must read as zeros: the
+    // fast pair kernel runs a range's last chunk through its full-chunk path
+    // and corrects for the padding exactly; a reused arena may hold old rows
+    CK(cudaMemset(pl.zarena.p, 0, (size_t)pl.zrows * pl.ldz * 4));
     if (prec != LINGAM_PREC_FP64) CK(ensure(pl.zloarena, (size_t)pl.zrows * pl.ldz * 4, true));
     char *base = reinterpret_cast<char *>(pl.arena.p);
     for (int k = 0; k < K; ++k) {
