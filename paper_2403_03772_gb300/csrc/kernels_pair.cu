@@ -812,8 +812,8 @@ struct PairTable {
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
 using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19,
-                              20, 21, 22, 23, 24, 25, 26, 27, 28>;
-static_assert(PAIR_NCFG == 29, "PairKernels lists every configuration");
+                              20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30>;
+static_assert(PAIR_NCFG == 31, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {

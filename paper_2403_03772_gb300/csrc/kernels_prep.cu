@@ -435,8 +435,8 @@ cudaError_t launch_fill_test_z(float *z, int64_t ldz, int rows, int n, cudaStrea
 }
 
 // Low parts of the standardised columns for the double-float re-score,
-// z_lo = fl32(R_i / sigma_i - z_hi) with the same FP64 product the regress
-// kernel rounded to z_hi; only for steps that re-score (state routed to the
+// z_lo = fl32(R_i / sigma_i - z_hi), the FP64 product taken exactly inside
+// one FMA (z_hi is the regress kernel's FP32 rounding of that product); only for steps that re-score (state routed to the
 // double-float tier) or score every pair in double-float (`always`).
 constexpr int ZLO_CHUNK = 2048;   // samples per work item of k_zlo_b
 
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256) k_zlo_b(const ZloParams *__restrict__ Ps,
                 float *zl = P.zlo + (int64_t)a * P.ldz;
                 const int s1 = min(P.n, (c + 1) * ZLO_CHUNK);
                 for (int s = c * ZLO_CHUNK + threadIdx.x; s < s1; s += blockDim.x)
-                    zl[s] = (float)__dsub_rn(__dmul_rn(r[s], isd), (double)zh[s]);
+                    zl[s] = (float)__fma_rn(r[s], isd, -(double)zh[s]);   // one rounding
             }
         }
         __syncthreads();   // s_act is rewritten by the next chunk
@@ -483,29 +483,36 @@ cudaError_t launch_zlo_b(const ZloParams *P, int count, int blocks, cudaStream_t
 }
 
 // Rank-1 downdate of the covariance of the remaining variables (FP64):
-// C_ij <- C_ij - C_im C_jm / C_mm, written symmetric-exact.
+// C_ij <- C_ij - (C_im C_jm) (1 / C_mm), exactly symmetric: the thread of
+// (i, j) with r <= c writes both C_ij and C_ji (the product C_im C_jm is the
+// same for both, and the reciprocal is shared), so the FP64 work is half the
+// square and has no division per entry.  Column m is only read.
 // One launch covers every instance: prefix[k] is the first block of
-// instance k, whose (p - 1)^2 entries take ceil((p-1)/32) x ceil((p-1)/8)
+// instance k, whose (p - 1)^2 positions take ceil((p-1)/32) x ceil((p-1)/8)
 // blocks of 32 x 8 threads.
 __global__ void k_downdate_b(const DowndateParams *__restrict__ Ps, const int *__restrict__ prefix,
                              int count)
 {
+    __shared__ double s_inv;
     const int inst = find_instance(prefix, count, blockIdx.x);
     const DowndateParams P = Ps[inst];
+    const int mpos = P.state->m_pos;
+    const int m = P.U[mpos];
+    double *C = P.C;
+    const int64_t ldc = P.ldc;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_inv = 1.0 / C[(int64_t)m * ldc + m];
+    __syncthreads();   // one reciprocal per block, before any thread leaves
     const int tx = (P.p - 1 + 31) / 32;
     const int local = blockIdx.x - prefix[inst];
     const int r = (local / tx) * blockDim.y + threadIdx.y;
     const int c = (local % tx) * blockDim.x + threadIdx.x;
-    if (r >= P.p - 1 || c >= P.p - 1) return;
-    const int mpos = P.state->m_pos;
-    const int m = P.U[mpos];
+    if (r >= P.p - 1 || c >= P.p - 1 || r > c) return;
     const int i = P.U[r + (r >= mpos ? 1 : 0)];
     const int j = P.U[c + (c >= mpos ? 1 : 0)];
-    double *C = P.C;
-    const int64_t ldc = P.ldc;
-    const double cmm = C[(int64_t)m * ldc + m];
     const double cim = C[(int64_t)i * ldc + m], cjm = C[(int64_t)j * ldc + m];
-    C[(int64_t)i * ldc + j] -= (cim * cjm) / cmm;
+    const double v = C[(int64_t)i * ldc + j] - (cim * cjm) * s_inv;
+    C[(int64_t)i * ldc + j] = v;
+    if (i != j) C[(int64_t)j * ldc + i] = v;
 }
 
 int downdate_blocks(int p) { return p < 2 ? 0 : ((p - 1 + 31) / 32) * ((p - 1 + 7) / 8); }

@@ -915,7 +915,10 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             }
         }
         const int cnt = (int)sc.size();
-        const int hp_blocks = ctx->num_sms * 8;   // 64 warps per SM, 24 resident
+        // re-score passes: 8 blocks per SM (64 warps, 24 resident) striding
+        // over the units; one wave of resident blocks was measured slower on
+        // the passes that have work, and a pass without work costs ~4 us
+        const int hp_blocks = ctx->num_sms * 8;
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t;

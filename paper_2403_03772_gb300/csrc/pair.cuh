@@ -60,6 +60,8 @@ constexpr PairCfg PAIR_CFGS[] = {
     {2, 2, 2, 4, 3, 80, 80, 2, 16, 1, 2, 1}, // 26: as 24, |u| sums as f32x2 pairs
     {4, 2, 1, 4, 2, 128, 128, 2, 16, 1, 2, 1}, // 27: as 25, |u| sums as f32x2 pairs
     {2, 4, 2, 2, 3, 128, 128, 2, 16, 1, 2, 1}, // 28: 2 x 4 pairs per warp, 4 x 8 tile, 3 CTAs per SM
+    {4, 2, 2, 4, 2, 128, 128, 2, 16, 1, 2, 1}, // 29: as 27 with 8 warps (8 x 8 tile), 2 CTAs per SM
+    {4, 2, 1, 4, 3, 128, 128, 2, 16, 1, 2, 1}, // 30: as 27 with 3 stages, 3 CTAs per SM
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
