@@ -379,7 +379,7 @@ int32_t lingam_shard_owner(int64_t i, int64_t j, int64_t p, int32_t nranks);
 lingam_status lingam_set_input_gate(lingam_ctx *ctx, const uint32_t *flag, double timeout_s);
 
 /* Number of pair-kernel tile configurations. */
-#define LINGAM_PAIR_TILES 31
+#define LINGAM_PAIR_TILES 33
 
 /*
  * Shape of tile configuration `tile` (no context or GPU needed): out[9] =

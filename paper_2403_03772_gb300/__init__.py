@@ -521,7 +521,7 @@ def lingam_step_measures(ctx: Context, X):
     return ctx.step_measures(X)
 
 
-PAIR_TILES = 31
+PAIR_TILES = 33
 _TILE_KEYS = ("wi", "wj", "wgi", "wgj", "stages", "groups", "fold", "packed", "sub")
 
 

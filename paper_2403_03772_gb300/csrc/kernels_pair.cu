@@ -459,6 +459,73 @@ __device__ __forceinline__ void pair_chunk_pk(const float *__restrict__ rows,
     }
 }
 
+// The same chunk with every row loaded first and the sample steps outermost:
+// each step h runs all WI x WJ pairs, so WI WJ independent chains lie between
+// a MUFU result and its use.
+template <int WI, int WJ, int S, bool FIRST, bool ABS2>
+__device__ __forceinline__ void pair_chunk_pk_h(const float *__restrict__ rows,
+                                                const float *__restrict__ cols,
+                                                const float2 (&A)[WI][WJ],
+                                                const float2 (&NB)[WI][WJ], float2 (&pr)[WI][WJ],
+                                                float (&asum)[WI][WJ], float2 (&acc)[WI][WJ],
+                                                int lane)
+{
+    static_assert(S == 256, "one iteration of 8 samples per lane covers a chunk");
+    const int s0 = lane * 4;
+    float zi[WI][8], zj[WJ][8];
+#pragma unroll
+    for (int r = 0; r < WI; ++r) {
+        const float4 t0 = *reinterpret_cast<const float4 *>(rows + r * S + s0);
+        const float4 t1 = *reinterpret_cast<const float4 *>(rows + r * S + s0 + 128);
+        zi[r][0] = t0.x; zi[r][1] = t0.y; zi[r][2] = t0.z; zi[r][3] = t0.w;
+        zi[r][4] = t1.x; zi[r][5] = t1.y; zi[r][6] = t1.z; zi[r][7] = t1.w;
+    }
+#pragma unroll
+    for (int c = 0; c < WJ; ++c) {
+        const float4 t0 = *reinterpret_cast<const float4 *>(cols + c * S + s0);
+        const float4 t1 = *reinterpret_cast<const float4 *>(cols + c * S + s0 + 128);
+        zj[c][0] = t0.x; zj[c][1] = t0.y; zj[c][2] = t0.z; zj[c][3] = t0.w;
+        zj[c][4] = t1.x; zj[c][5] = t1.y; zj[c][6] = t1.z; zj[c][7] = t1.w;
+    }
+    const float2 C2 = make_float2(FAST_C2, FAST_C2);
+    const float2 ONE = make_float2(1.0f, 1.0f);
+    float2 as2[WI][WJ];
+#pragma unroll
+    for (int r = 0; r < WI; ++r)
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) {
+            if (FIRST) pr[r][c] = ONE;
+            as2[r][c] = make_float2(FIRST ? 0.0f : asum[r][c], 0.0f);
+        }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+#pragma unroll
+        for (int r = 0; r < WI; ++r) {
+#pragma unroll
+            for (int c = 0; c < WJ; ++c) {
+                const float2 zi2 = make_float2(zi[r][2 * h], zi[r][2 * h + 1]);
+                const float2 zj2 = make_float2(zj[c][2 * h], zj[c][2 * h + 1]);
+                const float2 u = __ffma2_rn(A[r][c], zi2, __fmul2_rn(NB[r][c], zj2));
+                const float2 sq = __fmul2_rn(u, u);
+                const float2 e = make_float2(ex2_approx(-sq.x), ex2_approx(-sq.y));
+                acc[r][c] = __ffma2_rn(u, e, acc[r][c]);
+                const float2 q = __fmul2_rn(u, C2);
+                const float2 y = make_float2(ex2_approx(-fabsf(q.x)), ex2_approx(-fabsf(q.y)));
+                pr[r][c] = __ffma2_rn(y, pr[r][c], pr[r][c]);
+                if (ABS2) {
+                    as2[r][c] = __fadd2_rn(as2[r][c], make_float2(fabsf(u.x), fabsf(u.y)));
+                } else {
+                    as2[r][c].x = as2[r][c].x + fabsf(u.x) + fabsf(u.y);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < WI; ++r)
+#pragma unroll
+        for (int c = 0; c < WJ; ++c) asum[r][c] = ABS2 ? as2[r][c].x + as2[r][c].y : as2[r][c].x;
+}
+
 template <int MODE, int CFG>
 __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUtensorMap *tmJ,
                                               const PairParams &P, const int ti, const int tj,
@@ -622,13 +689,23 @@ __device__ __forceinline__ void pair_block_v2(const CUtensorMap *tmI, const CUte
         bool pending = false;
         if (PK && k < nfs) {
             // every chunk of the stage is full: no per-chunk checks
-            pair_chunk_pk<WI, WJ, S, true, G.absadd != 0>(sb + ri0 * S, sb + TI * S + cj0 * S, A,
-                                                          NB, pr, asum, acc, lane);
+            if constexpr (G.hmajor != 0)
+                pair_chunk_pk_h<WI, WJ, S, true, G.absadd != 0>(sb + ri0 * S, sb + TI * S + cj0 * S,
+                                                                A, NB, pr, asum, acc, lane);
+            else
+                pair_chunk_pk<WI, WJ, S, true, G.absadd != 0>(sb + ri0 * S, sb + TI * S + cj0 * S,
+                                                              A, NB, pr, asum, acc, lane);
 #pragma unroll
-            for (int b = 1; b < SUB; ++b)
-                pair_chunk_pk<WI, WJ, S, false, G.absadd != 0>(
-                    sb + b * CHUNK_FLOATS + ri0 * S, sb + b * CHUNK_FLOATS + TI * S + cj0 * S, A,
-                    NB, pr, asum, acc, lane);
+            for (int b = 1; b < SUB; ++b) {
+                const float *rb = sb + b * CHUNK_FLOATS + ri0 * S;
+                const float *cb2 = sb + b * CHUNK_FLOATS + TI * S + cj0 * S;
+                if constexpr (G.hmajor != 0)
+                    pair_chunk_pk_h<WI, WJ, S, false, G.absadd != 0>(rb, cb2, A, NB, pr, asum, acc,
+                                                                     lane);
+                else
+                    pair_chunk_pk<WI, WJ, S, false, G.absadd != 0>(rb, cb2, A, NB, pr, asum, acc,
+                                                                   lane);
+            }
             pending = true;
         } else
 #pragma unroll
@@ -812,8 +889,8 @@ struct PairTable {
     static constexpr PairKernel acc[sizeof...(C)] = {k_pair_accurate_b<C>...};
 };
 using PairKernels = PairTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19,
-                              20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30>;
-static_assert(PAIR_NCFG == 31, "PairKernels lists every configuration");
+                              20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32>;
+static_assert(PAIR_NCFG == 33, "PairKernels lists every configuration");
 
 static PairKernel pair_kernel(int mode, int cfg)
 {

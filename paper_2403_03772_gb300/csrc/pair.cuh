@@ -23,6 +23,8 @@ struct PairCfg {
     int sub;                 // 0: one chunk per ring stage (pair_block); >= 1: the streamlined
                              // block (pair_block_v2) with `sub` chunks per stage
     int absadd;              // streamlined paired form: 1 sums |u| as f32x2 pairs
+    int hmajor;              // streamlined paired form: 1 loads every row first and runs the
+                             // sample steps outermost (all WI x WJ pairs per step)
     constexpr int ti() const { return wi * wgi; }
     constexpr int tj() const { return wj * wgj; }
     constexpr int warps() const { return wgi * wgj; }
@@ -62,6 +64,8 @@ constexpr PairCfg PAIR_CFGS[] = {
     {2, 4, 2, 2, 3, 128, 128, 2, 16, 1, 2, 1}, // 28: 2 x 4 pairs per warp, 4 x 8 tile, 3 CTAs per SM
     {4, 2, 2, 4, 2, 128, 128, 2, 16, 1, 2, 1}, // 29: as 27 with 8 warps (8 x 8 tile), 2 CTAs per SM
     {4, 2, 1, 4, 3, 128, 128, 2, 16, 1, 2, 1}, // 30: as 27 with 3 stages, 3 CTAs per SM
+    {4, 2, 1, 4, 2, 128, 128, 2, 16, 1, 2, 1, 1}, // 31: as 27, sample steps outermost
+    {2, 2, 2, 4, 3, 80, 80, 2, 16, 1, 2, 1, 1},   // 32: as 26, sample steps outermost
 };
 constexpr int PAIR_NCFG = (int)(sizeof(PAIR_CFGS) / sizeof(PAIR_CFGS[0]));
 constexpr int PAIR_S = 256;                  // samples per TMA chunk
