@@ -473,21 +473,23 @@ def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float)
 # under profiles/ gives the command).  It describes only the kernel source it
 # was taken on, identified by the SHA-256 of these files; after any change
 # the roofline reports traffic null until the capture is repeated.
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# fast pair-kernel launch at p = 1000 of the d = 1000, n = 10000 order (the
-# first step; one ncu capture, profiles/k_pair_fast_b_cfg24_d1000_n10000.md),
-# against the 40 MB of z columns that launch must read.  Reported only while
-# the kernel's sources are the captured ones.
-PAIR_TRAFFIC = {"bytes_per_launch": 45.06e6, "algorithmic_bytes": 40.0e6, "p": 1000, "tile": 24,
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) and thread
+# instructions per residual-sample of one fast pair-kernel launch at p = 1000
+# of the d = 1000, n = 10000 order (the first step; one ncu capture,
+# profiles/k_pair_fast_b_cfg31_d1000_n10000.md), against the 40 MB of z
+# columns that launch must read.  Reported only while the kernel's sources
+# are the captured ones.
+PAIR_TRAFFIC = {"bytes_per_launch": 45.78e6, "algorithmic_bytes": 40.0e6, "p": 1000, "tile": 31,
+                "instructions_per_residual_sample": 7.441,
                 "sources": ['paper_2403_03772_gb300/csrc/kernels_pair.cu', 'paper_2403_03772_gb300/csrc/pair.cuh', 'paper_2403_03772_gb300/csrc/common.cuh'],
-                "sha256": "f051010d45de21aa341009e6b2bb5c31f3747a8e61388cb9788602d4d400a6dd"}
+                "sha256": "c334d97b40b27a77af943cffc86044449a475131b6f46dad799e1a92739a4c96"}
 
 # Issue slots per residual-sample of the plain FP32 pair kernel (CUDA's
 # accurate expf / log1pf; one ncu capture at p = 1000,
 # profiles/k_pair_accurate_b_cfg14_d1000_n10000.md): its bound is the issue
 # rate, 128 thread instructions per SM and clock.
-ACC_ISSUE = {"instructions_per_residual_sample": 55.04, "tile": 14,
-             "sources": PAIR_TRAFFIC["sources"], "sha256": "f051010d45de21aa341009e6b2bb5c31f3747a8e61388cb9788602d4d400a6dd"}
+ACC_ISSUE = {"instructions_per_residual_sample": 55.05, "tile": 14,
+             "sources": PAIR_TRAFFIC["sources"], "sha256": "c334d97b40b27a77af943cffc86044449a475131b6f46dad799e1a92739a4c96"}
 
 
 def _sources_current(rec):
@@ -815,6 +817,12 @@ def run_ours(args, rank, world):
                        mix["mufu_lg2"] / (per_clk["lg2"] * hz))
     fp32_rate = per_clk["fp32_ops"] * hz / mix["fp32_pipe"]
     issue_rate = 128.0 * hz / (mix["mufu_ex2"] + mix["mufu_lg2"] + mix["fp32_instructions"])
+    issue_from = "op model"
+    if (head == "mixed" and _sources_current(PAIR_TRAFFIC)
+            and tune["tile"][-1] == PAIR_TRAFFIC["tile"]):
+        # the tuned tile's own instruction count from its ncu capture
+        issue_rate = 128.0 * hz / PAIR_TRAFFIC["instructions_per_residual_sample"]
+        issue_from = "captured instruction count of the tuned tile"
     peak = min(mufu_rate, fp32_rate, issue_rate)
     f = forms[head]
     achieved = f["pair_units"] / (f["pair_ms"] * 1e-3) if f["pair_ms"] > 0 else 0.0
@@ -828,6 +836,7 @@ def run_ours(args, rank, world):
                               "mufu_bound_gres": mufu_rate / 1e9,
                               "fp32_bound_gres": fp32_rate / 1e9,
                               "issue_bound_gres": issue_rate / 1e9,
+                              "issue_bound_from": issue_from,
                               "ops_per_residual_sample": mix,
                               "note": "of measured unit rates (lingam_peak_probe) at the "
                                       "median SM clock of the timed region"},
@@ -852,7 +861,7 @@ def run_ours(args, rank, world):
                                  "achieved": ach / 1e9, "peak": ipk / 1e9, "unit": "Gres/s",
                                  "frac": ach / ipk,
                                  "note": "128 thread instructions per SM and clock over the "
-                                         "captured 55.0 instructions per residual-sample"}
+                                         "captured 55.05 instructions per residual-sample"}
 
     # the streaming step (column stats + regress-out + downdate, fused in
     # k_regress_b / k_downdate_b): algorithmic HBM bytes per (variable, sample)
