@@ -39,3 +39,33 @@ def test_traffic_is_reported_only_for_the_measured_sources_and_tile():
 def test_work_count_is_the_sum_over_steps():
     for d, n in [(10, 1000), (100, 5000), (1000, 10000)]:
         assert gen.residual_samples(d, n) == n * sum(p * (p - 1) for p in range(2, d + 1))
+
+
+def test_oracle_errors_read_the_stored_values():
+    """The bench states each GPU form's error against stored oracle values
+    (it never runs the oracle there): equal values give zero error, a moved
+    score or coefficient shows up, and data with another digest is not
+    compared."""
+    import numpy as np
+    order, digest = bench.golden_order("cfg2")
+    rows = bench.golden_rows("cfg2", digest)
+    assert order is not None and rows is not None
+    d = len(order)
+    M0 = np.zeros(d)
+    M0[rows["step0_vars"]] = rows["step0_M"]
+    B = np.zeros((d, d))
+    B[rows["B_vars"]] = rows["B_rows"]
+    e = bench.oracle_errors("cfg2", digest, order, M0, B)
+    assert e == {"order_equals_oracle": True, "max_rel_dM_step0": 0.0, "max_abs_dB": 0.0}
+    M1 = M0.copy()
+    M1[rows["step0_vars"][3]] += 1e-3 * np.max(np.abs(M0))
+    B1 = B.copy()
+    B1[rows["B_vars"][0], 0] += 2e-5
+    swapped = list(order)
+    swapped[0], swapped[1] = swapped[1], swapped[0]
+    e = bench.oracle_errors("cfg2", digest, swapped, M1, B1)
+    assert e["order_equals_oracle"] is False
+    assert abs(e["max_rel_dM_step0"] - 1e-3) < 1e-9
+    assert abs(e["max_abs_dB"] - 2e-5) < 1e-12
+    assert bench.golden_rows("cfg2", "0" * 16) is None
+    assert bench.oracle_errors("cfg2", "0" * 16, order)["order_equals_oracle"] is None
