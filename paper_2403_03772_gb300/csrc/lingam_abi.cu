@@ -433,15 +433,30 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
             state, isd, I32, ra, hvar, S, expo, cand, cdbl, allow;
     };
     std::vector<Off> o(K);
+    // MIXED form: tensor-core covariance for every instance.  The BF16 digit
+    // planes and exponents are scratch of one instance's launch at a time
+    // (the instances' covariance launches run in stream order), so all
+    // instances share one region sized for the largest.
+    const bool tc = TC_GRAM_ENABLED && prec == LINGAM_PREC_MIXED;
+    size_t tcS = 0, tcE = 0;
+    if (tc) {
+        size_t maxS = 0, maxE = 0;
+        for (int k = 0; k < K; ++k) {
+            maxS = std::max(maxS, (size_t)6 * gram_tc_dpad((int)spec[k].d) *
+                                      gram_tc_ldk((int)spec[k].n) * 2);
+            maxE = std::max(maxE, (size_t)gram_tc_expo_count((int)spec[k].n, (int)spec[k].d) * 4);
+        }
+        tcS = take(maxS);
+        tcE = take(maxE);
+    }
     for (int k = 0; k < K; ++k) {
         const int64_t n = spec[k].n, d = spec[k].d, ldr = pl.inst[k].ldr;
         o[k].R = take((size_t)d * ldr * 8);
         o[k].C = take((size_t)d * d * 8);
-        const bool tc = TC_GRAM_ENABLED && prec == LINGAM_PREC_MIXED && K == 1;
         pl.inst[k].tc_ksplit = tc ? gram_tc_ksplit((int)n, (int)d, ctx->num_sms) : 0;
         o[k].Cpart = take((size_t)std::max(pl.inst[k].ksplit, pl.inst[k].tc_ksplit) * d * d * 8);
-        o[k].S = tc ? take((size_t)6 * gram_tc_dpad((int)d) * gram_tc_ldk((int)n) * 2) : 0;
-        o[k].expo = tc ? take((size_t)gram_tc_expo_count((int)n, (int)d) * 4) : 0;
+        o[k].S = tcS;
+        o[k].expo = tcE;
         o[k].mom = take(pl.inst[k].mom_elems * 8);
         o[k].hz = take(pl.inst[k].hz_elems * 8);
         o[k].M = take((size_t)d * 8);
@@ -524,8 +539,10 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
             cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)6 * dpad};
             cuuint64_t strides[1] = {(cuuint64_t)(ldk * 2)};
             cuuint32_t box[2] = {64, 128}, elem[2] = {1, 1};
-            lingam_status st = make_tensor_maps(ctx, pl);   // loads the encoder
-            if (st) return st;
+            if (!g_encode) {
+                lingam_status st = make_tensor_maps(ctx, pl);   // loads the encoder
+                if (st) return st;
+            }
             CUresult r = g_encode(&I.tmS, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, I.S, dims, strides,
                                   box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -671,10 +688,12 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             io[k] = IotaParams{I.U0, (int)I.d, I.state};
             maxks = std::max(maxks, I.ksplit);
         }
-        if (K == 1 && pl.inst[0].tc_ksplit > 0) {
-            Launch lt{K_GRAM_TC};
-            lt.c = 0;
-            L.push_back(lt);
+        if (pl.inst[0].tc_ksplit > 0) {
+            for (int k = 0; k < K; ++k) {   // one tensor-core covariance per instance
+                Launch lt{K_GRAM_TC};
+                lt.c = k;
+                L.push_back(lt);
+            }
         } else {
             Launch lg_{K_GRAM};
             lg_.off = blob.add(g);
