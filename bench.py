@@ -943,6 +943,12 @@ def run_ours(args, rank, world):
                       "pair_roofline": pair_rooflines.get(p)} for p in args.forms},
         "configs": configs,
         "cpu_baselines": cpu_all,
+        "context": {
+            "paper": "GPU DirectLiNGAM up to 32x a sequential CPU run (NVIDIA RTX 6000 Ada, "
+                     "Sec. 3.1; VarLiNGAM about 30x); no absolute times published",
+            "this_run_vs_cpu_oracle": (value / cpu["value"]) if cpu else None,
+            "note": "the oracle is a plain FP64 program on the box's host cores, a stated "
+                    "baseline rather than a tuned one"},
         "batched": batch_info,
         "long_n": long_info,
         "readouts": readouts,
