@@ -5,8 +5,9 @@ sample splits and the compensated sums at large n.
 
 Checks: first-step scores of sampled variables against the oracle's literal
 Algorithm 1 rows; the full order against the stored oracle order when
-tests/golden/make_golden.py has written it; the order is a permutation and
-agrees between forms otherwise.
+tests/golden/make_golden.py has written it (the order is a permutation and
+agrees between forms otherwise); scores of sampled variables at steps 5 and
+15 against literal rows on the oracle's residual data along the stored order.
 """
 import numpy as np
 import pytest
@@ -64,3 +65,32 @@ def test_order_matches_stored_oracle_order(longn, runs, prec):
         pytest.skip("the n=1e6 oracle order has not been stored yet")
     assert dig == longn.digest()
     assert list(runs[prec][0]) == list(gold)
+
+
+LATER_STEPS = (5, 15)
+
+
+@pytest.fixture(scope="module")
+def later_rows(longn):
+    gold, dig = read_golden_order("long_n")
+    if gold is None or dig != longn.digest():
+        pytest.skip("the n=1e6 oracle order has not been stored yet")
+    res = oracle.Residuals(longn.X, gold)
+    out = {}
+    for t in LATER_STEPS:
+        res.advance(t)
+        U = res.U
+        pos = sorted({0, U.size // 2, U.size - 1, int(np.searchsorted(U, gold[t]))})
+        out[t] = (U, U[pos], oracle.row_scores(res.data, pos, U=U))
+    return out
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_later_step_rows_match_oracle(runs, later_rows, prec):
+    order, scores, _ = runs[prec]
+    for t, (U, vars_, ref) in later_rows.items():
+        row = scores[t]
+        assert np.all(np.isfinite(row[U]))
+        scale = np.max(np.abs(row[U]))
+        assert np.all(np.abs(row[vars_] - ref) <= M_REL * scale + M_ABS), (prec, t)
+        assert int(np.nanargmax(row)) == int(order[t])
