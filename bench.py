@@ -482,14 +482,14 @@ def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float)
 PAIR_TRAFFIC = {"bytes_per_launch": 45.78e6, "algorithmic_bytes": 40.0e6, "p": 1000, "tile": 31,
                 "instructions_per_residual_sample": 7.441,
                 "sources": ['paper_2403_03772_gb300/csrc/kernels_pair.cu', 'paper_2403_03772_gb300/csrc/pair.cuh', 'paper_2403_03772_gb300/csrc/common.cuh'],
-                "sha256": "c334d97b40b27a77af943cffc86044449a475131b6f46dad799e1a92739a4c96"}
+                "sha256": "93588ac0d7fbaf00ca7d9944b2b98202f8c5c996c7165858e5d3aa41085e684c"}
 
 # Issue slots per residual-sample of the plain FP32 pair kernel (CUDA's
 # accurate expf / log1pf; one ncu capture at p = 1000,
 # profiles/k_pair_accurate_b_cfg14_d1000_n10000.md): its bound is the issue
 # rate, 128 thread instructions per SM and clock.
 ACC_ISSUE = {"instructions_per_residual_sample": 55.05, "tile": 14,
-             "sources": PAIR_TRAFFIC["sources"], "sha256": "c334d97b40b27a77af943cffc86044449a475131b6f46dad799e1a92739a4c96"}
+             "sources": PAIR_TRAFFIC["sources"], "sha256": "93588ac0d7fbaf00ca7d9944b2b98202f8c5c996c7165858e5d3aa41085e684c"}
 
 
 def _sources_current(rec):
