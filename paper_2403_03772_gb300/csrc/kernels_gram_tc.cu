@@ -124,7 +124,7 @@ __host__ __device__ constexpr uint32_t tc_instr_desc(int M, int N)
 }
 
 // ------------------------------------------------------------- slicing ----
-// One block per padded variable row, one warp per drain period of 128
+// One block per padded variable row, one warp per drain period of TC_DRAIN
 // samples: the period's scale exponent e (max |x| < 2^e over the period, so
 // a large value elsewhere in the column costs no digits here) and the six
 // digit planes of its samples, zero beyond n and for rows beyond d.
@@ -149,18 +149,30 @@ __global__ void __launch_bounds__(256) k_gram_slices(const double *__restrict__ 
         int e = 0;
         if (m > 0.0) frexp(m, &e);                  // m = f 2^e, f in [0.5, 1)
         if (lane == 0) expo[(int64_t)p * d_pad + i] = e;
-        const double inv = ldexp(1.0, -e);
 #pragma unroll
         for (int v = 0; v < TC_DRAIN / 32; ++v) {
             const int64_t s = (int64_t)p * TC_DRAIN + v * 32 + lane;
             if (s >= ldk) continue;
-            double r = x[v] * inv;                   // |r| < 1
+            // The digits of r = x 2^-e (|r| < 1) in base 128, sign apart, are
+            // the 7-bit groups of F = floor(|r| 2^(7 TC_SLICES)): the steps
+            // r <- 128 r - trunc(128 r), each exact in FP64, peel exactly
+            // these.  F comes from the bits of x with integer shifts (no FP64
+            // arithmetic): |x| = M 2^(E - 1075) for the 53-bit significand M.
+            const unsigned long long b = (unsigned long long)__double_as_longlong(x[v]);
+            int E = (int)((b >> 52) & 0x7ff);
+            unsigned long long M = b & ((1ull << 52) - 1);
+            if (E > 0) M |= 1ull << 52;
+            else E = 1;                              // subnormal or zero
+            const int sh = 1075 - 7 * TC_SLICES + e - E;
+            const unsigned long long F = sh >= 0 ? (sh < 64 ? M >> sh : 0ull)
+                                                 : (sh > -64 ? M << -sh : 0ull);
+            const int sgn = (b >> 63) ? -1 : 1;
 #pragma unroll
             for (int k = 0; k < TC_SLICES; ++k) {
-                const double sr = r * 128.0;
-                const double sg = trunc(sr);         // |sg| <= 127
-                r = sr - sg;                         // exact
-                S[((int64_t)k * d_pad + i) * ldk + s] = __float2bfloat16_rn(ldexpf((float)sg, -7 * k));
+                const int dg = (int)((F >> (7 * (TC_SLICES - 1 - k))) & 127u);   // <= 127
+                const float scale = __int_as_float((127 - 7 * k) << 23);       // 2^-7k
+                S[((int64_t)k * d_pad + i) * ldk + s] =
+                    __float2bfloat16_rn((float)(sgn * dg) * scale);
             }
         }
     }

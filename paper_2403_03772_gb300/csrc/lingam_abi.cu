@@ -127,8 +127,14 @@ struct StepSplit {
 
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO, K_FORK, K_JOIN
 };
+
+// Batched MIXED calls compute the instances' tensor-core covariances on up
+// to this many streams at once (fork/join in the step graph), each stream
+// with its own digit-plane scratch: one instance's launches (at most a few
+// dozen CTAs for d <= 400) leave most of the GPU idle.
+constexpr int GRAM_STREAMS = 8;
 
 // Timing events per ordering step when profiling: before the pair moments,
 // after them, after score + select, after the FP64 passes, after regress-out.
@@ -138,7 +144,8 @@ struct Launch {
     LaunchKind kind;
     size_t off = 0, off2 = 0;
     int count = 0, a = 0, b = 0, c = 0;
-    int x = 0;   // K_SCORE of a sharded call: p of the step whose partial M, E are exchanged
+    int x = 0;   // K_SCORE of a sharded call: p of the step whose partial M, E are exchanged;
+                 // K_GRAM_TC: 1 + the side stream it runs on (0: the call's stream)
 };
 
 struct Plan {
@@ -156,6 +163,9 @@ struct Plan {
     std::vector<double> punits;
     std::vector<Launch> eager;   // sharded calls: the launches, run in order with the
                                  // exchange after each sharded score (no graph)
+    int nside = 0;               // side streams of the covariance fork (ctx-owned handles)
+    cudaStream_t side[GRAM_STREAMS]{};
+    cudaEvent_t ev_side[GRAM_STREAMS]{}, ev_fork = nullptr;
 };
 
 }  // namespace
@@ -183,6 +193,9 @@ struct lingam_ctx {
     lingam_allreduce_fn allreduce = nullptr;
     void *allreduce_user = nullptr;
     std::vector<double> xbuf;         // host buffer of the exchange
+    // side streams of the batched covariance (made on first use)
+    cudaStream_t side[GRAM_STREAMS]{};
+    cudaEvent_t ev_side[GRAM_STREAMS]{}, ev_fork = nullptr;
 };
 
 static std::string g_create_error;
@@ -434,20 +447,35 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
     };
     std::vector<Off> o(K);
     // MIXED form: tensor-core covariance for every instance.  The BF16 digit
-    // planes and exponents are scratch of one instance's launch at a time
-    // (the instances' covariance launches run in stream order), so all
-    // instances share one region sized for the largest.
+    // planes and exponents are scratch of one instance's launches at a time:
+    // a batch runs its instances' covariances on W side streams, instance k
+    // on stream k mod W in order, so W regions sized for the largest
+    // instance serve them all (region k mod W).
     const bool tc = TC_GRAM_ENABLED && prec == LINGAM_PREC_MIXED;
-    size_t tcS = 0, tcE = 0;
+    size_t tcS = 0, tcE = 0, maxS = 0, maxE = 0;
+    const int W = (tc && K > 1) ? std::min(K, GRAM_STREAMS) : 1;   // scratch regions
     if (tc) {
-        size_t maxS = 0, maxE = 0;
         for (int k = 0; k < K; ++k) {
             maxS = std::max(maxS, (size_t)6 * gram_tc_dpad((int)spec[k].d) *
                                       gram_tc_ldk((int)spec[k].n) * 2);
             maxE = std::max(maxE, (size_t)gram_tc_expo_count((int)spec[k].n, (int)spec[k].d) * 4);
         }
-        tcS = take(maxS);
-        tcE = take(maxE);
+        maxS = (size_t)roundup((int64_t)maxS, 1024);
+        maxE = (size_t)roundup((int64_t)maxE, 256);
+        tcS = take(maxS * W);
+        tcE = take(maxE * W);
+    }
+    pl.nside = W > 1 ? W : 0;
+    for (int k = 0; k < pl.nside; ++k) {   // the context's side streams, made once
+        if (!ctx->side[k]) CK(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
+        if (!ctx->ev_side[k])
+            CK(cudaEventCreateWithFlags(&ctx->ev_side[k], cudaEventDisableTiming));
+        pl.side[k] = ctx->side[k];
+        pl.ev_side[k] = ctx->ev_side[k];
+    }
+    if (pl.nside > 0) {
+        if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        pl.ev_fork = ctx->ev_fork;
     }
     for (int k = 0; k < K; ++k) {
         const int64_t n = spec[k].n, d = spec[k].d, ldr = pl.inst[k].ldr;
@@ -455,8 +483,8 @@ static lingam_status layout_plan(lingam_ctx *ctx, Plan &pl, const std::vector<In
         o[k].C = take((size_t)d * d * 8);
         pl.inst[k].tc_ksplit = tc ? gram_tc_ksplit((int)n, (int)d, ctx->num_sms) : 0;
         o[k].Cpart = take((size_t)std::max(pl.inst[k].ksplit, pl.inst[k].tc_ksplit) * d * d * 8);
-        o[k].S = tcS;
-        o[k].expo = tcE;
+        o[k].S = tcS + (size_t)(k % W) * maxS;
+        o[k].expo = tcE + (size_t)(k % W) * maxE;
         o[k].mom = take(pl.inst[k].mom_elems * 8);
         o[k].hz = take(pl.inst[k].hz_elems * 8);
         o[k].M = take((size_t)d * 8);
@@ -620,11 +648,23 @@ static cudaError_t issue_launch(Plan &pl, const Launch &l, char *pb, cudaStream_
         break;
     case K_GRAM_TC: {
         InstDev &I = pl.inst[l.c];
+        const cudaStream_t gs = l.x > 0 ? pl.side[l.x - 1] : s;
         e = launch_gram_tc(&I.tmS, I.R, I.ldr, (int)I.n, (int)I.d, I.S, I.expo, I.Cpart,
-                           I.tc_ksplit, I.C, I.d, I.ref_var, &I.state->status, s);
+                           I.tc_ksplit, I.C, I.d, I.ref_var, &I.state->status, gs);
         *nodes += 2;
         break;
     }
+    case K_FORK:   // the side streams start after everything before on s
+        e = cudaEventRecord(pl.ev_fork, s);
+        for (int k = 0; k < l.a && e == cudaSuccess; ++k)
+            e = cudaStreamWaitEvent(pl.side[k], pl.ev_fork, 0);
+        return e;
+    case K_JOIN:   // s continues after everything issued on the side streams
+        for (int k = 0; k < l.a && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(pl.ev_side[k], pl.side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pl.ev_side[k], 0);
+        }
+        return e;
     case K_ZLO: e = launch_zlo_b((const ZloParams *)P, l.count, l.a, s); break;
     case K_FILL_NAN:
         e = launch_fill_nan(pl.inst[l.c].hist, (size_t)pl.inst[l.c].d * pl.inst[l.c].d, s);
@@ -689,10 +729,24 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             maxks = std::max(maxks, I.ksplit);
         }
         if (pl.inst[0].tc_ksplit > 0) {
-            for (int k = 0; k < K; ++k) {   // one tensor-core covariance per instance
+            // one tensor-core covariance per instance; a batch spreads them
+            // over the side streams (instance k on stream k mod nside, which
+            // owns scratch region k mod nside)
+            if (pl.nside > 0) {
+                Launch lf{K_FORK};
+                lf.a = pl.nside;
+                L.push_back(lf);
+            }
+            for (int k = 0; k < K; ++k) {
                 Launch lt{K_GRAM_TC};
                 lt.c = k;
+                lt.x = pl.nside > 0 ? 1 + k % pl.nside : 0;
                 L.push_back(lt);
+            }
+            if (pl.nside > 0) {
+                Launch lj{K_JOIN};
+                lj.a = pl.nside;
+                L.push_back(lj);
             }
         } else {
             Launch lg_{K_GRAM};
@@ -1073,7 +1127,10 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         pl.exec = nullptr;
         pl.eager = L;
         pl.nodes = 0;
-        for (const Launch &l : L) pl.nodes += l.kind == K_EVENT ? 0 : (l.kind == K_GRAM_TC ? 3 : 1);
+        for (const Launch &l : L)
+            pl.nodes += (l.kind == K_EVENT || l.kind == K_FORK || l.kind == K_JOIN)
+                            ? 0
+                            : (l.kind == K_GRAM_TC ? 3 : 1);
         pl.profile = profile ? 1 : 0;
         pl.partial = false;
         return LINGAM_OK;
@@ -1400,9 +1457,13 @@ lingam_status lingam_destroy(lingam_ctx *ctx)
                   &ctx->eT,     &ctx->ePos, &ctx->eOrd, &ctx->ePtr,    &ctx->eOut,
                   &ctx->eStatus, &ctx->prior};
     for (Buf *b : aux) release(*b);
-    cudaEvent_t evs[] = {ctx->e0, ctx->e1, ctx->g0, ctx->g1};
+    cudaEvent_t evs[] = {ctx->e0, ctx->e1, ctx->g0, ctx->g1, ctx->ev_fork};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
+    for (int k = 0; k < GRAM_STREAMS; ++k) {
+        if (ctx->ev_side[k]) cudaEventDestroy(ctx->ev_side[k]);
+        if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+    }
     if (ctx->s) cudaStreamDestroy(ctx->s);
     delete ctx;
     return LINGAM_OK;
