@@ -405,7 +405,12 @@ typedef struct {
     double graph_build_ms;    /* capture + instantiate time (0 if cached) */
     int32_t fp64_candidates;  /* candidates re-scored in FP64 over the run */
     int32_t df_candidates;    /* candidates re-scored in double-float */
-    int32_t reserved[4];
+    int32_t cond_nodes;       /* kernel nodes of graph_nodes inside conditional
+                                 re-score blocks (run only at steps that leave
+                                 candidates after their first scores) */
+    int32_t cond_bodies;      /* those blocks (one per step of a single-instance
+                                 graph; 0 for batches and sharded calls) */
+    int32_t reserved[2];
     double score_ms;          /* summed score + select time (profile=1) */
     double refine_ms;         /* summed re-score passes (profile=1) */
     double regress_ms;        /* summed regress-out + downdate (profile=1) */

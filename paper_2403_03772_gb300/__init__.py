@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("refined_steps", ctypes.c_int32), ("genuine_ties", ctypes.c_int32),
                 ("candidates_max", ctypes.c_int32), ("graph_nodes", ctypes.c_int32),
                 ("graph_build_ms", ctypes.c_double), ("fp64_candidates", ctypes.c_int32),
-                ("df_candidates", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+                ("df_candidates", ctypes.c_int32), ("cond_nodes", ctypes.c_int32),
+                ("cond_bodies", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
                 ("score_ms", ctypes.c_double),
                 ("refine_ms", ctypes.c_double), ("regress_ms", ctypes.c_double)]
 

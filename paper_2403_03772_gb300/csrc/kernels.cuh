@@ -193,6 +193,8 @@ struct SelectParams {
     const int8_t *prior;  // [ldp][ldp] ancestry knowledge by original index, or null:
     int64_t ldp;          //   prior[i ldp + j] = 1 x_j is an ancestor of x_i, 0 is not, -1 unknown
     uint8_t *allow;       // [p] workspace: positions that may be chosen at this step
+    const unsigned long long *cond;   // or null: the graph's conditional handle of the
+                                      // step's re-score block, set to 1 iff candidates remain
 };
 
 struct RefineSelectParams {

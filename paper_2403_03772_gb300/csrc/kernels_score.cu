@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restric
             st->ncand = 1;
             st->resolved = 1;
             st->pass_begin = st->pass_end = 0;
+            if (P.cond) cudaGraphSetConditional(*P.cond, 0u);   // the re-score block is skipped
         }
         return;
     }
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restric
         st->pass_end = P.tier == 1 ? min(2, cnt) : cnt;
         st->refined_steps += 1;
         if (cnt > st->cand_max) st->cand_max = cnt;
+        if (P.cond) cudaGraphSetConditional(*P.cond, 1u);
     }
 }
 

@@ -127,7 +127,8 @@ struct StepSplit {
 
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
-    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO, K_FORK, K_JOIN
+    K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO, K_FORK, K_JOIN,
+    K_COND_BEGIN, K_COND_END
 };
 
 // Batched MIXED calls compute the instances' tensor-core covariances on up
@@ -163,6 +164,8 @@ struct Plan {
     std::vector<double> punits;
     std::vector<Launch> eager;   // sharded calls: the launches, run in order with the
                                  // exchange after each sharded score (no graph)
+    Buf conds;                   // [maxd] conditional handles of the steps' re-score blocks
+    int cond_nodes = 0, cond_bodies = 0;   // kernel nodes inside them, and their number
     int nside = 0;               // side streams of the covariance fork (ctx-owned handles)
     cudaStream_t side[GRAM_STREAMS]{};
     cudaEvent_t ev_side[GRAM_STREAMS]{}, ev_fork = nullptr;
@@ -195,6 +198,8 @@ struct lingam_ctx {
     std::vector<double> xbuf;         // host buffer of the exchange
     // side streams of the batched covariance (made on first use)
     cudaStream_t side[GRAM_STREAMS]{};
+    cudaStream_t sbody = nullptr;   // captures the bodies of conditional nodes
+    bool no_cond = false;           // conditional nodes failed to capture here: plain graphs
     cudaEvent_t ev_side[GRAM_STREAMS]{}, ev_fork = nullptr;
 };
 
@@ -380,6 +385,7 @@ static void destroy_plan(Plan &pl)
     release(pl.zarena);
     release(pl.zloarena);
     release(pl.params);
+    release(pl.conds);
     pl.inst.clear();
     pl.spec.clear();
     pl.prec = pl.profile = pl.scores = pl.lcoef = pl.rows = -1;
@@ -659,6 +665,9 @@ static cudaError_t issue_launch(Plan &pl, const Launch &l, char *pb, cudaStream_
         for (int k = 0; k < l.a && e == cudaSuccess; ++k)
             e = cudaStreamWaitEvent(pl.side[k], pl.ev_fork, 0);
         return e;
+    case K_COND_BEGIN:   // captured by capture_plan; an eager run issues the body as is
+    case K_COND_END:
+        return cudaSuccess;
     case K_JOIN:   // s continues after everything issued on the side streams
         for (int k = 0; k < l.a && e == cudaSuccess; ++k) {
             e = cudaEventRecord(pl.ev_side[k], pl.side[k]);
@@ -674,6 +683,38 @@ static cudaError_t issue_launch(Plan &pl, const Launch &l, char *pb, cudaStream_
     return e;
 }
 
+// Adds an if-node after the work captured so far on s (its condition: a new
+// handle, 0 at every graph launch until a kernel sets it), makes it the
+// point where the capture of s continues, and starts capturing its body on
+// sb.
+static cudaError_t begin_cond_body(cudaStream_t s, cudaStream_t sb, unsigned long long *handle)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edata, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle h = 0;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, edata, nd, &np);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    *handle = h;
+    return cudaStreamBeginCaptureToGraph(sb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+}
+
 // Capture the covariance + ordering loop of the current plan into one graph.
 // stop_after_score0 captures only the first step up to its scores (and writes
 // I(i, j) of the single instance to Iout and the per-entry bounds to epsOut).
@@ -687,6 +728,14 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     const bool sharded = ctx->shard_n > 1;
     cudaStream_t s = ctx->s;
     const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
+    // A single-instance graph puts each step's re-score block (the low parts
+    // and the double-float and FP64 passes, no-ops unless candidates remain)
+    // under a conditional node that the select kernel sets: steps decided by
+    // their FP32 scores skip those launches.  A batch keeps them (the select
+    // blocks of its instances would race to set one condition).
+    const bool use_cond = pl.inst.size() == 1 && !sharded && !stop_after_score0 && !ctx->no_cond;
+    if (use_cond) CK(ensure(pl.conds, (size_t)pl.maxd * sizeof(unsigned long long)));
+    std::vector<unsigned long long> hconds(use_cond ? pl.maxd : 0, 0ull);
     // Moment-error model of the FP32 pair kernels and the regress kernel
     // (ErrModel): per-sample worst cases of the MUFU ex2/lg2 approximations
     // (relative 2^-22.5 / absolute 2^-22.6), the FP32 product of four 1 + y
@@ -956,6 +1005,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 1,
                                       ctx->prior_d > 0 ? (const int8_t *)ctx->prior.p : nullptr,
                                       ctx->prior_d, I.allow});
+            if (use_cond) se.back().cond = ptr<unsigned long long>(pl.conds) + t;
             fd1.push_back(hpp(1, 1, I.fmom));
             fd2.push_back(hpp(1, 0, I.fmom));
             f64.push_back(hpp(1, 1, I.fmom));
@@ -1057,6 +1107,11 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         // re-score passes: double-float pass 1 and 2, then FP64; each is a
         // no-op unless the step's state routes candidates to it (as is the
         // low-part kernel the double-float passes read)
+        if (use_cond) {
+            Launch lc{K_COND_BEGIN};
+            lc.a = t;
+            L.push_back(lc);
+        }
         if (!zl_cond.empty()) {
             Launch l{K_ZLO};
             l.off = blob.add(zl_cond);
@@ -1080,6 +1135,7 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             lrs.a = maxp;
             L.push_back(lrs);
         }
+        if (use_cond) L.push_back(Launch{K_COND_END});
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t + 3;
@@ -1128,33 +1184,64 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         pl.eager = L;
         pl.nodes = 0;
         for (const Launch &l : L)
-            pl.nodes += (l.kind == K_EVENT || l.kind == K_FORK || l.kind == K_JOIN)
+            pl.nodes += (l.kind == K_EVENT || l.kind == K_FORK || l.kind == K_JOIN ||
+                         l.kind == K_COND_BEGIN || l.kind == K_COND_END)
                             ? 0
                             : (l.kind == K_GRAM_TC ? 3 : 1);
         pl.profile = profile ? 1 : 0;
         pl.partial = false;
         return LINGAM_OK;
     }
+    if (use_cond && !ctx->sbody) CK(cudaStreamCreateWithFlags(&ctx->sbody, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    int nodes = 0;
+    int nodes = 0, cnodes = 0, bodies = 0;
     cudaError_t e = cudaSuccess;
+    cudaStream_t cur = s;   // the body of a conditional node is captured on sbody
     for (const Launch &l : L) {
-        e = issue_launch(pl, l, pb, s, true, &nodes);
+        if (l.kind == K_COND_BEGIN) {
+            e = begin_cond_body(s, ctx->sbody, &hconds[l.a]);
+            if (e != cudaSuccess) break;
+            cur = ctx->sbody;
+            ++bodies;
+            continue;
+        }
+        if (l.kind == K_COND_END) {
+            cudaGraph_t body = nullptr;
+            e = cudaStreamEndCapture(ctx->sbody, &body);
+            cur = s;
+            if (e != cudaSuccess) break;
+            continue;
+        }
+        const int before = nodes;
+        e = issue_launch(pl, l, pb, cur, true, &nodes);
+        if (cur != s) cnodes += nodes - before;
         if (e != cudaSuccess) break;
+    }
+    if (cur != s) {   // a failure inside a body: end that capture too
+        cudaGraph_t body = nullptr;
+        cudaStreamEndCapture(ctx->sbody, &body);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (use_cond) {   // no conditional nodes here: capture plain graphs from now on
+            ctx->no_cond = true;
+            return capture_plan(ctx, stop_after_score0, Iout, epsOut);
+        }
         return fail_cuda(ctx, e != cudaSuccess ? e : e2, "graph capture", __LINE__);
     }
-    cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    CK(e);
+    if (use_cond)
+        CK(cudaMemcpy(pl.conds.p, hconds.data(), hconds.size() * sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice));
     if (pl.exec) cudaGraphExecDestroy(pl.exec);
     pl.exec = ex;
     pl.nodes = nodes;
+    pl.cond_nodes = cnodes;
+    pl.cond_bodies = bodies;
     pl.profile = profile ? 1 : 0;
     pl.partial = stop_after_score0;
     return LINGAM_OK;
@@ -1347,6 +1434,8 @@ static lingam_status run_plan(lingam_ctx *ctx, int32_t *const *orders_out, doubl
 
     }
     st.graph_nodes = pl.nodes;
+    st.cond_nodes = pl.exec ? pl.cond_nodes : 0;
+    st.cond_bodies = pl.exec ? pl.cond_bodies : 0;
     if (pl.profile && !pl.pev.empty()) {
         double ph[4] = {0, 0, 0, 0}, units = 0;
         int64_t launches = 0;
@@ -1464,6 +1553,7 @@ lingam_status lingam_destroy(lingam_ctx *ctx)
         if (ctx->ev_side[k]) cudaEventDestroy(ctx->ev_side[k]);
         if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
     }
+    if (ctx->sbody) cudaStreamDestroy(ctx->sbody);
     if (ctx->s) cudaStreamDestroy(ctx->s);
     delete ctx;
     return LINGAM_OK;

@@ -175,6 +175,9 @@ def test_stats_report_the_run(ctx, torch_cuda, datasets):
     c.causal_order(_dev(torch_cuda, ds.X, "fp32"))
     st = c.stats()
     assert st["total_ms"] > 0 and st["graph_nodes"] >= 7 * (ds.d - 1)
+    # every step's re-score block sits under a conditional node of the graph
+    assert st["cond_bodies"] == ds.d - 1
+    assert 6 * (ds.d - 1) <= st["cond_nodes"] < st["graph_nodes"]
 
 
 @pytest.mark.parametrize("tie", [300.0, 1e7])
