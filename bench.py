@@ -590,7 +590,7 @@ def run_one_order(args):
     ds = {"long_n": lambda: gen.long_n(seed=gen.SEEDS[6]), "cfg2": gen.cfg2,
           "cfg3": gen.cfg3}[args.workload]()
     X = torch.from_numpy(ds.X).to("cuda:0")
-    with pkg.Context(0, prec) as ctx:
+    with pkg.Context(0, prec, conditional_rescore=args.conditional_rescore) as ctx:
         if prec in ("mixed", "fp32") and args.tile is not None:
             ctx.set_tuning({"count": 1, "precision": pkg.PREC[prec], "p_max": [2 ** 31 - 1],
                             "tile": [args.tile], "ctas_per_sm": [args.ctas]})
@@ -1017,6 +1017,8 @@ def main():
     ap.add_argument("--ctas", type=int, default=4, help="--one-order --tile: CTAs per SM")
     ap.add_argument("--repeat", type=int, default=1,
                     help="--one-order: timed calls (the first is the profiled one)")
+    ap.add_argument("--conditional-rescore", action="store_true",
+                    help="--one-order (single dataset): conditional re-score blocks in the graph")
     ap.add_argument("--no-batched-sequential", dest="batched_sequential", action="store_false",
                     help="skip the batch's instances as single calls")
     ap.add_argument("--no-configs", dest="configs", action="store_false",

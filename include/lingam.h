@@ -82,7 +82,14 @@ typedef struct {
     double tie_scale;      /* multiplies the FP32 and double-float error
                               bounds that select the candidates re-scored in
                               the next tier; 0 means 1.0 */
-    int32_t reserved[8];
+    int32_t conditional_rescore; /* 1: a single-instance graph puts each step's
+                              re-score launches under a conditional node
+                              that a kernel after the step's select sets, so steps
+                              decided by their FP32 scores skip them (fewer
+                              launches; Nsight Compute cannot profile the
+                              kernel nodes of such a graph); 0 (default):
+                              plain graph */
+    int32_t reserved[7];
 } lingam_opts;
 
 /* Create a context on CUDA device `device`.  opts may be NULL (FP32, no

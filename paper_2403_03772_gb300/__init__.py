@@ -35,7 +35,8 @@ class LingamError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("tie_scale", ctypes.c_double), ("reserved", ctypes.c_int32 * 8)]
+                ("tie_scale", ctypes.c_double), ("conditional_rescore", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -201,9 +202,10 @@ class Context:
     """A library context on one CUDA device (owns workspace and graphs)."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", profile: bool = False,
-                 tie_scale: float = 0.0):
+                 tie_scale: float = 0.0, conditional_rescore: bool = False):
         lib = load()
-        opts = Opts(PREC[precision], int(bool(profile)), float(tie_scale))
+        opts = Opts(PREC[precision], int(bool(profile)), float(tie_scale),
+                    int(bool(conditional_rescore)))
         h = ctypes.c_void_p()
         code = lib.lingam_create(ctypes.byref(h), int(device), ctypes.byref(opts))
         if code != OK:

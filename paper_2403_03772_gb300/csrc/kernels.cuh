@@ -193,8 +193,6 @@ struct SelectParams {
     const int8_t *prior;  // [ldp][ldp] ancestry knowledge by original index, or null:
     int64_t ldp;          //   prior[i ldp + j] = 1 x_j is an ancestor of x_i, 0 is not, -1 unknown
     uint8_t *allow;       // [p] workspace: positions that may be chosen at this step
-    const unsigned long long *cond;   // or null: the graph's conditional handle of the
-                                      // step's re-score block, set to 1 iff candidates remain
 };
 
 struct RefineSelectParams {
@@ -325,6 +323,8 @@ int score_blocks(int p);
 cudaError_t launch_score_b(const ScoreParams *P, const int *prefix, int count, int total_blocks,
                            int maxp, cudaStream_t s);
 cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s);
+cudaError_t launch_set_rescore_cond(const DevState *st, const unsigned long long *cond,
+                                    cudaStream_t s);
 cudaError_t launch_refine_select_b(const RefineSelectParams *P, int count, int maxp,
                                    cudaStream_t s);
 

@@ -259,7 +259,6 @@ __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restric
             st->ncand = 1;
             st->resolved = 1;
             st->pass_begin = st->pass_end = 0;
-            if (P.cond) cudaGraphSetConditional(*P.cond, 0u);   // the re-score block is skipped
         }
         return;
     }
@@ -286,7 +285,6 @@ __global__ void __launch_bounds__(1024) k_select_b(const SelectParams *__restric
         st->pass_end = P.tier == 1 ? min(2, cnt) : cnt;
         st->refined_steps += 1;
         if (cnt > st->cand_max) st->cand_max = cnt;
-        if (P.cond) cudaGraphSetConditional(*P.cond, 1u);
     }
 }
 
@@ -294,6 +292,22 @@ cudaError_t launch_select_b(const SelectParams *P, int count, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     k_select_b<<<count, 1024, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+// The condition of a step's conditional re-score block (graphs captured with
+// conditional_rescore): 1 iff the select kernel left candidates.  A kernel of
+// its own, so that the select kernel stays free of device-side graph calls.
+__global__ void k_set_rescore_cond(const DevState *__restrict__ st,
+                                   const unsigned long long *__restrict__ cond)
+{
+    cudaGraphSetConditional(*cond, st->resolved ? 0u : 1u);
+}
+
+cudaError_t launch_set_rescore_cond(const DevState *st, const unsigned long long *cond,
+                                    cudaStream_t s)
+{
+    k_set_rescore_cond<<<1, 1, 0, s>>>(st, cond);
     return cudaGetLastError();
 }
 

@@ -128,7 +128,7 @@ struct StepSplit {
 enum LaunchKind {
     K_GRAM, K_IOTA, K_REG_INIT, K_PAIR, K_HP_ALL, K_SCORE, K_SELECT, K_HP_PASS, K_REFINE,
     K_REGRESS, K_DOWNDATE, K_FINISH, K_EVENT, K_FILL_NAN, K_GRAM_TC, K_ZLO, K_FORK, K_JOIN,
-    K_COND_BEGIN, K_COND_END
+    K_COND_BEGIN, K_COND_END, K_SET_COND
 };
 
 // Batched MIXED calls compute the instances' tensor-core covariances on up
@@ -634,6 +634,9 @@ static cudaError_t issue_launch(Plan &pl, const Launch &l, char *pb, cudaStream_
         ++*nodes;   // k_hvar_b + k_score_b
         break;
     case K_SELECT: e = launch_select_b((const SelectParams *)P, l.count, s); break;
+    case K_SET_COND:
+        e = launch_set_rescore_cond(pl.inst[0].state, ptr<unsigned long long>(pl.conds) + l.a, s);
+        break;
     case K_HP_PASS: e = launch_pairs_hp_b(l.c, (const HpParams *)P, l.count, l.a, s); break;
     case K_REFINE:
         e = launch_refine_select_b((const RefineSelectParams *)P, l.count, l.a, s);
@@ -728,12 +731,16 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
     const bool sharded = ctx->shard_n > 1;
     cudaStream_t s = ctx->s;
     const double tie = ctx->opts.tie_scale > 0 ? ctx->opts.tie_scale : 1.0;
-    // A single-instance graph puts each step's re-score block (the low parts
-    // and the double-float and FP64 passes, no-ops unless candidates remain)
-    // under a conditional node that the select kernel sets: steps decided by
-    // their FP32 scores skip those launches.  A batch keeps them (the select
-    // blocks of its instances would race to set one condition).
-    const bool use_cond = pl.inst.size() == 1 && !sharded && !stop_after_score0 && !ctx->no_cond;
+    // On request (opts.conditional_rescore) a single-instance graph puts each
+    // step's re-score block (the low parts and the double-float and FP64
+    // passes, no-ops unless candidates remain) under a conditional node that
+    // a one-thread kernel after the select kernel sets: steps decided by
+    // their FP32 scores skip those launches.  A batch keeps them (one
+    // condition would have to summarise all its instances).  Off by default:
+    // Nsight Compute does not profile the kernel nodes of a graph with
+    // conditional nodes, and at d = 1000 the blocks cost more than they save.
+    const bool use_cond = ctx->opts.conditional_rescore != 0 && pl.inst.size() == 1 &&
+                          !sharded && !stop_after_score0 && !ctx->no_cond;
     if (use_cond) CK(ensure(pl.conds, (size_t)pl.maxd * sizeof(unsigned long long)));
     std::vector<unsigned long long> hconds(use_cond ? pl.maxd : 0, 0ull);
     // Moment-error model of the FP32 pair kernels and the regress kernel
@@ -1005,7 +1012,6 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
             se.push_back(SelectParams{I.M, I.E, Uc, p, I.state, I.scratch, hp ? 2 : 1,
                                       ctx->prior_d > 0 ? (const int8_t *)ctx->prior.p : nullptr,
                                       ctx->prior_d, I.allow});
-            if (use_cond) se.back().cond = ptr<unsigned long long>(pl.conds) + t;
             fd1.push_back(hpp(1, 1, I.fmom));
             fd2.push_back(hpp(1, 0, I.fmom));
             f64.push_back(hpp(1, 1, I.fmom));
@@ -1099,6 +1105,11 @@ static lingam_status capture_plan(lingam_ctx *ctx, bool stop_after_score0, doubl
         lse.off = blob.add(se);
         lse.count = cnt;
         L.push_back(lse);
+        if (use_cond) {
+            Launch lsc{K_SET_COND};
+            lsc.a = t;
+            L.push_back(lsc);
+        }
         if (profile) {
             Launch ev{K_EVENT};
             ev.a = EV_PER_STEP * t + 2;

@@ -175,9 +175,28 @@ def test_stats_report_the_run(ctx, torch_cuda, datasets):
     c.causal_order(_dev(torch_cuda, ds.X, "fp32"))
     st = c.stats()
     assert st["total_ms"] > 0 and st["graph_nodes"] >= 7 * (ds.d - 1)
-    # every step's re-score block sits under a conditional node of the graph
+    assert st["cond_bodies"] == 0 and st["cond_nodes"] == 0   # plain graph by default
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_conditional_rescore_blocks_keep_the_order(torch_cuda, datasets, prec):
+    """With conditional_rescore each step's re-score launches sit under a
+    conditional graph node set by the select kernel; the order and the score
+    history must be those of the plain graph (and the oracle's)."""
+    import paper_2403_03772_gb300 as pkg
+    ds = datasets("cfg2")
+    gold, _ = read_golden_order("cfg2")
+    X = _dev(torch_cuda, ds.X, prec)
+    with pkg.Context(0, prec, conditional_rescore=True) as c:
+        order, scores = c.causal_order(X, scores=True)
+        st = c.stats()
+        again = c.causal_order(X)
+    assert list(order) == list(again) == list(gold)
     assert st["cond_bodies"] == ds.d - 1
     assert 6 * (ds.d - 1) <= st["cond_nodes"] < st["graph_nodes"]
+    with pkg.Context(0, prec) as c:
+        _, plain = c.causal_order(X, scores=True)
+    np.testing.assert_array_equal(np.nan_to_num(scores), np.nan_to_num(plain))
 
 
 @pytest.mark.parametrize("tie", [300.0, 1e7])
