@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "conv.cuh"
 #include "kernels.cuh"
 
 namespace lg {
@@ -303,9 +304,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int q = 0; q < 32; ++q) {
                         const int col = bj * TC_TILE + cb * 32 + q;
                         if (col < P.d) {
-                            const double v = ldexp((((double)a0[q] + (double)a1[q]) +
-                                                    (double)a2[q]) + (double)a3[q],
-                                                   erow + s_ecol[cb * 32 + q]);
+                            // exact conversions off the FP64 pipe; the scale
+                            // 2^k by one multiply (ldexp where 2^k is not a
+                            // normal double)
+                            const double sum = ((f32_to_f64(a0[q]) + f32_to_f64(a1[q])) +
+                                                f32_to_f64(a2[q])) + f32_to_f64(a3[q]);
+                            const int k = erow + s_ecol[cb * 32 + q];
+                            const double v =
+                                (k >= -1022 && k <= 1023)
+                                    ? sum * __longlong_as_double((long long)(k + 1023) << 52)
+                                    : ldexp(sum, k);
                             o[q] = first_drain ? v : o[q] + v;
                         }
                     }

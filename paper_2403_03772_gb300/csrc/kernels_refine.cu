@@ -21,6 +21,7 @@
 
 #include <math.h>
 
+#include "conv.cuh"
 #include "df.cuh"
 #include "kernels.cuh"
 
@@ -138,7 +139,7 @@ struct DfAcc {
     }
     __device__ __forceinline__ void fold()
     {
-        d += (double)s.hi + (double)s.lo;
+        d += f32_to_f64(s.hi) + f32_to_f64(s.lo);   // exact conversions off the FP64 pipe
         s = dfl{0.0f, 0.0f};
     }
 };
