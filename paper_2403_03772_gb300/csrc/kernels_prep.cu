@@ -353,20 +353,29 @@ __global__ void __launch_bounds__(256) k_regress_b(const RegressParams *__restri
         pos = col + (col >= mpos ? 1 : 0);
     }
     const int i = P.U[pos];
-    const double cii = P.C[(int64_t)i * P.ldc + i];
-    if (INIT) {
-        var = cii;
-    } else {
-        const double cmm = P.C[(int64_t)m * P.ldc + m];
-        const double cim = P.C[(int64_t)i * P.ldc + m];
-        coef = cim / cmm;
-        var = cii - (cim * cim) / cmm;
+    // the column's coefficient and scale, by one thread (FP64 divisions and the
+    // square root cost dozens of FP64-pipe instructions each)
+    __shared__ double s_coef, s_isd;
+    if (threadIdx.x == 0) {
+        const double cii = P.C[(int64_t)i * P.ldc + i];
+        if (INIT) {
+            var = cii;
+        } else {
+            const double cmm = P.C[(int64_t)m * P.ldc + m];
+            const double cim = P.C[(int64_t)i * P.ldc + m];
+            coef = cim / cmm;
+            var = cii - (cim * cim) / cmm;
+        }
+        if (!(var > 1e-12 * P.ref_var[i])) {
+            set_status(P.status, ST_DEGENERATE);
+            var = 1.0;
+        }
+        s_coef = coef;
+        s_isd = 1.0 / sqrt(var);
     }
-    if (!(var > 1e-12 * P.ref_var[i])) {
-        if (threadIdx.x == 0) set_status(P.status, ST_DEGENERATE);
-        var = 1.0;
-    }
-    const double isd = 1.0 / sqrt(var);
+    __syncthreads();
+    coef = s_coef;
+    const double isd = s_isd;
     double *ri = P.R + (int64_t)i * P.ldr;
     const double *rm = INIT ? nullptr : P.R + (int64_t)m * P.ldr;
     float *zo = P.z + (int64_t)col * P.ldz;

@@ -30,9 +30,30 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     const ScoreParams P = Ps[inst];
     const int rb = blockIdx.x - prefix[inst];   // row block of the instance
     float *wsh = reinterpret_cast<float *>(hsh + P.p);
-    const double invn = 1.0 / (double)P.n;
     const bool df = P.mom2 != nullptr;
     dfl *hd = reinterpret_cast<dfl *>(wsh + P.p + (P.p & 1));   // h(z_j) as double-floats
+    // the block's constants, by one thread (an FP64 division and the FP64 ->
+    // double-float splits are dozens of FP64-pipe instructions per thread)
+    __shared__ double s_invn;
+    __shared__ float s_cst[10];   // c1, b1, c2 as (hi, lo); epsI and the model's d1, d2, da
+    if (threadIdx.x == 0) {
+        const double invn0 = 1.0 / (double)P.n;
+        s_invn = invn0;
+        if (df) {
+            const dfl c1 = df_split(P.a1 * invn0), b1 = df_split(P.b1),
+                      c2 = df_split(P.a2 * invn0);
+            s_cst[0] = c1.hi;
+            s_cst[1] = c1.lo;
+            s_cst[2] = b1.hi;
+            s_cst[3] = b1.lo;
+            s_cst[4] = c2.hi;
+            s_cst[5] = c2.lo;
+            s_cst[6] = (float)P.epsI;
+            s_cst[7] = (float)P.model.d1;
+            s_cst[8] = (float)P.model.d2;
+            s_cst[9] = (float)P.model.da;
+        }
+    }
     for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
         if (df && P.hvar) {
             // computed once for the step by k_hvar_b (no FP64 work per block)
@@ -40,11 +61,12 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
             hd[j] = dfl{v.x, v.y};
             wsh[j] = v.z;
         } else {
-            score_var(P, j, invn, hsh[j], wsh[j]);
+            score_var(P, j, 1.0 / (double)P.n, hsh[j], wsh[j]);
             if (df) hd[j] = df_split(hsh[j]);
         }
     }
     __syncthreads();
+    const double invn = s_invn;
     // SCORE_WPR warps per row i: warp wr of the row takes j = 32 wr + lane +
     // 32 SCORE_WPR k; the row's partial sums are added in warp order.
     __shared__ double racc[8], rerr[8];
@@ -54,14 +76,13 @@ __global__ void __launch_bounds__(256, 3) k_score_b(const ScoreParams *__restric
     double acc = 0.0, err = 0.0;
     if (i < P.p && df) {
         // FP32-scored step: double-float combine, FP32 bounds
-        const dfl c1 = df_split(P.a1 * invn), b1 = df_split(P.b1), c2 = df_split(P.a2 * invn);
+        const dfl c1{s_cst[0], s_cst[1]}, b1{s_cst[2], s_cst[3]}, c2{s_cst[4], s_cst[5]};
         dfl accd{0.0f, 0.0f};
         float errf = 0.0f;
         const int oi = P.U[i];
         const float wi = wsh[i];
-        // the model's FP32 constants, converted once (not per entry)
-        const float epsI = (float)P.epsI, md1 = (float)P.model.d1, md2 = (float)P.model.d2,
-                    mda = (float)P.model.da;
+        // the model's FP32 constants, converted once per block (not per entry)
+        const float epsI = s_cst[6], md1 = s_cst[7], md2 = s_cst[8], mda = s_cst[9];
         for (int j = wr * 32 + lane; j < P.p; j += 32 * SCORE_WPR) {
             if (j == i) continue;
             if (P.shard_n > 1 && shard_owner(i, j, P.p, P.shard_n) != P.shard_rank) continue;
