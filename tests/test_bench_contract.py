@@ -1,6 +1,7 @@
 """bench.py's host-side contract pieces that need no GPU: the recorded DRAM
 traffic of the pair kernel is reported only for the sources and tile it was
-measured on, and the work count matches its closed form."""
+measured on, the work count matches its closed form, and the count of
+launched kernels leaves out the conditional re-score blocks that do not run."""
 import copy
 
 import bench
@@ -69,3 +70,13 @@ def test_oracle_errors_read_the_stored_values():
     assert abs(e["max_abs_dB"] - 2e-5) < 1e-12
     assert bench.golden_rows("cfg2", "0" * 16) is None
     assert bench.oracle_errors("cfg2", "0" * 16, order)["order_equals_oracle"] is None
+
+
+def test_launched_kernels_count_conditional_blocks_only_where_they_run():
+    # plain graph: every kernel node runs
+    assert bench.launched_nodes({"graph_nodes": 13, "cond_nodes": 0, "cond_bodies": 0,
+                                 "refined_steps": 5}) == 13
+    # 10 steps with a conditional block of 7 kernel nodes each; 4 steps left
+    # candidates, so only their blocks run
+    st = {"graph_nodes": 10 * 14, "cond_nodes": 10 * 7, "cond_bodies": 10, "refined_steps": 4}
+    assert bench.launched_nodes(st) == 10 * 7 + 4 * 7
